@@ -1,0 +1,174 @@
+/*
+ * lm.h -- C ABI of the GB300 local-max matching library (liblm.so).
+ *
+ * Computes maximal matchings with the local max algorithm of Birn, Osipov,
+ * Sanders, Schulz and Sitchinava, "Efficient Parallel and External Matching"
+ * (Sec. 1 defines the algorithm; Sec. 2 the data-parallel phase: candidate
+ * selection by a segmented maximum over each vertex's edges, mutual-choice
+ * matching, deletion and compaction of the edge set, repeated until no edge
+ * is left).
+ *
+ * Edge order.  Edges are compared by the 64-bit key
+ *     K(e) = ord(w_e) << 32 | perm_seed(e)
+ * where ord() maps a non-NaN float32 monotonically to uint32 (-0.0 == +0.0)
+ * and perm_seed() is a seeded bijection of the 32-bit edge index e (the index
+ * of the edge in the caller's edge list).  This total order stands in for the
+ * paper's "ties broken by random perturbation" (Sec. 1); it is fixed for the
+ * whole call.  With a strict order fixed for the run, local max selects
+ * exactly the greedy matching of Sec. 4 under the same order, so the result
+ * is unique for a given (graph, seed).
+ *     perm_seed(e) = fmix32(fmix32(e ^ k0) ^ k1),
+ *     (k0, k1) = low and high 32 bits of SplitMix64(seed) (its first output),
+ *     fmix32 = the MurmurHash3 32-bit finaliser.
+ *
+ * Conventions.
+ *   - All functions return LM_OK (0) or an LM_E* code; lm_strerror() names it.
+ *   - Vertex ids and edge indices are uint32; n >= 1 unless m == 0 as well;
+ *     2*m must fit in 32 bits (m <= 2^31 - 1).
+ *   - Pointers are host or device (GPU global memory of the context's
+ *     device); where both are accepted the kind is detected with
+ *     cudaPointerGetAttributes, and `mem` arguments say which explicitly.
+ *   - Calls on one context are ordered on the context's stream and are not
+ *     thread-safe with respect to each other, except lm_submit / lm_poll /
+ *     lm_wait, which may be called from any thread.
+ *   - After an LM_ECUDA error the context is poisoned: every later call on it
+ *     returns LM_ECUDA.  LM_ETIMEOUT means a bounded device-side wait gave up;
+ *     the result of that call is undefined but the context stays usable.
+ */
+#ifndef LM_H
+#define LM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LM_OK        0
+#define LM_EINVAL    1   /* bad argument: null pointer, id >= n, self loop, NaN weight, sizes */
+#define LM_ENOMEM    2   /* device or pinned allocation failed, or HBM budget exceeded */
+#define LM_EAGAIN    3   /* serving: no admission slot / budget right now (retry later) */
+#define LM_ETIMEOUT  4   /* a bounded device wait or lm_wait's timeout expired */
+#define LM_ECUDA     5   /* CUDA runtime error; the context is poisoned */
+#define LM_ENOTFOUND 6   /* unknown ticket */
+
+#define LM_NIL  0xFFFFFFFFu  /* mate[v] of an unmatched vertex */
+
+#define LM_HOST    0
+#define LM_DEVICE  1
+
+/* lm_config.flags */
+#define LM_F_PROFILE   1u   /* record CUDA events around every kernel (fills lm_stats timings) */
+
+typedef struct lm_ctx lm_ctx;
+typedef struct lm_graph lm_graph;
+
+typedef struct {
+    int      device;            /* CUDA device ordinal */
+    void*    stream;            /* cudaStream_t the context works on; NULL = the legacy default stream */
+    uint64_t hbm_budget_bytes;  /* serving admission budget; 0 = 40 GiB */
+    uint32_t max_slots;         /* serving: maximum requests in flight; 0 = 4096 */
+    uint32_t flags;             /* LM_F_* */
+} lm_config;
+
+#define LM_STATS_ROUNDS 64
+/* kernel kinds (index into the per-kind arrays of lm_stats) */
+#define LM_K_INIT    0   /* reset of mate / candidate / deletion state */
+#define LM_K_SWEEP   1   /* candidate (segmented max) + deletion + compaction over live entries */
+#define LM_K_VERTEX  2   /* mutual-choice match over live vertices + tile index */
+#define LM_K_TAIL    3   /* single-CTA finish of the last rounds */
+#define LM_K_OTHER   4   /* result conversion, batch set-up */
+#define LM_K_COUNT   5
+
+typedef struct {
+    uint32_t rounds;                        /* local-max iterations performed */
+    uint32_t launches;                      /* kernels launched by the call */
+    uint64_t matched;                       /* |M| */
+    uint64_t round_m[LM_STATS_ROUNDS];      /* live edges at the start of round r (r < 64) */
+    uint64_t round_n[LM_STATS_ROUNDS];      /* live vertices at the start of round r (r < 64) */
+    /* filled only with LM_F_PROFILE: */
+    double   kernel_ms[LM_K_COUNT];         /* summed device time per kernel kind */
+    uint32_t kernel_launches[LM_K_COUNT];   /* launches per kernel kind */
+    uint64_t kernel_bytes[LM_K_COUNT];      /* modelled algorithmic HBM bytes per kernel kind */
+    double   total_ms;                      /* device time from first to last kernel of the call */
+} lm_stats;
+
+/* Create a context on cfg->device working on cfg->stream.  *out receives the
+ * handle, owned by the caller until lm_destroy.  Errors: LM_EINVAL (null
+ * argument, bad device), LM_ECUDA. */
+int  lm_create(const lm_config* cfg, lm_ctx** out);
+
+/* Destroy a context: waits for its stream, stops the serving thread, frees
+ * every device / pinned buffer it owns.  Graphs created on it must be
+ * destroyed first.  NULL is ignored. */
+void lm_destroy(lm_ctx* ctx);
+
+/* Build a device graph from an undirected edge list (Sec. 2, "graph
+ * representation": offsets V over the vertices, the adjacency array A of
+ * (vertex, edge) entries, and per-edge records).  Edge i joins eu[i] and ev[i]
+ * with weight w[i]; its index i is the edge id used by perm_seed.  Parallel
+ * edges are allowed.
+ *   n, m    : vertex and edge counts (m may be 0; 2*m < 2^32)
+ *   eu, ev  : uint32[m] endpoints, each < n, eu[i] != ev[i]
+ *   w       : float32[m] weights, any non-NaN value (+-inf and -0.0 allowed)
+ *   mem     : LM_HOST or LM_DEVICE, where eu / ev / w live
+ * The arrays are copied; the caller keeps ownership.  The graph is immutable
+ * and may be matched any number of times, also concurrently through
+ * different contexts on the same device.  Errors: LM_EINVAL (null pointer
+ * with m > 0, n == 0 with m > 0, endpoint >= n, self loop, NaN weight,
+ * m > 2^31 - 1), LM_ENOMEM, LM_ECUDA. */
+int  lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev,
+                     const float* w, int mem, lm_graph** out);
+
+/* Free a graph's device memory (waits for the context's stream).  NULL ok. */
+void lm_graph_destroy(lm_graph* g);
+
+/* Vertex count, edge count and device bytes held by a graph. */
+int  lm_graph_info(const lm_graph* g, uint32_t* n, uint32_t* m, uint64_t* device_bytes);
+
+/* Maximal matching of g by local max under the order K (Sec. 1, Sec. 2):
+ *   mate : uint32[n], caller-owned, host or device memory; on success
+ *          mate[v] is v's partner or LM_NIL.
+ *   stats: optional (NULL ok).
+ * Returns when mate is complete.  Scratch memory is the context's
+ * (allocated on first use, reused).  Errors: LM_EINVAL, LM_ENOMEM, LM_ECUDA,
+ * LM_ETIMEOUT. */
+int  lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_stats* stats);
+
+/* Match `count` independent graphs together: their rounds run in the same
+ * kernel launches over the disjoint union of the graphs (each graph keeps its
+ * own seed and edge ids, so every result equals lm_match of that graph alone).
+ *   g[i], seeds[i], mates[i] (uint32[n_i], host or device), stats[i] (optional
+ *   array of `count`, or NULL).  stats[i].rounds is graph i's own round count.
+ * Errors: as lm_match. */
+int  lm_batch_match(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uint64_t* seeds,
+                    uint32_t* const* mates, lm_stats* stats);
+
+/* Serving: queue a matching request and return at once with a ticket.  A
+ * scheduler thread of the context admits requests while their device
+ * footprint fits the HBM budget and a slot is free, and runs rounds of all
+ * admitted requests together (a request joins between rounds).  mate
+ * (uint32[n], host or device) must stay valid until the request completes;
+ * the graph must outlive it.  Errors: LM_EINVAL, LM_EAGAIN (queue full),
+ * LM_ENOMEM (the request alone exceeds the budget), LM_ECUDA. */
+int  lm_submit(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, uint64_t* ticket);
+
+/* *done = 1 once the request's mate is complete (then stats, if non-NULL, is
+ * filled and the ticket is released), else 0.  Errors: LM_ENOTFOUND, or the
+ * request's own error code. */
+int  lm_poll(lm_ctx* ctx, uint64_t ticket, int* done, lm_stats* stats);
+
+/* Block until the request completes or timeout_ms passes (LM_ETIMEOUT; the
+ * ticket stays valid).  Does not release the ticket: call lm_poll after. */
+int  lm_wait(lm_ctx* ctx, uint64_t ticket, uint32_t timeout_ms);
+
+/* Static description of an error code. */
+const char* lm_strerror(int code);
+
+/* Last detailed error message of the context (empty if none). */
+const char* lm_last_error(const lm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LM_H */

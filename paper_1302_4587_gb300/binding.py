@@ -1,0 +1,242 @@
+"""Thin Python binding of liblm.so (include/lm.h), argument marshalling only.
+
+The functions carry the C names.  Arrays are torch tensors (CUDA or CPU) or
+numpy arrays; device memory and streams come from PyTorch.  Every step of the
+matching runs in the library's CUDA kernels: there is no Python or CPU
+fallback, and loading fails loudly when the library cannot be built or
+loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+LM_OK, LM_EINVAL, LM_ENOMEM, LM_EAGAIN, LM_ETIMEOUT, LM_ECUDA, LM_ENOTFOUND = range(7)
+LM_NIL = 0xFFFFFFFF
+LM_HOST, LM_DEVICE = 0, 1
+LM_F_PROFILE = 1
+LM_STATS_ROUNDS = 64
+LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_TAIL, LM_K_OTHER, LM_K_COUNT = range(6)
+
+# names exported by include/lm.h (the loader checks that every one is present)
+EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
+           "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error")
+
+
+class LmConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("max_slots", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class LmStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("matched", ctypes.c_uint64),
+                ("round_m", ctypes.c_uint64 * LM_STATS_ROUNDS), ("round_n", ctypes.c_uint64 * LM_STATS_ROUNDS),
+                ("kernel_ms", ctypes.c_double * LM_K_COUNT), ("kernel_launches", ctypes.c_uint32 * LM_K_COUNT),
+                ("kernel_bytes", ctypes.c_uint64 * LM_K_COUNT), ("total_ms", ctypes.c_double)]
+
+    def to_dict(self) -> dict:
+        r = int(self.rounds)
+        k = min(r, LM_STATS_ROUNDS)
+        return {"rounds": r, "launches": int(self.launches), "matched": int(self.matched),
+                "round_m": [int(x) for x in self.round_m[:k]], "round_n": [int(x) for x in self.round_n[:k]],
+                "kernel_ms": [float(x) for x in self.kernel_ms],
+                "kernel_launches": [int(x) for x in self.kernel_launches], "total_ms": float(self.total_ms)}
+
+
+class LmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load liblm.so (building it in-tree first if needed).  Raises if impossible."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        missing = [n for n in EXPORTS if not hasattr(lib, n)]
+        if missing:
+            raise RuntimeError(f"liblm.so lacks exports {missing}")
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        lib.lm_create.argtypes = [ctypes.POINTER(LmConfig), ctypes.POINTER(vp)]
+        lib.lm_destroy.argtypes = [vp]
+        lib.lm_destroy.restype = None
+        lib.lm_graph_create.argtypes = [vp, u32, u32, vp, vp, vp, ctypes.c_int, ctypes.POINTER(vp)]
+        lib.lm_graph_destroy.argtypes = [vp]
+        lib.lm_graph_destroy.restype = None
+        lib.lm_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u64)]
+        lib.lm_match.argtypes = [vp, vp, u64, vp, ctypes.POINTER(LmStats)]
+        lib.lm_batch_match.argtypes = [vp, ctypes.POINTER(vp), u32, ctypes.POINTER(u64), ctypes.POINTER(vp),
+                                       ctypes.POINTER(LmStats)]
+        lib.lm_submit.argtypes = [vp, vp, u64, vp, ctypes.POINTER(u64)]
+        lib.lm_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(LmStats)]
+        lib.lm_wait.argtypes = [vp, u64, u32]
+        lib.lm_strerror.argtypes = [ctypes.c_int]
+        lib.lm_strerror.restype = ctypes.c_char_p
+        lib.lm_last_error.argtypes = [vp]
+        lib.lm_last_error.restype = ctypes.c_char_p
+        _LIB = lib
+        return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != LM_OK:
+        lib = load()
+        msg = lib.lm_strerror(rc).decode()
+        if ctx is not None:
+            detail = lib.lm_last_error(ctx).decode()
+            if detail:
+                msg = f"{msg}: {detail}"
+        raise LmError(rc, msg)
+
+
+def _ptr(a):
+    """(pointer, keepalive, is_device) of a torch tensor or numpy array."""
+    if a is None:
+        return None, None, False
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, a, False
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), a, a.is_cuda
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as(a, np_dtype, torch_dtype):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np_dtype)
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch_dtype:
+            a = a.to(torch_dtype)
+        return a.contiguous()
+    return np.ascontiguousarray(np.asarray(a), dtype=np_dtype)
+
+
+# ------------------------------------------------------------------ C-named functions
+
+def lm_create(device: int = 0, stream=None, hbm_budget_bytes: int = 0, max_slots: int = 0, flags: int = 0):
+    """Create a context; `stream` is a torch.cuda.Stream, a raw cudaStream_t int, or None
+    for torch's current stream on `device`."""
+    lib = load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    cfg = LmConfig(device, ctypes.c_void_p(stream), hbm_budget_bytes, max_slots, flags)
+    out = ctypes.c_void_p()
+    _check(lib.lm_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def lm_destroy(ctx) -> None:
+    load().lm_destroy(ctx)
+
+
+def lm_graph_create(ctx, n: int, eu, ev, w):
+    """Build a device graph from edge arrays (uint32 endpoints, float32 weights),
+    all on the host (numpy / CPU tensors) or all on the device (CUDA tensors)."""
+    lib = load()
+    import torch
+    u32 = torch.int32
+    eu = _as(eu, np.uint32, u32)
+    ev = _as(ev, np.uint32, u32)
+    w = _as(w, np.float32, torch.float32)
+    pu, ku, du = _ptr(eu)
+    pv, kv, dv = _ptr(ev)
+    pw, kw, dw = _ptr(w)
+    m = int(eu.shape[0])
+    if not (int(ev.shape[0]) == m == int(w.shape[0])):
+        raise ValueError("eu, ev, w must have the same length")
+    if len({du, dv, dw}) != 1:
+        raise ValueError("eu, ev, w must all be host arrays or all device tensors")
+    mem = LM_DEVICE if du else LM_HOST
+    out = ctypes.c_void_p()
+    _check(lib.lm_graph_create(ctx, n, m, pu, pv, pw, mem, ctypes.byref(out)), ctx)
+    return out
+
+
+def lm_graph_destroy(g) -> None:
+    load().lm_graph_destroy(g)
+
+
+def lm_graph_info(g):
+    n, m, b = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(load().lm_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(b)))
+    return int(n.value), int(m.value), int(b.value)
+
+
+def lm_match(ctx, g, seed: int, mate=None, stats: bool = False):
+    """Run local max on g; `mate` is an int32 tensor of n entries (CUDA or CPU) or a
+    uint32 numpy array, allocated on the graph's device when None.  Returns mate
+    (and the stats dict when stats=True)."""
+    lib = load()
+    if mate is None:
+        import torch
+        n = lm_graph_info(g)[0]
+        dev = torch.cuda.current_device()
+        mate = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{dev}")[:n]
+    p, keep, _ = _ptr(mate)
+    st = LmStats()
+    _check(lib.lm_match(ctx, g, seed & (2**64 - 1), p, ctypes.byref(st)), ctx)
+    return (keep, st.to_dict()) if stats else keep
+
+
+def lm_batch_match(ctx, graphs, seeds, mates, stats: bool = False):
+    lib = load()
+    cnt = len(graphs)
+    G = (ctypes.c_void_p * cnt)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
+    S = (ctypes.c_uint64 * cnt)(*[int(s) & (2**64 - 1) for s in seeds])
+    ptrs, keep = [], []
+    for mt in mates:
+        p, k, _ = _ptr(mt)
+        ptrs.append(p)
+        keep.append(k)
+    M = (ctypes.c_void_p * cnt)(*ptrs)
+    st = (LmStats * cnt)()
+    _check(lib.lm_batch_match(ctx, G, cnt, S, M, st), ctx)
+    return (keep, [s.to_dict() for s in st]) if stats else keep
+
+
+def lm_submit(ctx, g, seed: int, mate) -> int:
+    p, _, _ = _ptr(mate)
+    t = ctypes.c_uint64()
+    _check(load().lm_submit(ctx, g, seed & (2**64 - 1), p, ctypes.byref(t)), ctx)
+    return int(t.value)
+
+
+def lm_poll(ctx, ticket: int):
+    """(done, stats dict or None); raises the request's error if it failed."""
+    d = ctypes.c_int()
+    st = LmStats()
+    _check(load().lm_poll(ctx, ticket, ctypes.byref(d), ctypes.byref(st)), ctx)
+    return bool(d.value), (st.to_dict() if d.value else None)
+
+
+def lm_wait(ctx, ticket: int, timeout_ms: int) -> bool:
+    rc = load().lm_wait(ctx, ticket, timeout_ms)
+    if rc == LM_ETIMEOUT:
+        return False
+    _check(rc, ctx)
+    return True
+
+
+def lm_strerror(code: int) -> str:
+    return load().lm_strerror(code).decode()

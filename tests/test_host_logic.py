@@ -1,0 +1,56 @@
+"""CPU checks of the CUDA library's host-side logic and of its C ABI surface
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1302_4587_gb300", "csrc")
+
+
+def test_segmented_aggregate_is_a_monoid(tmp_path):
+    exe = str(tmp_path / "agg_check")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I" + CSRC, os.path.join(ROOT, "tests", "host", "agg_check.cpp"),
+                           "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "lm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    import paper_1302_4587_gb300 as lm
+    lib = lm.load()
+    declared = _declared_functions()
+    assert "lm_match" in declared and "lm_batch_match" in declared and "lm_submit" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) <= set(lm.EXPORTS) | set(declared)
+    nm = subprocess.run(["nm", "-D", "--defined-only", lm._build.LIB], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in nm.splitlines() if " T " in l}
+    assert set(declared) <= exported
+    # nothing beyond the header leaks out as an lm_ symbol
+    assert {s for s in exported if s.startswith("lm_")} == set(declared)
+
+
+def test_strerror_without_gpu():
+    import paper_1302_4587_gb300 as lm
+    assert lm.lm_strerror(lm.LM_OK) == "ok"
+    assert "invalid" in lm.lm_strerror(lm.LM_EINVAL)
+    assert lm.lm_strerror(999) == "unknown error"
+
+
+def test_kernels_compile_for_sm103a_without_spills_in_vertex_pass():
+    # -Xptxas -v report of the kernel translation unit (compile only, no GPU)
+    out = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
+                          "-c", os.path.join(CSRC, "lm_kernels.cu"), "-o", os.devnull],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert "k_vertex_live" in out.stderr
