@@ -776,11 +776,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* in,
 size_t exclusive_scan_tmp_words(uint32_t count) {
     size_t words = 0;
     uint64_t c = count;
-    while (c > 1) {
+    while (c > SCAN_TILE) {
         c = (c + SCAN_TILE - 1) / SCAN_TILE;
-        words += c + 1;
+        words += 2 * c + 2;  // block sums and their scan at this level
     }
-    return words + 2;
+    return words + 4;
 }
 
 int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint32_t count, uint32_t* tmp,
