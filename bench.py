@@ -125,6 +125,9 @@ def make_workload(name: str):
     if name == "rmat23":
         return synth.rmat(scale=23, edge_factor=16, seed=3), 103, \
             "R-MAT scale 23, edge factor 16, a=.57 b=.19 c=.19 d=.05, relabelled, dedup, w~U[0,1)"
+    if name == "rmat21":
+        return synth.rmat(scale=21, edge_factor=16, seed=3), 103, \
+            "R-MAT scale 21, edge factor 16 (profiling-size case of the R-MAT family)"
     if name == "grid":
         return synth.grid(1024, 1024, 0.05, seed=2), 102, "2D grid 1024x1024 4-neighbour + 5% long-range, w~U[0,1)"
     if name == "er":
@@ -291,7 +294,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
-    ap.add_argument("--workload", default="rmat23", choices=["rmat23", "grid", "er"])
+    ap.add_argument("--workload", default="rmat23", choices=["rmat23", "rmat21", "grid", "er"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = _dist()

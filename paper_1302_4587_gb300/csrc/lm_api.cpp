@@ -159,9 +159,8 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t nr, uin
         c.add(&nw.vid[b], (size_t)nw.cap_r + 1);
     }
     c.add(&nw.tilemap, (size_t)nw.cap_t + 2);
-    c.add(&nw.lb_status, (size_t)nw.cap_t + 1);
-    c.add(&nw.lb_agg, (size_t)nw.cap_t + 1);
-    c.add(&nw.lb_incl, (size_t)nw.cap_t + 1);
+    c.add(&nw.lb_desc, 4 * ((size_t)nw.cap_t + 1));
+    c.add(&nw.lb_part, (size_t)nw.cap_t + 1);
     c.add(&nw.segs, (size_t)nw.cap_g);
     c.add(&nw.gvbase, (size_t)nw.cap_g + 1);
     c.add(&nw.grounds, (size_t)nw.cap_g);
@@ -183,8 +182,8 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t nr, uin
     nw.block = p;
     nw.bytes = c.total;
     e.ws = nw;
-    // look-back statuses start at generation 0, which no sweep uses
-    LM_CK(ctx, cudaMemsetAsync(e.ws.lb_status, 0, ((size_t)nw.cap_t + 1) * sizeof(uint32_t), e.stream));
+    // look-back descriptors start at generation 0, which no sweep uses
+    LM_CK(ctx, cudaMemsetAsync(e.ws.lb_desc, 0, 4 * ((size_t)nw.cap_t + 1) * sizeof(uint32_t), e.stream));
     return LM_OK;
 }
 
@@ -207,9 +206,8 @@ SweepArgs base_sweep_args(Engine& e, uint32_t nvert) {
     a.cnbr = w.cnbr;
     a.dead = w.dead;
     a.nvert = nvert;
-    a.lb_status = w.lb_status;
-    a.lb_agg = w.lb_agg;
-    a.lb_incl = w.lb_incl;
+    a.lb_desc = w.lb_desc;
+    a.lb_part = w.lb_part;
     a.lb_cap = w.cap_t + 1;
     a.st = e.st;
     a.out_cap = w.cap_e;

@@ -28,9 +28,8 @@ struct Workspace {
     uint32_t* off[2] = {nullptr, nullptr};   // [cap_r + 1] live row offsets
     uint32_t* vid[2] = {nullptr, nullptr};   // [cap_r] live row vertex ids
     uint32_t* tilemap = nullptr;     // [cap_t + 1] first row of each tile of the live entries
-    uint32_t* lb_status = nullptr;   // [cap_t] look-back status words
-    LbRec* lb_agg = nullptr;         // [cap_t] tile aggregates
-    LbRec* lb_incl = nullptr;        // [cap_t] inclusive prefixes
+    uint32_t* lb_desc = nullptr;     // [4 * cap_t] look-back descriptors
+    Part* lb_part = nullptr;         // [cap_t] partial row maxima per tile
     SegDesc* segs = nullptr;         // [cap_g] input segments of a sweep
     uint32_t* gvbase = nullptr;      // [cap_g + 1] first union vertex of each graph
     uint32_t* grounds = nullptr;     // [cap_g] rounds per graph

@@ -36,52 +36,58 @@ constexpr uint32_t ERR_INPUT = 4u;      // device-side input validation failed
 // rows (one row per live vertex); an entry "survives" when neither endpoint
 // was matched.  For a contiguous run X of entries:
 //   S   number of survivors in X
-//   h   X contains the first entry of some row
-//   hk  largest key among survivors of the head segment (entries of X before
-//       its first row start; all of X when !h); 0 = none.  hu = its neighbour.
-//   tk  largest key among survivors of the tail segment (from the last row
-//       start in X to its end); equals hk when !h.  tu = its neighbour.
-//   nr  rows that start inside X and already have a survivor inside X (each
-//       such row becomes one row of the compacted graph)
-// Keys of real edges are never 0 (the order maps every weight to a high half
-// >= 0x007FFFFF), so "k == 0" means "no survivor".
+//   H   X contains the first entry of some row
+//   HS  the head segment (entries of X before its first row start; all of X
+//       when !H) has a survivor
+//   TS  the tail segment (from the last row start in X to its end) has a
+//       survivor; equals HS when !H
+//   nr  rows that start inside X and have a survivor inside X (each such row
+//       becomes one row of the compacted graph)
 // combine(X, Y) describes X followed by Y; it is associative with identity
 // agg_identity().  The exclusive prefix of a tile is the combination of all
-// earlier tiles; since the first tile starts a row, a prefix has h = 1, its
-// S is the output position of the tile's first survivor, its nr the number
-// of compacted rows before the tile, and its tail (tk, tu) the running
-// maximum of the row that continues into the tile.
+// earlier tiles; the first tile starts a row, so a prefix has H set, its S is
+// the output position of the tile's first survivor, its nr the number of
+// compacted rows before the tile, and its TS says whether the row that
+// continues into the tile already has a survivor.
+constexpr uint32_t F_H = 1u, F_HS = 2u, F_TS = 4u;
+
 struct Agg {
-    uint64_t hk, tk;
-    uint32_t hu, tu;
-    uint32_t S, nr;
-    uint32_t h, pad;
+    uint32_t S, nr, f;
 };
 
 LM_HD Agg agg_identity() {
     Agg a;
-    a.hk = 0; a.tk = 0; a.hu = NIL; a.tu = NIL; a.S = 0; a.nr = 0; a.h = 0; a.pad = 0;
+    a.S = 0; a.nr = 0; a.f = 0;
     return a;
+}
+
+LM_HD Agg agg_combine(const Agg& X, const Agg& Y) {
+    const bool xh = (X.f & F_H) != 0, yh = (Y.f & F_H) != 0;
+    const bool xhs = (X.f & F_HS) != 0, yhs = (Y.f & F_HS) != 0;
+    const bool xts = (X.f & F_TS) != 0, yts = (Y.f & F_TS) != 0;
+    Agg r;
+    r.S = X.S + Y.S;
+    // Y's head continues X's tail row; if X has a row start, that row started
+    // inside X and gets its first survivor in Y exactly when X's tail had none.
+    r.nr = X.nr + Y.nr + ((xh && yhs && !xts) ? 1u : 0u);
+    const bool h = xh || yh;
+    const bool hs = xh ? xhs : (xhs || yhs);
+    const bool ts = yh ? yts : (xts || yhs);
+    r.f = (h ? F_H : 0u) | (hs ? F_HS : 0u) | (ts ? F_TS : 0u);
+    return r;
 }
 
 LM_HD void kv_max(uint64_t& k, uint32_t& u, uint64_t k2, uint32_t u2) {
     if (k2 > k) { k = k2; u = u2; }
 }
 
-LM_HD Agg agg_combine(const Agg& X, const Agg& Y) {
-    Agg r;
-    r.S = X.S + Y.S;
-    r.h = X.h | Y.h;
-    if (X.h) { r.hk = X.hk; r.hu = X.hu; }
-    else { r.hk = X.hk; r.hu = X.hu; kv_max(r.hk, r.hu, Y.hk, Y.hu); }
-    // Y's head continues X's tail row; if X has a row start, that row started
-    // inside X and gets its first survivor in Y exactly when X's tail had none.
-    r.nr = X.nr + Y.nr + ((X.h && Y.hk != 0 && X.tk == 0) ? 1u : 0u);
-    if (Y.h) { r.tk = Y.tk; r.tu = Y.tu; }
-    else { r.tk = X.tk; r.tu = X.tu; kv_max(r.tk, r.tu, Y.hk, Y.hu); }
-    r.pad = 0;
-    return r;
-}
+// Partial maxima of one tile, for rows cut by tile boundaries: the heaviest
+// surviving key (0 = none) and its neighbour in the head segment and in the
+// tail segment (tail = head when the tile has no row start).
+struct alignas(16) Part {
+    uint64_t hk, tk;
+    uint32_t hu, tu, pad0, pad1;
+};
 
 // ---------------------------------------------------------------------------
 // Device-side control block (one per context workspace).
@@ -96,12 +102,6 @@ struct DevState {
     unsigned long long matched2;  // matched vertices (= 2 |M|)
     uint64_t ring_m[64];      // live edges at the start of round r
     uint64_t ring_n[64];      // live rows at the start of round r
-};
-
-// Look-back record of one tile (32 bytes); h and the kind live in the status word.
-struct alignas(16) LbRec {
-    uint64_t hk, tk;
-    uint32_t hu, tu, S, nr;
 };
 
 // One input graph as a source segment of a sweep (the graph's own CSR).
@@ -141,11 +141,12 @@ struct SweepArgs {
     uint32_t* cnbr;           // [N] chosen neighbour of each vertex (written for the next round)
     const uint8_t* dead;      // [N] 1 = matched
     uint32_t nvert;           // N (bounds checks)
-    // look-back storage
-    uint32_t* lb_status;
-    LbRec* lb_agg;
-    LbRec* lb_incl;
-    uint32_t lb_cap;          // records available
+    // look-back storage: one 16-byte descriptor per tile {status, S, nr, flags}
+    // (status = generation << 2 | 1 aggregate / 2 inclusive prefix) and the
+    // tile's partial maxima
+    uint32_t* lb_desc;        // [lb_cap * 4]
+    Part* lb_part;            // [lb_cap]
+    uint32_t lb_cap;          // tiles that fit
     DevState* st;
 };
 

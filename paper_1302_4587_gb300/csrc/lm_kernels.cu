@@ -75,78 +75,116 @@ __device__ __forceinline__ void set_err(DevState* st, uint32_t bit, uint32_t inf
     if ((atomicOr(&st->err, bit) & bit) == 0) st->err_info = info;
 }
 
-// The wait for a predecessor tile is bounded: after LOOKBACK_LIMIT_NS the
-// sweep records ERR_TIMEOUT, uses an empty prefix and carries on (the host
-// reports LM_ETIMEOUT; every index stays checked, so nothing runs out of
-// bounds and the kernel ends).
+// The wait for a predecessor tile is bounded: after LOOKBACK_LIMIT_NS (or as
+// soon as any tile of the launch has given up) the sweep records ERR_TIMEOUT,
+// treats the missing tiles as empty and carries on; every index stays
+// checked, so nothing runs out of bounds and the kernel ends.
 constexpr uint64_t LOOKBACK_LIMIT_NS = 1000000000ull;
 
-__device__ __forceinline__ void publish(LbRec* rec, uint32_t* status, uint32_t t, const Agg& A,
-                                        uint32_t epoch, uint32_t kind) {
-    __stcg(reinterpret_cast<ulonglong2*>(&rec[t]), make_ulonglong2(A.hk, A.tk));
-    __stcg(reinterpret_cast<uint4*>(&rec[t]) + 1, make_uint4(A.hu, A.tu, A.S, A.nr));
-    __threadfence();
-    *reinterpret_cast<volatile uint32_t*>(&status[t]) = (epoch << 3) | ((A.h & 1u) << 2) | kind;
+__device__ __forceinline__ uint4 ld_volatile_v4(const uint32_t* p) {
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_volatile_v4(uint32_t* p, uint4 v) {
+    asm volatile("st.volatile.global.v4.u32 [%0], {%1,%2,%3,%4};"
+                 :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+// A tile's descriptor is one aligned 16-byte word written and read with
+// single vector accesses, so a reader sees either the aggregate or the
+// inclusive prefix, never a mix.
+__device__ __forceinline__ void publish_desc(uint32_t* desc, uint32_t t, uint32_t epoch, uint32_t kind, const Agg& A) {
+    st_volatile_v4(desc + 4 * (size_t)t, make_uint4((epoch << 2) | kind, A.S, A.nr, A.f));
 }
 
-__device__ __forceinline__ Agg read_rec(const LbRec* rec, uint32_t t, uint32_t h) {
-    const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(&rec[t]));
-    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(&rec[t]) + 1);
-    Agg r;
-    r.hk = a.x; r.tk = a.y; r.hu = b.x; r.tu = b.y; r.S = b.z; r.nr = b.w; r.h = h; r.pad = 0;
-    return r;
-}
+// Exclusive prefix of tile t >= 1, computed by one full warp; every lane
+// returns the same value.  A window covers LB_PER_LANE * 32 predecessors read
+// in one round trip: lane l watches tiles base - LB_PER_LANE*l - q.  Only the
+// tiles between this one and the nearest inclusive prefix are waited for; the
+// window is combined oldest first (inside a lane, then by an ordered tree
+// reduction over lanes).
+constexpr int LB_PER_LANE = 4;
 
-// Exclusive prefix of tile t (t >= 1), computed by one full warp.  The
-// result is valid in lane 0.
 __device__ Agg lookback(const SweepArgs& a, uint32_t t, uint32_t epoch, int lane, bool& timed_out) {
     Agg suf = agg_identity();
     int64_t base = (int64_t)t - 1;
     const uint64_t t_start = globaltimer_ns();
+    const uint4 empty_incl = make_uint4((epoch << 2) | 2u, 0u, 0u, F_H);  // below tile 0: an empty prefix
     for (;;) {
-        const int64_t k = base - lane;
-        uint32_t kind = 2, hbit = 1;
-        if (k >= 0) {
-            uint32_t s;
-            for (;;) {
-                s = ld_volatile_u32(&a.lb_status[k]);
-                if ((s >> 3) == epoch && (s & 3u) != 0) break;
-                if (globaltimer_ns() - t_start > LOOKBACK_LIMIT_NS ||
-                    (ld_volatile_u32(&a.st->err) & ERR_TIMEOUT)) {
+        uint4 d[LB_PER_LANE];
+        bool valid[LB_PER_LANE];
+#pragma unroll
+        for (int q = 0; q < LB_PER_LANE; q++) {
+            d[q] = empty_incl;
+            valid[q] = base - (int64_t)(LB_PER_LANE * lane + q) < 0;
+        }
+        uint32_t my_incl = LB_PER_LANE;  // nearest inclusive element inside this lane
+        for (int spins = 0;; spins++) {
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++) {
+                if (!valid[q]) {
+                    d[q] = ld_volatile_v4(a.lb_desc + 4 * (size_t)(base - (LB_PER_LANE * lane + q)));
+                    valid[q] = (d[q].x >> 2) == epoch && (d[q].x & 3u) != 0;
+                }
+            }
+            // this lane is ready when its elements up to its first inclusive one are valid
+            bool ready = true;
+            my_incl = LB_PER_LANE;
+#pragma unroll
+            for (int q = LB_PER_LANE - 1; q >= 0; q--)
+                if (valid[q] && (d[q].x & 3u) == 2u) my_incl = q;
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++)
+                if (q <= (int)my_incl && q < LB_PER_LANE && !valid[q]) ready = false;
+            const uint32_t imask = __ballot_sync(FULL, my_incl < LB_PER_LANE);
+            const uint32_t rmask = __ballot_sync(FULL, ready);
+            const uint32_t need = imask ? ((2u << (__ffs(imask) - 1)) - 1u) : FULL;  // lanes up to the first inclusive
+            if ((rmask & need) == need) break;
+            if (spins > 8) {
+                bool give_up = false;
+                if (lane == 0)
+                    give_up = globaltimer_ns() - t_start > LOOKBACK_LIMIT_NS || (ld_volatile_u32(&a.st->err) & ERR_TIMEOUT);
+                if (__shfl_sync(FULL, give_up, 0)) {
                     timed_out = true;
-                    s = (epoch << 3) | 4u | 2u;   // treat as an (empty) inclusive record
+#pragma unroll
+                    for (int q = 0; q < LB_PER_LANE; q++)
+                        if (!valid[q]) { d[q] = empty_incl; valid[q] = true; }
+                    my_incl = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(spins < 64 ? 32 : 256);
             }
-            kind = s & 3u;
-            hbit = (s >> 2) & 1u;
         }
-        const uint32_t incl = __ballot_sync(FULL, kind == 2);
-        const uint32_t hmask = __ballot_sync(FULL, hbit != 0);
-        const bool any_to = __any_sync(FULL, timed_out);
-        __threadfence();
-        Agg res = suf;
-        if (incl) {
-            if (lane == 0) {
-                const int j = __ffs(incl) - 1;
-                const int64_t k0 = base - j;
-                Agg acc = (k0 >= 0 && !any_to) ? read_rec(a.lb_incl, (uint32_t)k0, 1u) : agg_identity();
-                if (any_to) acc.h = 1;
-                for (int l = j - 1; l >= 0; l--)
-                    acc = agg_combine(acc, read_rec(a.lb_agg, (uint32_t)(base - l), (hmask >> l) & 1u));
-                res = agg_combine(acc, suf);
+        const uint32_t imask = __ballot_sync(FULL, my_incl < LB_PER_LANE);
+        const int jl = imask ? __ffs(imask) - 1 : 32;
+        // combine this lane's elements oldest first, cut at the nearest inclusive one
+        Agg v = agg_identity();
+        if (lane <= jl) {
+            const int qmax = (lane == jl) ? (int)my_incl : LB_PER_LANE - 1;
+#pragma unroll
+            for (int q = LB_PER_LANE - 1; q >= 0; q--) {
+                if (q <= qmax) {
+                    Agg x;
+                    x.S = d[q].y; x.nr = d[q].z; x.f = d[q].w;
+                    v = agg_combine(v, x);
+                }
             }
-            if (any_to) timed_out = true;
-            return res;
         }
-        if (lane == 0) {
-            Agg acc = agg_identity();
-            for (int l = 31; l >= 0; l--)
-                acc = agg_combine(acc, read_rec(a.lb_agg, (uint32_t)(base - l), (hmask >> l) & 1u));
-            suf = agg_combine(acc, suf);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            Agg w;
+            w.S = __shfl_down_sync(FULL, v.S, o);
+            w.nr = __shfl_down_sync(FULL, v.nr, o);
+            w.f = __shfl_down_sync(FULL, v.f, o);
+            if (lane + o < 32) v = agg_combine(w, v);
         }
-        base -= 32;
+        v.S = __shfl_sync(FULL, v.S, 0);
+        v.nr = __shfl_sync(FULL, v.nr, 0);
+        v.f = __shfl_sync(FULL, v.f, 0);
+        suf = agg_combine(v, suf);
+        if (imask) return suf;
+        base -= 32 * LB_PER_LANE;
     }
 }
 
@@ -163,7 +201,9 @@ struct SweepSmem {
     uint32_t scanS[SWEEP_WARPS], scanE[SWEEP_WARPS];
     Agg pre;                         // exclusive prefix of the tile
     Agg tot;                         // aggregate of the tile
-    uint32_t tile, j0, nent, r_lo, nload, nrt, b0, seg;
+    uint64_t hk_fin;                 // head row: maximum over earlier tiles (0 = none)
+    uint32_t hu_fin;
+    uint32_t tile, j0, nent, r_lo, nload, nrt, b0, seg, tile_begin;
     uint32_t vbase, k0, k1, last, bad;
     uint8_t rdead[SWEEP_T + 4];      // per local row: vertex matched this round
 };
@@ -193,14 +233,15 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
         }
         return;
     }
-    const uint32_t epoch = ld_volatile_u32(&st->epoch) & 0x1FFFFFFFu;
-    if (ntiles + 1 > a.lb_cap) {
+    const uint32_t epoch = ld_volatile_u32(&st->epoch) & 0x3FFFFFFFu;
+    if (ntiles > a.lb_cap) {
         if (blockIdx.x == 0 && tid == 0) set_err(st, ERR_BOUNDS, ntiles);
         return;  // no tile is processed, so no look-back record is awaited
     }
 
     for (;;) {
         // ------------------------------------------------ locate the tile
+        // (ids are taken when a tile starts, so every earlier tile has started)
         if (tid == 0) {
             const uint32_t t = atomicAdd(&st->tile_ctr, 1u);
             s.tile = t;
@@ -215,6 +256,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
                     }
                     const SegDesc& sg = a.segs[lo];
                     s.seg = lo;
+                    s.tile_begin = sg.tile_begin;
                     lt = t - sg.tile_begin;
                     tm = sg.tilemap;
                     nrows_seg = sg.nrows;
@@ -224,7 +266,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
                     tm = a.in_tilemap;
                     nrows_seg = live_rows;
                     nent_seg = live_ent;
-                    s.seg = 0; s.vbase = 0; s.k0 = 0; s.k1 = 0;
+                    s.seg = 0; s.tile_begin = 0; s.vbase = 0; s.k0 = 0; s.k1 = 0;
                 }
                 const uint32_t j0 = lt * SWEEP_T;
                 uint32_t nent = min((uint32_t)SWEEP_T, nent_seg - j0);
@@ -404,14 +446,19 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
             if (tid == 0) { s.tot.S = TS; s.tot.nr = TE; }
         }
         if (tid == 0) {
+            // aggregate flags and partial maxima of the tile
             Agg& A = s.tot;
             if (!COMPACT) { A.S = 0; A.nr = 0; }
-            A.h = (b0 || nrt > 1) ? 1u : 0u;
-            if (!b0) { A.hk = s.kmax[0]; A.hu = s.knbr[0]; } else { A.hk = 0; A.hu = NIL; }
-            if (A.h && nrt > 0) { A.tk = s.kmax[nrt - 1]; A.tu = s.knbr[nrt - 1]; }
-            else if (A.h) { A.tk = 0; A.tu = NIL; }
-            else { A.tk = A.hk; A.tu = A.hu; }
-            A.pad = 0;
+            const bool h = b0 || nrt > 1;
+            Part P;
+            P.pad0 = P.pad1 = 0;
+            if (!b0 && nrt > 0) { P.hk = s.kmax[0]; P.hu = s.knbr[0]; } else { P.hk = 0; P.hu = NIL; }
+            if (h && nrt > 0) { P.tk = s.kmax[nrt - 1]; P.tu = s.knbr[nrt - 1]; }
+            else if (h) { P.tk = 0; P.tu = NIL; }
+            else { P.tk = P.hk; P.tu = P.hu; }
+            A.f = (h ? F_H : 0u) | (P.hk ? F_HS : 0u) | (P.tk ? F_TS : 0u);
+            __stcg(reinterpret_cast<ulonglong2*>(&a.lb_part[t]), make_ulonglong2(P.hk, P.tk));
+            __stcg(reinterpret_cast<uint4*>(&a.lb_part[t]) + 1, make_uint4(P.hu, P.tu, 0u, 0u));
         }
         __syncthreads();
 
@@ -421,20 +468,25 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
             Agg P = agg_identity();
             bool to = false;
             if (t == 0) {
-                P.h = 1;
+                P.f = F_H;
                 if (a.prefix_in) {
                     P.S = ld_volatile_u32(&a.prefix_in[0]);
                     P.nr = ld_volatile_u32(&a.prefix_in[1]);
                 }
             } else {
-                if (lane == 0) publish(a.lb_agg, a.lb_status, t, A, epoch, 1u);
+                if (lane == 0) {
+                    __threadfence();  // partial maxima before the aggregate
+                    publish_desc(a.lb_desc, t, epoch, 1u, A);
+                }
                 P = lookback(a, t, epoch, lane, to);
+                to = __any_sync(FULL, to);
             }
+            Agg I = agg_combine(P, A);
+            I.f = F_H | (I.f & F_TS);
             if (lane == 0) {
                 if (to) set_err(st, ERR_TIMEOUT, t);
-                Agg I = agg_combine(P, A);
-                I.h = 1;
-                publish(a.lb_incl, a.lb_status, t, I, epoch, 2u);
+                if (t == 0) __threadfence();
+                publish_desc(a.lb_desc, t, epoch, 2u, I);
                 s.pre = P;
                 if (COMPACT && s.last) {
                     // totals of the sweep: sentinel offset and the next round's counts
@@ -451,6 +503,31 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
                     if (S_tot == 0) st->rounds = rn;
                 }
             }
+            // head row continuing from earlier tiles: gather its maximum from their
+            // partials (all earlier tiles have published them: the look-back saw
+            // every one of them at least as an aggregate)
+            const bool need_head = !bad && !b0 && nrt > 0 && (nrt > 1 || s.off[nrt] == j0 + nent);
+            uint64_t hk = 0;
+            uint32_t hu = NIL;
+            if (need_head) {
+                __threadfence();
+                const uint32_t gt_start = s.tile_begin + s.off[0] / SWEEP_T;  // tile where the row starts
+                for (uint32_t k = gt_start + lane; k < t; k += 32) {
+                    const Part* pp = &a.lb_part[k];
+                    const ulonglong2 kk = __ldcg(reinterpret_cast<const ulonglong2*>(pp));
+                    const uint4 uu = __ldcg(reinterpret_cast<const uint4*>(pp) + 1);
+                    // the start tile contributes its tail, the tiles after it their whole (head) part
+                    if (k == gt_start) kv_max(hk, hu, kk.y, uu.y);
+                    else kv_max(hk, hu, kk.x, uu.x);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t k2 = __shfl_xor_sync(FULL, hk, o);
+                    const uint32_t u2 = __shfl_xor_sync(FULL, hu, o);
+                    kv_max(hk, hu, k2, u2);
+                }
+            }
+            if (lane == 0) { s.hk_fin = hk; s.hu_fin = hu; }
         }
         __syncthreads();
         const Agg P = s.pre;
@@ -477,7 +554,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
         // ------------------------------------------------ rows: compacted rows, next candidates
         {
             const bool head_cont = (b0 == 0);
-            const bool head_new = COMPACT && head_cont && s.cnt[0] > 0 && P.tk == 0;
+            const bool prev_surv = (P.f & F_TS) != 0;
+            const bool head_new = COMPACT && head_cont && s.cnt[0] > 0 && !prev_surv;
             uint32_t posr = P.S + oS;
             uint32_t idx = P.nr + (head_new ? 1u : 0u) + oE;
             const bool last_ends = (s.off[nrt] == j0 + nent);
@@ -501,7 +579,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
                 if (!bad && (r + 1 < nrt || last_ends)) {
                     uint64_t k = s.kmax[r];
                     uint32_t u = s.knbr[r];
-                    if (is_head) kv_max(k, u, P.tk, P.tu);
+                    if (is_head) kv_max(k, u, s.hk_fin, s.hu_fin);
                     if (k != 0) a.cnbr[s.vid[r]] = u;
                 }
             }
@@ -517,7 +595,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
         if (done == gridDim.x - 1) {
             st->tile_ctr = 0;
             st->exit_ctr = 0;
-            uint32_t e = (st->epoch + 1) & 0x1FFFFFFFu;
+            uint32_t e = (st->epoch + 1) & 0x3FFFFFFFu;
             st->epoch = e ? e : 1u;
             __threadfence();
         }
