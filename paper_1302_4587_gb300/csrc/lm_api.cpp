@@ -94,23 +94,17 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-SegDesc seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t tile_begin) {
-    SegDesc d;
+SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase) {
+    SegIn d;
     memset(&d, 0, sizeof d);
     const uint64_t z = splitmix64_first(seed);
-    d.off = g->off;
-    d.vid = g->vid;
     d.nbr = g->nbr;
     d.eid = g->eid;
     d.ordw = g->ordw;
-    d.tilemap = g->tilemap;
-    d.nrows = g->nrows;
-    d.nent = g->nent;
+    d.ebase = ebase;
     d.vbase = vbase;
     d.k0 = (uint32_t)z;
     d.k1 = (uint32_t)(z >> 32);
-    d.tile_begin = tile_begin;
-    d.ntiles = g->ntiles;
     return d;
 }
 
@@ -120,10 +114,9 @@ int engine_init(lm_ctx* ctx, Engine& e, cudaStream_t stream) {
     LM_CK(ctx, cudaMalloc(&e.st, sizeof(DevState)));
     LM_CK(ctx, cudaMallocHost(&e.st_host, sizeof(DevState)));
     memset(e.st_host, 0, sizeof(DevState));
-    e.st_host->epoch = 1;  // look-back records of generation 0 never count
     LM_CK(ctx, cudaMemcpy(e.st, e.st_host, sizeof(DevState), cudaMemcpyHostToDevice));
-    e.sweep_grid = sweep_grid(ctx->device);
-    e.vertex_grid = vertex_grid(ctx->device);
+    e.sweep_grid = 0;
+    e.vertex_grid = 0;
     return LM_OK;
 }
 
@@ -138,35 +131,44 @@ void engine_free(Engine& e) {
     e = Engine();
 }
 
-int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t nr, uint32_t nt, uint32_t ng) {
+int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     Workspace& w = e.ws;
-    if (w.block && nv <= w.cap_v && ne <= w.cap_e && nr <= w.cap_r && nt <= w.cap_t && ng <= w.cap_g) return LM_OK;
+    const uint32_t nc = chunks_cap(ne);
+    if (w.block && nv <= w.cap_v && ne <= w.cap_e && nc <= w.cap_c && ng <= w.cap_g) return LM_OK;
     LM_CK(ctx, cudaStreamSynchronize(e.stream));
     Workspace nw;
     nw.cap_v = std::max(nv, w.cap_v);
     nw.cap_e = std::max(ne, w.cap_e);
-    nw.cap_r = std::max(nr, w.cap_r);
-    nw.cap_t = std::max(nt, w.cap_t);
+    nw.cap_c = std::max(nc, w.cap_c);
     nw.cap_g = std::max(std::max(ng, w.cap_g), 1u);
+    const size_t V = (size_t)nw.cap_v + 1, E = (size_t)nw.cap_e + 4, C = nw.cap_c, G = nw.cap_g;
     Carver c;
-    c.add(&nw.cnbr, (size_t)nw.cap_v + 1);
-    c.add(&nw.dead, (size_t)nw.cap_v + 1);
-    c.add(&nw.mate, (size_t)nw.cap_v + 1);
-    for (int b = 0; b < 2; b++) {
-        c.add(&nw.key[b], (size_t)nw.cap_e + 4);
-        c.add(&nw.nbr[b], (size_t)nw.cap_e + 4);
-        c.add(&nw.off[b], (size_t)nw.cap_r + 2);
-        c.add(&nw.vid[b], (size_t)nw.cap_r + 1);
+    c.add(&nw.start, V);
+    c.add(&nw.gid, V);
+    c.add(&nw.len[0], V);
+    c.add(&nw.len[1], V);
+    c.add(&nw.cnbr, V);
+    c.add(&nw.dead, V);
+    c.add(&nw.mate, V);
+    c.add(&nw.bcnt, V);
+    for (int k = 0; k < 4; k++) {
+        c.add(&nw.T[k], V);
+        c.add(&nw.M[k], V);
+        c.add(&nw.C[k], C);
     }
-    c.add(&nw.tilemap, (size_t)nw.cap_t + 2);
-    c.add(&nw.lb_desc, 4 * ((size_t)nw.cap_t + 1));
-    c.add(&nw.lb_part, (size_t)nw.cap_t + 1);
-    c.add(&nw.segs, (size_t)nw.cap_g);
-    c.add(&nw.gvbase, (size_t)nw.cap_g + 1);
-    c.add(&nw.grounds, (size_t)nw.cap_g);
-    c.add(&nw.gdst, (size_t)nw.cap_g);
-    c.add(&nw.gmatched, (size_t)nw.cap_g);
-    c.add(&nw.rows_per, (size_t)nw.cap_g);
+    c.add(&nw.part, C);
+    for (int b = 0; b < 2; b++) {
+        c.add(&nw.key[b], E);
+        c.add(&nw.nbr[b], E);
+    }
+    c.add(&nw.segs, G);
+    c.add(&nw.gvbase, G + 1);
+    c.add(&nw.gebase, G);
+    c.add(&nw.goff, G);
+    c.add(&nw.grounds, G);
+    c.add(&nw.glive, G);
+    c.add(&nw.gdst, G);
+    c.add(&nw.gmatched, G);
     if (w.block) {
         cudaFree(w.block);
         w.block = nullptr;
@@ -182,8 +184,8 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t nr, uin
     nw.block = p;
     nw.bytes = c.total;
     e.ws = nw;
-    // look-back descriptors start at generation 0, which no sweep uses
-    LM_CK(ctx, cudaMemsetAsync(e.ws.lb_desc, 0, 4 * ((size_t)nw.cap_t + 1) * sizeof(uint32_t), e.stream));
+    // finished-chunk counters start at zero (every sweep leaves them at zero)
+    LM_CK(ctx, cudaMemsetAsync(e.ws.bcnt, 0, V * sizeof(uint32_t), e.stream));
     return LM_OK;
 }
 
@@ -199,178 +201,154 @@ int ensure_pinned(lm_ctx* ctx, Engine& e, size_t bytes) {
     return LM_OK;
 }
 
-SweepArgs base_sweep_args(Engine& e, uint32_t nvert) {
-    SweepArgs a;
-    memset(&a, 0, sizeof a);
-    Workspace& w = e.ws;
-    a.cnbr = w.cnbr;
-    a.dead = w.dead;
-    a.nvert = nvert;
-    a.lb_desc = w.lb_desc;
-    a.lb_part = w.lb_part;
-    a.lb_cap = w.cap_t + 1;
-    a.st = e.st;
-    a.out_cap = w.cap_e;
-    a.out_rows_cap = w.cap_r;
-    return a;
+Lists lists_of(Engine& e, int k) {
+    Lists l;
+    l.T = e.ws.T[k];
+    l.M = e.ws.M[k];
+    l.C = e.ws.C[k];
+    l.capT = e.ws.cap_v;
+    l.capM = e.ws.cap_v;
+    l.capC = e.ws.cap_c;
+    l.cnt = &e.st->lcnt[k][0];
+    return l;
 }
 
-VertexArgs base_vertex_args(Engine& e, uint32_t nvert, uint32_t* mate) {
-    VertexArgs v;
-    memset(&v, 0, sizeof v);
-    v.nvert = nvert;
-    v.cnbr = e.ws.cnbr;
-    v.dead = e.ws.dead;
-    v.mate = mate;
-    v.tilemap = e.ws.tilemap;
-    v.tilemap_cap = e.ws.cap_t + 2;
-    v.st = e.st;
-    return v;
+VertexArrays vertex_arrays(Engine& e, uint32_t nvert, const uint32_t* start, bool with_gid, uint32_t* mate) {
+    VertexArrays va;
+    va.start = start ? start : e.ws.start;
+    va.len[0] = e.ws.len[0];
+    va.len[1] = e.ws.len[1];
+    va.cnbr = e.ws.cnbr;
+    va.dead = e.ws.dead;
+    va.mate = mate;
+    va.bcnt = e.ws.bcnt;
+    va.gid = with_gid ? e.ws.gid : nullptr;
+    va.nvert = nvert;
+    return va;
 }
 
-}  // namespace lm
-
-// ============================================================ the round loop
-namespace {
-
-// Per-kernel CUDA-event timing of one call (LM_F_PROFILE).
-struct Prof {
-    lm_ctx* ctx;
-    cudaStream_t s;
-    bool on;
-    int kind[MAX_PROFILE_EVENTS / 2];
-    int n = 0;
-    uint32_t launches[LM_K_COUNT] = {0, 0, 0, 0, 0};
-    Prof(lm_ctx* c, cudaStream_t st) : ctx(c), s(st), on((c->flags & LM_F_PROFILE) && c->ev_ready) {}
-    void begin(int k) {
-        launches[k]++;
-        if (!on || n >= MAX_PROFILE_EVENTS / 2) return;
-        kind[n] = k;
-        cudaEventRecord(ctx->ev[2 * n], s);
+Prof::Prof(lm_ctx* c, cudaStream_t st) : ctx(c), s(st), on(c && (c->flags & LM_F_PROFILE) && c->ev_ready) {}
+void Prof::begin(int k) {
+    launches[k]++;
+    if (!on || n >= MAX_PROFILE_EVENTS / 2) return;
+    kind[n] = k;
+    cudaEventRecord(ctx->ev[2 * n], s);
+}
+void Prof::end() {
+    if (!on || n >= MAX_PROFILE_EVENTS / 2) return;
+    cudaEventRecord(ctx->ev[2 * n + 1], s);
+    n++;
+}
+void Prof::fill(lm_stats* st) {
+    uint32_t tot = 0;
+    for (int k = 0; k < LM_K_COUNT; k++) {
+        st->kernel_launches[k] = launches[k];
+        tot += launches[k];
     }
-    void end() {
-        if (!on || n >= MAX_PROFILE_EVENTS / 2) return;
-        cudaEventRecord(ctx->ev[2 * n + 1], s);
-        n++;
-    }
-    void fill(lm_stats* st) {
-        uint32_t tot = 0;
-        for (int k = 0; k < LM_K_COUNT; k++) {
-            st->kernel_launches[k] = launches[k];
-            tot += launches[k];
-        }
-        st->launches = tot;
-        if (!on || n == 0) return;
-        for (int i = 0; i < n; i++) {
-            float ms = 0;
-            if (cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]) == cudaSuccess) st->kernel_ms[kind[i]] += ms;
-        }
+    st->launches = tot;
+    if (!on || n == 0) return;
+    for (int i = 0; i < n; i++) {
         float ms = 0;
-        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2 * n - 1]) == cudaSuccess) st->total_ms = ms;
-        cudaGetLastError();
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]) == cudaSuccess) st->kernel_ms[kind[i]] += ms;
     }
-};
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2 * n - 1]) == cudaSuccess) st->total_ms = ms;
+    cudaGetLastError();
+}
 
-// A set of input graphs (segments) over one union vertex space.
-struct Job {
-    std::vector<SegDesc> segs;       // non-empty graphs only
-    uint32_t nvert = 0;              // union vertices
-    uint32_t nent = 0, ntiles = 0;
-    uint32_t* mate = nullptr;        // union result (device)
-    const uint32_t* gvbase = nullptr;
-    uint32_t ngraphs = 0;
-    uint32_t* grounds = nullptr;
-};
-
-int check_err(lm_ctx* ctx, Engine& e) {
+static int check_err(lm_ctx* ctx, Engine& e) {
     const uint32_t err = e.st_host->err;
     if (err & ERR_BOUNDS) return fail(ctx, LM_ECUDA, "device index check failed (index %u)", e.st_host->err_info);
-    if (err & ERR_TIMEOUT) return fail(ctx, LM_ETIMEOUT, "look-back wait timed out at tile %u", e.st_host->err_info);
+    if (err & ERR_TIMEOUT) return fail(ctx, LM_ETIMEOUT, "a bounded device wait gave up (%u)", e.st_host->err_info);
     return LM_OK;
 }
 
-// Whole local-max loop for `job`: result in job.mate, DevState mirror refreshed.
+// The local-max loop.  Expects: the segment table in e.ws.segs, the vertex
+// state initialised (launch_init with the DevState), and for batches the
+// union arrays (start, gid, len[0]) set up.  Round r's vertex pass reads list
+// set r & 1 and fills set (r + 1) & 1, which round r's sweep consumes; the
+// live entries alternate between buffers 1 and 0 (round 0 reads the graphs'
+// own arrays).  The host reads the device's "done" flag between chunks of
+// rounds.
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     Workspace& w = e.ws;
     cudaStream_t s = e.stream;
-    if (!job.segs.empty()) {
-        int rc = ensure_pinned(ctx, e, job.segs.size() * sizeof(SegDesc));
-        if (rc) return rc;
-        memcpy(e.pinned, job.segs.data(), job.segs.size() * sizeof(SegDesc));
-        LM_CK(ctx, cudaMemcpyAsync(w.segs, e.pinned, job.segs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice, s));
-    }
-    prof.begin(LM_K_INIT);
-    LM_CK(ctx, launch_init(s, job.mate, w.cnbr, w.dead, job.nvert, e.st));
-    prof.end();
-
-    if (job.nent > 0) {
-        SweepArgs a = base_sweep_args(e, job.nvert);
-        a.segs = w.segs;
-        a.nsegs = (uint32_t)job.segs.size();
-        a.ntiles_in = job.ntiles;
-        a.round = 0;
-        // round 0, step 2 (Sec. 2): candidates from the graphs' own adjacency arrays
-        prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_input_cand(s, a, e.sweep_grid));
-        prof.end();
-        // round 0, step 3: mutual choice
-        VertexArgs va = base_vertex_args(e, job.nvert, job.mate);
-        va.vbegin = 0;
-        va.vcount = job.nvert;
-        va.gvbase = job.gvbase;
-        va.ngraphs = job.ngraphs;
-        va.grounds = job.grounds;
-        va.round = 0;
+    if (job.nseg > 0) {
+        // round 0 -- file every row, candidate-only sweep over the input
+        VertexArgs pre;
+        memset(&pre, 0, sizeof pre);
+        pre.va = job.va;
+        pre.in = lists_of(e, 0);
+        pre.in.cnt = nullptr;
+        pre.in_set = 4;
+        pre.vlist = job.vlist;
+        pre.nvlist = job.nvlist;
+        pre.deg0 = job.rdeg;
+        pre.out = lists_of(e, 0);
+        pre.out_set = 0;
+        pre.par = 0;
+        pre.match = 0;
+        pre.st = e.st;
         prof.begin(LM_K_VERTEX);
-        LM_CK(ctx, launch_vertex_all(s, va, e.vertex_grid));
+        LM_CK(ctx, launch_vertex(s, pre));
         prof.end();
-        // round 0, steps 4-6, fused with step 2 of round 1
-        a.out_key = w.key[1];
-        a.out_nbr = w.nbr[1];
-        a.out_off = w.off[1];
-        a.out_vid = w.vid[1];
-        a.out_buf = 1;
+        SweepArgs sw;
+        memset(&sw, 0, sizeof sw);
+        sw.va = job.va;
+        sw.in = lists_of(e, 0);
+        sw.par = 0;
+        sw.segs = w.segs;
+        sw.ecap = job.ecap;
+        sw.part = w.part;
+        sw.st = e.st;
         prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_input_compact(s, a, e.sweep_grid));
+        LM_CK(ctx, launch_sweep_cand(s, sw));
         prof.end();
 
-        // rounds >= 1 in chunks; the live edge count is read back between chunks
-        uint32_t r = 1, chunk = 4;
+        uint32_t r = 0, chunk = 4;
         for (;;) {
             for (uint32_t k = 0; k < chunk; k++, r++) {
-                const uint32_t b = r & 1u;
-                VertexArgs vl = base_vertex_args(e, job.nvert, job.mate);
-                vl.off = w.off[b];
-                vl.vid = w.vid[b];
-                vl.in_buf = b;
-                vl.round = r;
-                vl.gvbase = job.gvbase;
-                vl.ngraphs = job.ngraphs;
-                vl.grounds = job.grounds;
+                const uint32_t par = r & 1u;
+                VertexArgs v;
+                memset(&v, 0, sizeof v);
+                v.va = job.va;
+                v.in = lists_of(e, par);
+                v.in_set = par;
+                v.out = lists_of(e, par ^ 1u);
+                v.out_set = par ^ 1u;
+                v.par = par;
+                v.round = r;
+                v.match = 1;
+                v.grounds = job.grounds;
+                v.st = e.st;
                 prof.begin(LM_K_VERTEX);
-                LM_CK(ctx, launch_vertex_live(s, vl, e.vertex_grid));
+                LM_CK(ctx, launch_vertex(s, v));
                 prof.end();
-                SweepArgs l = base_sweep_args(e, job.nvert);
-                l.in_key = w.key[b];
-                l.in_nbr = w.nbr[b];
-                l.in_off = w.off[b];
-                l.in_vid = w.vid[b];
-                l.in_tilemap = w.tilemap;
-                l.in_buf = b;
-                l.out_key = w.key[b ^ 1u];
-                l.out_nbr = w.nbr[b ^ 1u];
-                l.out_off = w.off[b ^ 1u];
-                l.out_vid = w.vid[b ^ 1u];
-                l.out_buf = b ^ 1u;
-                l.round = r;
+                SweepArgs c;
+                memset(&c, 0, sizeof c);
+                c.va = job.va;
+                c.in = lists_of(e, par ^ 1u);
+                c.in_set = par ^ 1u;
+                c.par = par;
+                c.out_key = w.key[par ^ 1u];
+                c.out_nbr = w.nbr[par ^ 1u];
+                c.ecap = job.ecap;
+                c.part = w.part;
+                c.st = e.st;
                 prof.begin(LM_K_SWEEP);
-                LM_CK(ctx, launch_sweep_live(s, l, e.sweep_grid));
+                if (r == 0) {
+                    c.segs = w.segs;
+                    LM_CK(ctx, launch_sweep_input(s, c));
+                } else {
+                    c.in_key = w.key[par];
+                    c.in_nbr = w.nbr[par];
+                    LM_CK(ctx, launch_sweep_live(s, c));
+                }
                 prof.end();
             }
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             LM_CK(ctx, cudaStreamSynchronize(s));
-            if (e.st_host->err) break;
-            if (e.st_host->cnt[r & 1u][0] == 0) break;
+            if (e.st_host->err || e.st_host->done) break;
             chunk = std::min<uint32_t>(chunk * 2, 64);
         }
     }
@@ -379,15 +357,17 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     return check_err(ctx, e);
 }
 
-void fill_round_stats(const DevState& d, lm_stats* st, uint64_t m0, uint64_t n0) {
+}  // namespace lm
+
+namespace {
+
+void fill_round_stats(const DevState& d, lm_stats* st) {
     st->rounds = d.rounds;
     st->matched = d.matched2 / 2;
     for (int i = 0; i < LM_STATS_ROUNDS; i++) {
         st->round_m[i] = d.ring_m[i];
         st->round_n[i] = d.ring_n[i];
     }
-    st->round_m[0] = m0;
-    st->round_n[0] = n0;
 }
 
 }  // namespace
@@ -475,7 +455,6 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     g->n = n;
     g->m = m;
     g->nent = 2 * m;
-    g->ntiles = tiles_of(g->nent);
 
     const uint32_t* d_eu = eu;
     const uint32_t* d_ev = ev;
@@ -483,7 +462,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     const size_t nn = (size_t)n + 1;
     const size_t scan_words = exclusive_scan_tmp_words(n + 1);
     Carver tc;
-    uint32_t *t_eu = nullptr, *t_ev = nullptr, *deg = nullptr, *offall = nullptr, *cursor = nullptr;
+    uint32_t *t_eu = nullptr, *t_ev = nullptr, *deg = nullptr, *cursor = nullptr;
     uint32_t *flags = nullptr, *rowidx = nullptr, *scan_tmp = nullptr, *err = nullptr;
     float* t_w = nullptr;
     if (mem == LM_HOST && m > 0) {
@@ -492,7 +471,6 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
         tc.add(&t_w, m);
     }
     tc.add(&deg, nn);
-    tc.add(&offall, nn);
     tc.add(&cursor, nn);
     tc.add(&flags, nn);
     tc.add(&rowidx, nn);
@@ -519,35 +497,34 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     LM_CK(ctx, cudaMemsetAsync(err, 0, 16, s));
     // validation rides on the degree count: endpoint < n, no self loop, no NaN
     if (m > 0) LM_CK(ctx, launch_build_degrees(s, d_eu, d_ev, d_w, n, m, deg, err));
-    LM_CK(ctx, launch_exclusive_scan(s, deg, offall, n + 1, scan_tmp, scan_words));
-    LM_CK(ctx, launch_nonzero_flags(s, deg, n + 1, flags));
-    LM_CK(ctx, launch_exclusive_scan(s, flags, rowidx, n + 1, scan_tmp, scan_words));
     int rc = ensure_pinned(ctx, e, 64);
     if (rc) return rc;
     uint32_t* hp = static_cast<uint32_t*>(e.pinned);
-    LM_CK(ctx, cudaMemcpyAsync(&hp[0], rowidx + n, 4, cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaMemcpyAsync(&hp[1], err, 4, cudaMemcpyDeviceToHost, s));
+    LM_CK(ctx, launch_nonzero_flags(s, deg, n + 1, flags));
+    LM_CK(ctx, launch_exclusive_scan(s, flags, rowidx, n + 1, scan_tmp, scan_words));
+    LM_CK(ctx, cudaMemcpyAsync(&hp[0], rowidx + n, 4, cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaStreamSynchronize(s));
     if (hp[1]) return fail(ctx, LM_EINVAL, "edge list: endpoint >= n, self loop or NaN weight");
     g->nrows = hp[0];
 
     Carver gc;
-    gc.add(&g->off, (size_t)g->nrows + 1);
+    gc.add(&g->off, nn);
     gc.add(&g->vid, (size_t)g->nrows + 1);
+    gc.add(&g->rdeg, (size_t)g->nrows + 1);
     gc.add(&g->nbr, (size_t)g->nent + 4);
     gc.add(&g->eid, (size_t)g->nent + 4);
     gc.add(&g->ordw, (size_t)g->nent + 4);
-    gc.add(&g->tilemap, (size_t)g->ntiles + 2);
     ce = cudaMalloc(&g->block, gc.total);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
     gc.assign(g->block);
     g->bytes = gc.total;
+    LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
     if (m > 0) {
-        LM_CK(ctx, cudaMemcpyAsync(cursor, offall, nn * 4, cudaMemcpyDeviceToDevice, s));
-        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, offall, cursor, g->nbr, g->eid, g->ordw));
+        LM_CK(ctx, cudaMemcpyAsync(cursor, g->off, nn * 4, cudaMemcpyDeviceToDevice, s));
+        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->eid, g->ordw));
     }
-    LM_CK(ctx, launch_build_rows(s, deg, rowidx, offall, n, g->nrows, g->nent, g->off, g->vid));
-    if (g->nrows > 0) LM_CK(ctx, launch_build_tilemap(s, g->off, g->nrows, g->nent, g->tilemap));
+    LM_CK(ctx, launch_build_rows(s, deg, rowidx, n, g->vid, g->rdeg));
     LM_CK(ctx, cudaStreamSynchronize(s));
     *out = g.release();
     return LM_OK;
@@ -580,25 +557,38 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     DevGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
     Engine& e = ctx->eng;
+    cudaStream_t s = e.stream;
     if (stats) memset(stats, 0, sizeof *stats);
     const bool dev_out = is_device_ptr(mate);
-    int rc = ensure_ws(ctx, e, g->n, g->nent, g->nrows, g->ntiles + 1, 1);
+    int rc = ensure_ws(ctx, e, g->n, g->nent, 1);
+    if (rc) return rc;
+    rc = ensure_pinned(ctx, e, sizeof(SegIn));
     if (rc) return rc;
     Job job;
-    job.nvert = g->n;
-    job.nent = g->nent;
-    job.ntiles = g->ntiles;
-    job.mate = dev_out ? mate : e.ws.mate;
-    if (g->nent > 0) job.segs.push_back(seg_of(g, seed, 0, 0));
-    Prof prof(ctx, e.stream);
+    uint32_t* mate_d = dev_out ? mate : e.ws.mate;
+    job.va = vertex_arrays(e, g->n, g->off, false, mate_d);
+    job.ecap = g->nent;
+    job.vlist = g->vid;
+    job.rdeg = g->rdeg;
+    job.nvlist = g->nrows;
+    job.nseg = g->nent > 0 ? 1 : 0;
+    if (job.nseg) {
+        const SegIn sg = seg_of(g, seed, 0, 0);
+        memcpy(e.pinned, &sg, sizeof sg);
+        LM_CK(ctx, cudaMemcpyAsync(e.ws.segs, e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
+    }
+    Prof prof(ctx, s);
+    prof.begin(LM_K_INIT);
+    LM_CK(ctx, launch_init(s, mate_d, e.ws.dead, e.ws.bcnt, g->n, e.st));
+    prof.end();
     rc = run_job(ctx, e, job, prof);
     if (rc) return rc;
     if (!dev_out && g->n > 0) {
-        LM_CK(ctx, cudaMemcpyAsync(mate, job.mate, (size_t)g->n * 4, cudaMemcpyDeviceToHost, e.stream));
-        LM_CK(ctx, cudaStreamSynchronize(e.stream));
+        LM_CK(ctx, cudaMemcpyAsync(mate, mate_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+        LM_CK(ctx, cudaStreamSynchronize(s));
     }
     if (stats) {
-        fill_round_stats(*e.st_host, stats, g->m, g->nrows);
+        fill_round_stats(*e.st_host, stats);
         prof.fill(stats);
     }
     return LM_OK;
@@ -610,73 +600,82 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     if (ctx->poisoned) return LM_ECUDA;
     if (count == 0) return LM_OK;
     if (!gs || !seeds || !mates) return fail(ctx, LM_EINVAL, "null array");
-    uint64_t nv = 0, ne = 0, nr = 0, nt = 0;
+    uint64_t nv = 0, ne = 0;
     for (uint32_t i = 0; i < count; i++) {
         if (!gs[i] || !mates[i]) return fail(ctx, LM_EINVAL, "null graph or mate at %u", i);
         if (gs[i]->ctx->device != ctx->device) return fail(ctx, LM_EINVAL, "graph %u lives on another device", i);
         nv += gs[i]->n;
         ne += gs[i]->nent;
-        nr += gs[i]->nrows;
-        nt += gs[i]->ntiles;
     }
-    if (nv > 0xFFFFFFF0ull || ne > 0xFFFFFFF0ull || nt + count > 0xFFFFFFF0ull)
-        return fail(ctx, LM_EINVAL, "batch too large for 32-bit union ids (split it)");
+    if (nv > 0xFFFFFFF0ull || ne > 0xFFFFFFF0ull) return fail(ctx, LM_EINVAL, "batch too large for 32-bit union ids");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DevGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
     Engine& e = ctx->eng;
     cudaStream_t s = e.stream;
     if (stats) memset(stats, 0, sizeof(lm_stats) * count);
-    int rc = ensure_ws(ctx, e, (uint32_t)nv, (uint32_t)ne, (uint32_t)nr, (uint32_t)(nt + 1), count);
+    int rc = ensure_ws(ctx, e, (uint32_t)nv, (uint32_t)ne, count);
     if (rc) return rc;
     Workspace& w = e.ws;
-    Job job;
-    job.nvert = (uint32_t)nv;
-    job.nent = (uint32_t)ne;
-    job.mate = w.mate;
-    job.ngraphs = count;
-    job.gvbase = w.gvbase;
-    job.grounds = w.grounds;
-    std::vector<uint32_t> gvb(count + 1);
+    // host tables: graph vertex / entry bases, offsets, segments, destinations
+    std::vector<uint32_t> gvb(count + 1), geb(count);
+    std::vector<const uint32_t*> goff(count);
+    std::vector<SegIn> segs(count);
     std::vector<uint32_t*> dst(count);
     std::vector<char> host_dst(count);
-    uint32_t vb = 0, tb = 0;
+    uint32_t vb = 0, eb = 0;
     for (uint32_t i = 0; i < count; i++) {
         gvb[i] = vb;
-        if (gs[i]->nent > 0) {
-            job.segs.push_back(seg_of(gs[i], seeds[i], vb, tb));
-            tb += gs[i]->ntiles;
-        }
+        geb[i] = eb;
+        goff[i] = gs[i]->off;
+        segs[i] = seg_of(gs[i], seeds[i], vb, eb);
         host_dst[i] = !is_device_ptr(mates[i]);
-        dst[i] = host_dst[i] ? nullptr : mates[i];
+        dst[i] = host_dst[i] ? w.cnbr + vb : mates[i];  // host results are staged in the cnbr array
         vb += gs[i]->n;
+        eb += gs[i]->nent;
     }
     gvb[count] = vb;
-    job.ntiles = tb;
-    rc = ensure_pinned(ctx, e, std::max((count + 1) * sizeof(uint32_t) + count * sizeof(uint32_t*),
-                                        job.segs.size() * sizeof(SegDesc)) + 64);
+    const size_t b_gvb = (count + 1) * sizeof(uint32_t), b_geb = count * sizeof(uint32_t);
+    const size_t b_off = count * sizeof(void*), b_seg = count * sizeof(SegIn), b_dst = count * sizeof(void*);
+    rc = ensure_pinned(ctx, e, b_gvb + b_geb + b_off + b_seg + b_dst + 256);
     if (rc) return rc;
-    memcpy(e.pinned, gvb.data(), (count + 1) * sizeof(uint32_t));
-    LM_CK(ctx, cudaMemcpyAsync(w.gvbase, e.pinned, (count + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    char* pin = static_cast<char*>(e.pinned);
+    size_t o = 0;
+    auto stage = [&](void* dev, const void* src, size_t bytes) -> cudaError_t {
+        memcpy(pin + o, src, bytes);
+        cudaError_t r = cudaMemcpyAsync(dev, pin + o, bytes, cudaMemcpyHostToDevice, s);
+        o = align_up(o + bytes, 16);
+        return r;
+    };
+    LM_CK(ctx, stage(w.gvbase, gvb.data(), b_gvb));
+    LM_CK(ctx, stage(w.gebase, geb.data(), b_geb));
+    LM_CK(ctx, stage(w.goff, goff.data(), b_off));
+    LM_CK(ctx, stage(w.segs, segs.data(), b_seg));
+    LM_CK(ctx, stage(w.gdst, dst.data(), b_dst));
     LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, count * sizeof(uint32_t), s));
     LM_CK(ctx, cudaMemsetAsync(w.gmatched, 0, count * sizeof(unsigned long long), s));
-    LM_CK(ctx, cudaStreamSynchronize(s));  // the pinned staging is reused by run_job
     Prof prof(ctx, s);
+    prof.begin(LM_K_OTHER);
+    LM_CK(ctx, launch_union_setup(s, w.gvbase, w.gebase, w.goff, count, (uint32_t)nv, w.start, w.gid, w.len[0]));
+    prof.end();
+    prof.begin(LM_K_INIT);
+    LM_CK(ctx, launch_init(s, w.mate, w.dead, w.bcnt, (uint32_t)nv, e.st));
+    prof.end();
+    Job job;
+    job.va = vertex_arrays(e, (uint32_t)nv, nullptr, true, w.mate);
+    job.ecap = (uint32_t)ne;
+    job.vlist = nullptr;
+    job.rdeg = nullptr;
+    job.nvlist = (uint32_t)nv;
+    job.nseg = ne > 0 ? count : 0;
+    job.grounds = w.grounds;
     rc = run_job(ctx, e, job, prof);
     if (rc) return rc;
-    // device destinations are written directly; host ones go through the cnbr array as staging
-    bool any_host = false;
-    for (uint32_t i = 0; i < count; i++) {
-        if (host_dst[i]) {
-            any_host = true;
-            dst[i] = w.cnbr + gvb[i];
-        }
-    }
-    memcpy(e.pinned, dst.data(), count * sizeof(uint32_t*));
-    LM_CK(ctx, cudaMemcpyAsync(w.gdst, e.pinned, count * sizeof(uint32_t*), cudaMemcpyHostToDevice, s));
     prof.begin(LM_K_OTHER);
     LM_CK(ctx, launch_to_local_batch(s, w.mate, w.gvbase, count, w.gdst, w.gmatched, (uint32_t)nv));
     prof.end();
+    bool any_host = false;
+    for (uint32_t i = 0; i < count; i++) any_host |= host_dst[i] != 0;
     std::vector<uint32_t> hmate;
     if (any_host) {
         hmate.resize(nv);

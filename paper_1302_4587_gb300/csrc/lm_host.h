@@ -19,23 +19,32 @@ constexpr int MAX_PROFILE_EVENTS = 1024;
 struct Workspace {
     void* block = nullptr;
     size_t bytes = 0;
-    uint32_t cap_v = 0, cap_e = 0, cap_r = 0, cap_t = 0, cap_g = 0;
-    uint32_t* cnbr = nullptr;        // [cap_v] chosen neighbour per vertex
-    uint8_t* dead = nullptr;         // [cap_v] matched flag per vertex
+    uint32_t cap_v = 0, cap_e = 0, cap_c = 0, cap_g = 0;
+    // per-vertex arrays (union ids)
+    uint32_t* start = nullptr;       // [cap_v] row start (batches; a single graph uses its own offsets)
+    uint32_t* gid = nullptr;         // [cap_v] graph of each vertex (batches)
+    uint32_t* len[2] = {nullptr, nullptr};   // [cap_v] live row lengths by round parity
+    uint32_t* cnbr = nullptr;        // [cap_v] chosen neighbour
+    uint8_t* dead = nullptr;         // [cap_v] matched flag
     uint32_t* mate = nullptr;        // [cap_v] union result / staging
-    uint64_t* key[2] = {nullptr, nullptr};   // [cap_e] live keys (ping-pong)
-    uint32_t* nbr[2] = {nullptr, nullptr};   // [cap_e] live neighbours
-    uint32_t* off[2] = {nullptr, nullptr};   // [cap_r + 1] live row offsets
-    uint32_t* vid[2] = {nullptr, nullptr};   // [cap_r] live row vertex ids
-    uint32_t* tilemap = nullptr;     // [cap_t + 1] first row of each tile of the live entries
-    uint32_t* lb_desc = nullptr;     // [4 * cap_t] look-back descriptors
-    Part* lb_part = nullptr;         // [cap_t] partial row maxima per tile
-    SegDesc* segs = nullptr;         // [cap_g] input segments of a sweep
+    uint32_t* bcnt = nullptr;        // [cap_v] finished chunks of long rows
+    // task lists: four sets, each T and M [cap_v] and C [cap_c]
+    uint2* T[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint2* M[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint2* C[4] = {nullptr, nullptr, nullptr, nullptr};
+    ulonglong2* part = nullptr;      // [cap_c] partial maxima of chunks
+    // live entries (ping-pong), union entry space
+    uint64_t* key[2] = {nullptr, nullptr};   // [cap_e]
+    uint32_t* nbr[2] = {nullptr, nullptr};   // [cap_e]
+    // per-graph tables (batches / serving)
+    SegIn* segs = nullptr;           // [cap_g]
     uint32_t* gvbase = nullptr;      // [cap_g + 1] first union vertex of each graph
+    uint32_t* gebase = nullptr;      // [cap_g] first union entry of each graph
+    const uint32_t** goff = nullptr; // [cap_g] each graph's row offsets
     uint32_t* grounds = nullptr;     // [cap_g] rounds per graph
+    uint32_t* glive = nullptr;       // [cap_g] live rows per graph
     uint32_t** gdst = nullptr;       // [cap_g] result destination per graph
     unsigned long long* gmatched = nullptr;  // [cap_g] matched vertices per graph
-    uint32_t* rows_per = nullptr;    // [cap_g] live rows per graph
 };
 
 // Device state + workspace + the stream they are used on.
@@ -70,17 +79,20 @@ struct lm_ctx {
     lm::ServeState* serve = nullptr;
 };
 
+// A device graph (Sec. 2 representation): per-vertex offsets into the
+// adjacency array, whose entries carry the neighbour, the edge index and the
+// order-preserving image of the edge weight.
 struct lm_graph {
     lm_ctx* ctx = nullptr;
-    uint32_t n = 0, m = 0, nrows = 0, nent = 0, ntiles = 0;
+    uint32_t n = 0, m = 0, nrows = 0, nent = 0;
     void* block = nullptr;
     size_t bytes = 0;
-    uint32_t* off = nullptr;         // [nrows + 1]
-    uint32_t* vid = nullptr;         // [nrows]
-    uint32_t* nbr = nullptr;         // [2m]
-    uint32_t* eid = nullptr;         // [2m]
-    uint32_t* ordw = nullptr;        // [2m]
-    uint32_t* tilemap = nullptr;     // [ntiles + 1]
+    uint32_t* off = nullptr;         // [n + 1] row offsets of all vertices
+    uint32_t* vid = nullptr;         // [nrows] vertices with at least one edge
+    uint32_t* rdeg = nullptr;        // [nrows] their degrees
+    uint32_t* nbr = nullptr;         // [2m] neighbour of each entry
+    uint32_t* eid = nullptr;         // [2m] edge index of each entry
+    uint32_t* ordw = nullptr;        // [2m] ord(weight) of each entry
 };
 
 namespace lm {
@@ -89,16 +101,44 @@ int fail(lm_ctx* ctx, int code, const char* fmt, ...);
 int cuda_fail(lm_ctx* ctx, cudaError_t e, const char* where);
 bool is_device_ptr(const void* p);
 uint64_t splitmix64_first(uint64_t seed);
-SegDesc seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t tile_begin);
-inline uint32_t tiles_of(uint32_t nent) { return (nent + SWEEP_T - 1) / SWEEP_T; }
+SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase);
+// chunk-list capacity for a union entry space of `ne` entries
+inline uint32_t chunks_cap(uint64_t ne) { return (uint32_t)(2 * (ne / CHUNK) + 64); }
 
 int engine_init(lm_ctx* ctx, Engine& e, cudaStream_t stream);
 void engine_free(Engine& e);
-int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t nr, uint32_t nt, uint32_t ng);
+int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng);
 int ensure_pinned(lm_ctx* ctx, Engine& e, size_t bytes);
 
-SweepArgs base_sweep_args(Engine& e, uint32_t nvert);
-VertexArgs base_vertex_args(Engine& e, uint32_t nvert, uint32_t* mate);
+// list set `k` of an engine (device counters in DevState::lcnt[k])
+Lists lists_of(Engine& e, int k);
+// per-vertex arrays of a job whose rows start at `start` (NULL: the workspace's)
+VertexArrays vertex_arrays(Engine& e, uint32_t nvert, const uint32_t* start, bool with_gid, uint32_t* mate);
+
+// The local-max loop over prepared union arrays (see lm_api.cpp).
+struct Job {
+    VertexArrays va;
+    uint32_t nseg = 0;               // graphs with edges (segment table already on the device)
+    uint32_t ecap = 0;               // union entries
+    const uint32_t* vlist = nullptr; // round-0 rows: explicit list (single graph) ...
+    const uint32_t* rdeg = nullptr;
+    uint32_t nvlist = 0;             // ... or, with vlist == NULL, the dense range [0, nvlist)
+    uint32_t* grounds = nullptr;
+};
+// Per-kernel CUDA-event timing of one call (LM_F_PROFILE); NULL-safe helpers.
+struct Prof {
+    lm_ctx* ctx;
+    cudaStream_t s;
+    bool on;
+    int kind[MAX_PROFILE_EVENTS / 2];
+    int n = 0;
+    uint32_t launches[LM_K_COUNT] = {0, 0, 0, 0, 0};
+    Prof(lm_ctx* c, cudaStream_t st);
+    void begin(int k);
+    void end();
+    void fill(lm_stats* st);
+};
+int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof);
 
 }  // namespace lm
 

@@ -1,27 +1,27 @@
 // sm_103a kernels of the local-max matching path.
 //
-// One local-max round (the phase of Sec. 2, steps 1-6) is two launches:
+// One round of local max (the phase of Sec. 2: every live vertex picks its
+// heaviest live edge, edges picked by both ends join M, edges touching M are
+// deleted) is two launches:
 //
-//   k_vertex   one thread per live vertex v: u = cnbr[v] is the neighbour of
-//              v's heaviest live edge; if cnbr[u] == v the edge is chosen by
-//              both ends and joins M (step 3; both ends write their own mate
-//              slot, so no conflict).  The same pass indexes the live entries
-//              in tiles for the coming sweep.
-//   k_sweep    one persistent pass over the live adjacency entries, in tiles
-//              of SWEEP_T entries: an entry survives when neither endpoint is
-//              matched (steps 4 and 5: the deletion flag of a vertex is its
-//              own dead[] byte, so spreading it over the vertex's edges is
-//              one read per row); survivors are compacted in order (step 6)
-//              and, in the same pass, every vertex's heaviest surviving edge
-//              is found by a segmented maximum over its row (step 2 of the
-//              next round, Lemma "broadcast").  Tile results are chained by a
-//              decoupled look-back whose carried state is the segmented
-//              aggregate of lm_internal.h, so rows cut by tile boundaries get
-//              both their compacted position and their maximum in this pass.
+//   k_vertex  over the rows that were live after the previous round: a row v
+//             whose chosen neighbour u = cnbr[v] chose v back is matched
+//             (both ends write their own mate slot, so there is no conflict;
+//             step 3).  Every other live row is filed into this round's task
+//             lists by its length.  Rows of matched vertices are never read
+//             again: deleting a vertex's edges costs nothing (steps 4-6).
+//   k_sweep   one warp per task: reads the row's live entries, keeps an entry
+//             when its neighbour is unmatched, writes the survivors to the
+//             front of the row's range in the other buffer, and takes the
+//             maximum key of the survivors -- the row's candidate for the
+//             next round (step 2 of the next round; the segmented maximum of
+//             Lemma "broadcast" restricted to one row).
 //
-// Round 0 reads the graph's own CSR (neighbour, edge id, ord(weight)) and
-// builds the 64-bit keys K(e) = ord(w) << 32 | perm_seed(e) on the fly; it
-// runs one candidate-only sweep, the match, then a compacting sweep.
+// Round 0 first files every row (k_vertex without matching), runs a
+// candidate-only sweep over the graphs' own arrays, then the match and a
+// compacting sweep that builds the 64-bit keys
+//     K(e) = ord(w_e) << 32 | perm_seed(e)
+// from (ord(weight), edge id) on the fly.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "lm_internal.h"
@@ -53,11 +53,6 @@ __device__ __forceinline__ uint32_t ord_of_bits(uint32_t b) {
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -66,7 +61,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, x, o);
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
         if (lane >= o) x += y;
     }
     return x;
@@ -74,628 +69,445 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 __device__ __forceinline__ void set_err(DevState* st, uint32_t bit, uint32_t info) {
     if ((atomicOr(&st->err, bit) & bit) == 0) st->err_info = info;
 }
-
-// The wait for a predecessor tile is bounded: after LOOKBACK_LIMIT_NS (or as
-// soon as any tile of the launch has given up) the sweep records ERR_TIMEOUT,
-// treats the missing tiles as empty and carries on; every index stays
-// checked, so nothing runs out of bounds and the kernel ends.
-constexpr uint64_t LOOKBACK_LIMIT_NS = 1000000000ull;
-
-__device__ __forceinline__ uint4 ld_volatile_v4(const uint32_t* p) {
-    uint4 v;
-    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ void st_volatile_v4(uint32_t* p, uint4 v) {
-    asm volatile("st.volatile.global.v4.u32 [%0], {%1,%2,%3,%4};"
-                 :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
-}
-// A tile's descriptor is one aligned 16-byte word written and read with
-// single vector accesses, so a reader sees either the aggregate or the
-// inclusive prefix, never a mix.
-__device__ __forceinline__ void publish_desc(uint32_t* desc, uint32_t t, uint32_t epoch, uint32_t kind, const Agg& A) {
-    st_volatile_v4(desc + 4 * (size_t)t, make_uint4((epoch << 2) | kind, A.S, A.nr, A.f));
+// warp-wide maximum of (key, neighbour); keys are unique among live entries of a row
+__device__ __forceinline__ void warp_kv_max(uint64_t& k, uint32_t& u) {
+    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(k >> 32));
+    const uint32_t lo = __reduce_max_sync(FULL, ((uint32_t)(k >> 32) == hi) ? (uint32_t)k : 0u);
+    const uint64_t best = ((uint64_t)hi << 32) | lo;
+    const uint32_t owner = __ballot_sync(FULL, k == best && best != 0);
+    u = owner ? __shfl_sync(FULL, u, __ffs(owner) - 1) : NIL;
+    k = owner ? best : 0;
 }
 
-// Exclusive prefix of tile t >= 1, computed by one full warp; every lane
-// returns the same value.  A window covers LB_PER_LANE * 32 predecessors read
-// in one round trip: lane l watches tiles base - LB_PER_LANE*l - q.  Only the
-// tiles between this one and the nearest inclusive prefix are waited for; the
-// window is combined oldest first (inside a lane, then by an ordered tree
-// reduction over lanes).
-constexpr int LB_PER_LANE = 4;
-
-__device__ Agg lookback(const SweepArgs& a, uint32_t t, uint32_t epoch, int lane, bool& timed_out) {
-    Agg suf = agg_identity();
-    int64_t base = (int64_t)t - 1;
-    const uint64_t t_start = globaltimer_ns();
-    const uint4 empty_incl = make_uint4((epoch << 2) | 2u, 0u, 0u, F_H);  // below tile 0: an empty prefix
-    for (;;) {
-        uint4 d[LB_PER_LANE];
-        bool valid[LB_PER_LANE];
-#pragma unroll
-        for (int q = 0; q < LB_PER_LANE; q++) {
-            d[q] = empty_incl;
-            valid[q] = base - (int64_t)(LB_PER_LANE * lane + q) < 0;
-        }
-        uint32_t my_incl = LB_PER_LANE;  // nearest inclusive element inside this lane
-        for (int spins = 0;; spins++) {
-#pragma unroll
-            for (int q = 0; q < LB_PER_LANE; q++) {
-                if (!valid[q]) {
-                    d[q] = ld_volatile_v4(a.lb_desc + 4 * (size_t)(base - (LB_PER_LANE * lane + q)));
-                    valid[q] = (d[q].x >> 2) == epoch && (d[q].x & 3u) != 0;
-                }
-            }
-            // this lane is ready when its elements up to its first inclusive one are valid
-            bool ready = true;
-            my_incl = LB_PER_LANE;
-#pragma unroll
-            for (int q = LB_PER_LANE - 1; q >= 0; q--)
-                if (valid[q] && (d[q].x & 3u) == 2u) my_incl = q;
-#pragma unroll
-            for (int q = 0; q < LB_PER_LANE; q++)
-                if (q <= (int)my_incl && q < LB_PER_LANE && !valid[q]) ready = false;
-            const uint32_t imask = __ballot_sync(FULL, my_incl < LB_PER_LANE);
-            const uint32_t rmask = __ballot_sync(FULL, ready);
-            const uint32_t need = imask ? ((2u << (__ffs(imask) - 1)) - 1u) : FULL;  // lanes up to the first inclusive
-            if ((rmask & need) == need) break;
-            if (spins > 8) {
-                bool give_up = false;
-                if (lane == 0)
-                    give_up = globaltimer_ns() - t_start > LOOKBACK_LIMIT_NS || (ld_volatile_u32(&a.st->err) & ERR_TIMEOUT);
-                if (__shfl_sync(FULL, give_up, 0)) {
-                    timed_out = true;
-#pragma unroll
-                    for (int q = 0; q < LB_PER_LANE; q++)
-                        if (!valid[q]) { d[q] = empty_incl; valid[q] = true; }
-                    my_incl = 0;
-                    break;
-                }
-                __nanosleep(spins < 64 ? 32 : 256);
-            }
-        }
-        const uint32_t imask = __ballot_sync(FULL, my_incl < LB_PER_LANE);
-        const int jl = imask ? __ffs(imask) - 1 : 32;
-        // combine this lane's elements oldest first, cut at the nearest inclusive one
-        Agg v = agg_identity();
-        if (lane <= jl) {
-            const int qmax = (lane == jl) ? (int)my_incl : LB_PER_LANE - 1;
-#pragma unroll
-            for (int q = LB_PER_LANE - 1; q >= 0; q--) {
-                if (q <= qmax) {
-                    Agg x;
-                    x.S = d[q].y; x.nr = d[q].z; x.f = d[q].w;
-                    v = agg_combine(v, x);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Agg w;
-            w.S = __shfl_down_sync(FULL, v.S, o);
-            w.nr = __shfl_down_sync(FULL, v.nr, o);
-            w.f = __shfl_down_sync(FULL, v.f, o);
-            if (lane + o < 32) v = agg_combine(w, v);
-        }
-        v.S = __shfl_sync(FULL, v.S, 0);
-        v.nr = __shfl_sync(FULL, v.nr, 0);
-        v.f = __shfl_sync(FULL, v.f, 0);
-        suf = agg_combine(v, suf);
-        if (imask) return suf;
-        base -= 32 * LB_PER_LANE;
+// ---------------------------------------------------------------- init
+__global__ void k_init(uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n, DevState* st) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (mate) mate[v] = NIL;
+        dead[v] = 0;
+        bcnt[v] = 0;
     }
-}
-
-// ---------------------------------------------------------------- sweep
-struct SweepSmem {
-    uint64_t kmax[SWEEP_T + 1];      // per local row: max surviving key (0 = none)
-    uint32_t off[SWEEP_T + 2];       // offsets of rows r_lo .. r_lo + nload
-    uint32_t vid[SWEEP_T + 1];       // global vertex id per local row
-    uint32_t knbr[SWEEP_T + 1];      // neighbour of kmax
-    uint32_t cnt[SWEEP_T + 1];       // survivors per local row
-    uint32_t rsw[SWEEP_GROUPS];      // row-start bitmap of the tile's entries
-    uint32_t rsw_pre[SWEEP_GROUPS];  // exclusive popcount prefix of rsw
-    uint32_t wS[SWEEP_WARPS];        // survivors per warp
-    uint32_t scanS[SWEEP_WARPS], scanE[SWEEP_WARPS];
-    Agg pre;                         // exclusive prefix of the tile
-    Agg tot;                         // aggregate of the tile
-    uint64_t hk_fin;                 // head row: maximum over earlier tiles (0 = none)
-    uint32_t hu_fin;
-    uint32_t tile, j0, nent, r_lo, nload, nrt, b0, seg, tile_begin;
-    uint32_t vbase, k0, k1, last, bad;
-    uint8_t rdead[SWEEP_T + 4];      // per local row: vertex matched this round
-};
-
-template <bool INPUT, bool COMPACT>
-__global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem& s = *reinterpret_cast<SweepSmem*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    DevState* st = a.st;
-
-    uint32_t ntiles, live_ent = 0, live_rows = 0;
-    if (INPUT) {
-        ntiles = a.ntiles_in;
-    } else {
-        live_ent = ld_volatile_u32(&st->cnt[a.in_buf][0]);
-        live_rows = ld_volatile_u32(&st->cnt[a.in_buf][1]);
-        ntiles = (live_ent + SWEEP_T - 1) / SWEEP_T;
-    }
-    if (ntiles == 0) {
-        if (COMPACT && blockIdx.x == 0 && tid == 0) {
-            const uint32_t S0 = a.prefix_in ? ld_volatile_u32(&a.prefix_in[0]) : 0u;
-            const uint32_t N0 = a.prefix_in ? ld_volatile_u32(&a.prefix_in[1]) : 0u;
-            st->cnt[a.out_buf][0] = S0;
-            st->cnt[a.out_buf][1] = N0;
-            if (N0 <= a.out_rows_cap) a.out_off[N0] = S0;
-        }
-        return;
-    }
-    const uint32_t epoch = ld_volatile_u32(&st->epoch) & 0x3FFFFFFFu;
-    if (ntiles > a.lb_cap) {
-        if (blockIdx.x == 0 && tid == 0) set_err(st, ERR_BOUNDS, ntiles);
-        return;  // no tile is processed, so no look-back record is awaited
-    }
-
-    for (;;) {
-        // ------------------------------------------------ locate the tile
-        // (ids are taken when a tile starts, so every earlier tile has started)
-        if (tid == 0) {
-            const uint32_t t = atomicAdd(&st->tile_ctr, 1u);
-            s.tile = t;
-            if (t < ntiles) {
-                uint32_t lt = t, nrows_seg, nent_seg;
-                const uint32_t* tm;
-                if (INPUT) {
-                    uint32_t lo = 0, hi = a.nsegs - 1;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi + 1) >> 1;
-                        if (a.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-                    }
-                    const SegDesc& sg = a.segs[lo];
-                    s.seg = lo;
-                    s.tile_begin = sg.tile_begin;
-                    lt = t - sg.tile_begin;
-                    tm = sg.tilemap;
-                    nrows_seg = sg.nrows;
-                    nent_seg = sg.nent;
-                    s.vbase = sg.vbase; s.k0 = sg.k0; s.k1 = sg.k1;
-                } else {
-                    tm = a.in_tilemap;
-                    nrows_seg = live_rows;
-                    nent_seg = live_ent;
-                    s.seg = 0; s.tile_begin = 0; s.vbase = 0; s.k0 = 0; s.k1 = 0;
-                }
-                const uint32_t j0 = lt * SWEEP_T;
-                uint32_t nent = min((uint32_t)SWEEP_T, nent_seg - j0);
-                uint32_t r_lo = tm[lt];
-                const uint32_t r_nx = tm[lt + 1];
-                uint32_t bad = 0;
-                uint32_t r_cap = 0;
-                if (nrows_seg == 0 || r_lo >= nrows_seg) {
-                    bad = 1;
-                } else {
-                    r_cap = min(r_nx, nrows_seg - 1);
-                    if (r_lo > r_cap || r_cap - r_lo > (uint32_t)SWEEP_T) bad = 1;
-                }
-                if (bad) {
-                    // inconsistent tile index: record it and process the tile as empty
-                    set_err(st, ERR_BOUNDS, t);
-                    nent = 0; r_lo = 0; r_cap = 0;
-                }
-                s.bad = bad;
-                s.j0 = j0; s.nent = nent; s.r_lo = r_lo; s.nload = bad ? 0u : r_cap - r_lo + 1;
-                s.last = (t == ntiles - 1);
-            }
-        }
-        __syncthreads();
-        const uint32_t t = s.tile;
-        if (t >= ntiles) break;
-
-        const uint32_t* r_off;
-        const uint32_t* r_vid;
-        if (INPUT) { r_off = a.segs[s.seg].off; r_vid = a.segs[s.seg].vid; }
-        else { r_off = a.in_off; r_vid = a.in_vid; }
-        const uint32_t j0 = s.j0, nent = s.nent, r_lo = s.r_lo, nload = s.nload, vbase = s.vbase;
-
-        // ------------------------------------------------ row data
-        const bool bad = s.bad != 0;
-        if (!bad)
-            for (uint32_t i = tid; i <= nload; i += SWEEP_THREADS) s.off[i] = r_off[r_lo + i];
-        else if (tid == 0) { s.off[0] = j0; s.off[1] = j0; s.vid[0] = 0; s.kmax[0] = 0; s.knbr[0] = NIL; s.cnt[0] = 0; s.rdead[0] = 1; }
-        for (uint32_t i = tid; i < nload; i += SWEEP_THREADS) {
-            uint32_t v = r_vid[r_lo + i] + vbase;
-            if (v >= a.nvert) { set_err(st, ERR_BOUNDS, v); v = 0; }
-            s.vid[i] = v;
-            s.kmax[i] = 0;
-            s.knbr[i] = NIL;
-            s.cnt[i] = 0;
-            s.rdead[i] = COMPACT ? a.dead[v] : 0;
-        }
-        for (int i = tid; i < SWEEP_GROUPS; i += SWEEP_THREADS) s.rsw[i] = 0;
-        __syncthreads();
-        for (uint32_t i = tid; i < nload; i += SWEEP_THREADS) {
-            const uint32_t p = s.off[i];
-            if (p >= j0 && p < j0 + nent) atomicOr(&s.rsw[(p - j0) >> 5], 1u << ((p - j0) & 31));
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t w0 = s.rsw[2 * lane], w1 = s.rsw[2 * lane + 1];
-            const uint32_t c0 = __popc(w0), sum = c0 + __popc(w1);
-            const uint32_t incl = warp_incl_scan(sum, lane);
-            s.rsw_pre[2 * lane] = incl - sum;
-            s.rsw_pre[2 * lane + 1] = incl - sum + c0;
-            if (lane == 31) {
-                const uint32_t b0 = (s.off[0] == j0) ? 1u : 0u;
-                s.b0 = b0;
-                s.nrt = incl + (1u - b0);
-            }
-        }
-        __syncthreads();
-        const uint32_t b0 = s.b0, nrt = s.nrt;
-
-        // ------------------------------------------------ entries: load
-        uint64_t key[SWEEP_GPW];
-        uint32_t ug[SWEEP_GPW], lr[SWEEP_GPW], sm[SWEEP_GPW];
-        const uint32_t* in_nbr;
-        const uint32_t* in_eid = nullptr;
-        const uint32_t* in_ordw = nullptr;
-        if (INPUT) {
-            const SegDesc& sg = a.segs[s.seg];
-            in_nbr = sg.nbr; in_eid = sg.eid; in_ordw = sg.ordw;
-        } else {
-            in_nbr = a.in_nbr;
-        }
-        const uint32_t k0 = s.k0, k1 = s.k1;
-        uint32_t eidv[SWEEP_GPW];
-#pragma unroll
-        for (int i = 0; i < SWEEP_GPW; i++) {
-            const int g = warp * SWEEP_GPW + i;
-            const uint32_t q = (uint32_t)g * 32u + lane;
-            const uint32_t word = s.rsw[g];
-            const uint32_t r = s.rsw_pre[g] + __popc(word & (FULL >> (31 - lane))) - b0;
-            lr[i] = r;
-            bool live = false;
-            if (q < nent) live = (r < nrt) ? (s.rdead[r] == 0) : false;
-            key[i] = 0;
-            ug[i] = NIL;
-            eidv[i] = 0;
-            if (live) {
-                const uint32_t j = j0 + q;
-                ug[i] = in_nbr[j];
-                if (INPUT) {
-                    eidv[i] = in_eid[j];
-                    key[i] = (uint64_t)in_ordw[j] << 32;
-                } else {
-                    key[i] = a.in_key[j];
-                }
-            }
-        }
-        // ------------------------------------------------ entries: deletion test, per-row max / count
-#pragma unroll
-        for (int i = 0; i < SWEEP_GPW; i++) {
-            bool surv = key[i] != 0;
-            if (surv) {
-                if (INPUT) {
-                    ug[i] += vbase;
-                    key[i] |= perm_seed(eidv[i], k0, k1);
-                }
-                if (ug[i] >= a.nvert) { set_err(st, ERR_BOUNDS, ug[i]); surv = false; }
-                else if (COMPACT) surv = a.dead[ug[i]] == 0;
-            }
-            if (!surv) key[i] = 0;
-        }
-#pragma unroll
-        for (int i = 0; i < SWEEP_GPW; i++) {
-            const int g = warp * SWEEP_GPW + i;
-            const bool surv = key[i] != 0;
-            const uint32_t ball = __ballot_sync(FULL, surv);
-            sm[i] = ball;
-            if ((s.rsw[g] & 0xFFFFFFFEu) == 0) {
-                // the whole group lies in one row (the row of lane 0)
-                if (ball) {
-                    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i] >> 32));
-                    const uint32_t lo = __reduce_max_sync(FULL, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
-                    if (lane == 0) {
-                        atomicMax(reinterpret_cast<unsigned long long*>(&s.kmax[lr[i]]),
-                                  (unsigned long long)(((uint64_t)hi << 32) | lo));
-                        if (COMPACT) atomicAdd(&s.cnt[lr[i]], (uint32_t)__popc(ball));
-                    }
-                }
-            } else if (surv) {
-                atomicMax(reinterpret_cast<unsigned long long*>(&s.kmax[lr[i]]), (unsigned long long)key[i]);
-                if (COMPACT) atomicAdd(&s.cnt[lr[i]], 1u);
-            }
-        }
-        __syncthreads();
-        uint32_t wsum = 0;
-#pragma unroll
-        for (int i = 0; i < SWEEP_GPW; i++) {
-            if (key[i] != 0 && key[i] == s.kmax[lr[i]]) s.knbr[lr[i]] = ug[i];
-            wsum += __popc(sm[i]);
-        }
-        if (lane == 0) s.wS[warp] = wsum;
-
-        // ------------------------------------------------ row scans (survivor counts, new rows)
-        const uint32_t rbeg = min((uint32_t)tid * SWEEP_RPT, nrt);
-        const uint32_t rend = min(rbeg + SWEEP_RPT, nrt);
-        __syncthreads();
-        uint32_t cS = 0, cE = 0;
-        if (COMPACT) {
-            for (uint32_t r = rbeg; r < rend; r++) {
-                const uint32_t c = s.cnt[r];
-                cS += c;
-                if ((r > 0 || b0) && c > 0) cE++;
-            }
-        }
-        uint32_t oS = 0, oE = 0;
-        if (COMPACT) {
-            const uint32_t iS = warp_incl_scan(cS, lane), iE = warp_incl_scan(cE, lane);
-            if (lane == 31) { s.scanS[warp] = iS; s.scanE[warp] = iE; }
-            __syncthreads();
-            uint32_t bS = 0, bE = 0, TS = 0, TE = 0;
-#pragma unroll
-            for (int w = 0; w < SWEEP_WARPS; w++) {
-                if (w < warp) { bS += s.scanS[w]; bE += s.scanE[w]; }
-                TS += s.scanS[w]; TE += s.scanE[w];
-            }
-            oS = bS + iS - cS;
-            oE = bE + iE - cE;
-            if (tid == 0) { s.tot.S = TS; s.tot.nr = TE; }
-        }
-        if (tid == 0) {
-            // aggregate flags and partial maxima of the tile
-            Agg& A = s.tot;
-            if (!COMPACT) { A.S = 0; A.nr = 0; }
-            const bool h = b0 || nrt > 1;
-            Part P;
-            P.pad0 = P.pad1 = 0;
-            if (!b0 && nrt > 0) { P.hk = s.kmax[0]; P.hu = s.knbr[0]; } else { P.hk = 0; P.hu = NIL; }
-            if (h && nrt > 0) { P.tk = s.kmax[nrt - 1]; P.tu = s.knbr[nrt - 1]; }
-            else if (h) { P.tk = 0; P.tu = NIL; }
-            else { P.tk = P.hk; P.tu = P.hu; }
-            A.f = (h ? F_H : 0u) | (P.hk ? F_HS : 0u) | (P.tk ? F_TS : 0u);
-            __stcg(reinterpret_cast<ulonglong2*>(&a.lb_part[t]), make_ulonglong2(P.hk, P.tk));
-            __stcg(reinterpret_cast<uint4*>(&a.lb_part[t]) + 1, make_uint4(P.hu, P.tu, 0u, 0u));
-        }
-        __syncthreads();
-
-        // ------------------------------------------------ look-back
-        if (warp == 0) {
-            const Agg A = s.tot;
-            Agg P = agg_identity();
-            bool to = false;
-            if (t == 0) {
-                P.f = F_H;
-                if (a.prefix_in) {
-                    P.S = ld_volatile_u32(&a.prefix_in[0]);
-                    P.nr = ld_volatile_u32(&a.prefix_in[1]);
-                }
-            } else {
-                if (lane == 0) {
-                    __threadfence();  // partial maxima before the aggregate
-                    publish_desc(a.lb_desc, t, epoch, 1u, A);
-                }
-                P = lookback(a, t, epoch, lane, to);
-                to = __any_sync(FULL, to);
-            }
-            Agg I = agg_combine(P, A);
-            I.f = F_H | (I.f & F_TS);
-            if (lane == 0) {
-                if (to) set_err(st, ERR_TIMEOUT, t);
-                if (t == 0) __threadfence();
-                publish_desc(a.lb_desc, t, epoch, 2u, I);
-                s.pre = P;
-                if (COMPACT && s.last) {
-                    // totals of the sweep: sentinel offset and the next round's counts
-                    uint32_t S_tot = I.S, N_tot = I.nr;
-                    if (N_tot > a.out_rows_cap || S_tot > a.out_cap) {
-                        set_err(st, ERR_BOUNDS, N_tot);
-                        S_tot = 0; N_tot = 0;  // stop the loop rather than read past the arrays
-                    }
-                    a.out_off[N_tot] = S_tot;
-                    st->cnt[a.out_buf][0] = S_tot;
-                    st->cnt[a.out_buf][1] = N_tot;
-                    const uint32_t rn = a.round + 1;
-                    if (rn < 64) { st->ring_m[rn] = S_tot / 2; st->ring_n[rn] = N_tot; }
-                    if (S_tot == 0) st->rounds = rn;
-                }
-            }
-            // head row continuing from earlier tiles: gather its maximum from their
-            // partials (all earlier tiles have published them: the look-back saw
-            // every one of them at least as an aggregate)
-            const bool need_head = !bad && !b0 && nrt > 0 && (nrt > 1 || s.off[nrt] == j0 + nent);
-            uint64_t hk = 0;
-            uint32_t hu = NIL;
-            if (need_head) {
-                __threadfence();
-                const uint32_t gt_start = s.tile_begin + s.off[0] / SWEEP_T;  // tile where the row starts
-                for (uint32_t k = gt_start + lane; k < t; k += 32) {
-                    const Part* pp = &a.lb_part[k];
-                    const ulonglong2 kk = __ldcg(reinterpret_cast<const ulonglong2*>(pp));
-                    const uint4 uu = __ldcg(reinterpret_cast<const uint4*>(pp) + 1);
-                    // the start tile contributes its tail, the tiles after it their whole (head) part
-                    if (k == gt_start) kv_max(hk, hu, kk.y, uu.y);
-                    else kv_max(hk, hu, kk.x, uu.x);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const uint64_t k2 = __shfl_xor_sync(FULL, hk, o);
-                    const uint32_t u2 = __shfl_xor_sync(FULL, hu, o);
-                    kv_max(hk, hu, k2, u2);
-                }
-            }
-            if (lane == 0) { s.hk_fin = hk; s.hu_fin = hu; }
-        }
-        __syncthreads();
-        const Agg P = s.pre;
-
-        // ------------------------------------------------ compacted entries
-        if (COMPACT) {
-            uint32_t base = P.S;
-            for (int w = 0; w < warp; w++) base += s.wS[w];
-            const uint32_t lt_mask = lanemask_lt();
-#pragma unroll
-            for (int i = 0; i < SWEEP_GPW; i++) {
-                if (key[i] != 0) {
-                    const uint32_t pos = base + __popc(sm[i] & lt_mask);
-                    if (pos < a.out_cap) {
-                        a.out_key[pos] = key[i];
-                        a.out_nbr[pos] = ug[i];
-                    } else {
-                        set_err(st, ERR_BOUNDS, pos);
-                    }
-                }
-                base += __popc(sm[i]);
-            }
-        }
-        // ------------------------------------------------ rows: compacted rows, next candidates
-        {
-            const bool head_cont = (b0 == 0);
-            const bool prev_surv = (P.f & F_TS) != 0;
-            const bool head_new = COMPACT && head_cont && s.cnt[0] > 0 && !prev_surv;
-            uint32_t posr = P.S + oS;
-            uint32_t idx = P.nr + (head_new ? 1u : 0u) + oE;
-            const bool last_ends = (s.off[nrt] == j0 + nent);
-            for (uint32_t r = rbeg; r < rend; r++) {
-                const bool is_head = head_cont && r == 0;
-                if (COMPACT) {
-                    const uint32_t c = s.cnt[r];
-                    const bool isnew = !bad && (is_head ? head_new : (c > 0));
-                    if (isnew) {
-                        const uint32_t ni = is_head ? P.nr : idx;
-                        if (ni < a.out_rows_cap) {
-                            a.out_off[ni] = posr;
-                            a.out_vid[ni] = s.vid[r];
-                        } else {
-                            set_err(st, ERR_BOUNDS, ni);
-                        }
-                        if (!is_head) idx++;
-                    }
-                    posr += c;
-                }
-                if (!bad && (r + 1 < nrt || last_ends)) {
-                    uint64_t k = s.kmax[r];
-                    uint32_t u = s.knbr[r];
-                    if (is_head) kv_max(k, u, s.hk_fin, s.hu_fin);
-                    if (k != 0) a.cnbr[s.vid[r]] = u;
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    // every CTA passes here once; the last one resets the tile counter for
-    // the next sweep and advances the look-back generation
-    if (tid == 0) {
-        __threadfence();
-        const uint32_t done = atomicAdd(&st->exit_ctr, 1u);
-        if (done == gridDim.x - 1) {
-            st->tile_ctr = 0;
-            st->exit_ctr = 0;
-            uint32_t e = (st->epoch + 1) & 0x3FFFFFFFu;
-            st->epoch = e ? e : 1u;
-            __threadfence();
+    if (st && blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) { st->ring_m[i] = 0; st->ring_n[i] = 0; }
+        if (threadIdx.x < 16) (&st->lcnt[0][0])[threadIdx.x] = 0;
+        if (threadIdx.x == 0) {
+            st->err = 0; st->err_info = 0; st->rounds = 0; st->done = 0;
+            st->live_rows = 0; st->live_ent = 0; st->matched2 = 0;
         }
     }
 }
 
 // ---------------------------------------------------------------- vertex pass
-__device__ __forceinline__ void count_matched(DevState* st, bool m) {
-    const uint32_t b = __ballot_sync(FULL, m);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&st->matched2, (unsigned long long)__popc(b));
-}
+constexpr int VT = 256;  // threads
+constexpr int VI = 8;    // rows per thread per block iteration
 
-__device__ __forceinline__ void note_round(const VertexArgs& a, uint32_t v) {
-    if (!a.grounds) return;
-    uint32_t lo = 0, hi = a.ngraphs - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.gvbase[mid] <= v) lo = mid; else hi = mid - 1;
+// exclusive scan of three counters over the block (a, b, c become their
+// prefixes; tot receives the block totals)
+__device__ __forceinline__ void block_excl_scan3(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t* tmp,
+                                                 uint32_t tot[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ia = warp_incl_scan(a, lane), ib = warp_incl_scan(b, lane), ic = warp_incl_scan(c, lane);
+    if (lane == 31) { tmp[warp * 3] = ia; tmp[warp * 3 + 1] = ib; tmp[warp * 3 + 2] = ic; }
+    __syncthreads();
+    uint32_t pa = 0, pb = 0, pc = 0;
+    tot[0] = tot[1] = tot[2] = 0;
+#pragma unroll
+    for (int w = 0; w < VT / 32; w++) {
+        const uint32_t x = tmp[w * 3], y = tmp[w * 3 + 1], z = tmp[w * 3 + 2];
+        if (w < warp) { pa += x; pb += y; pc += z; }
+        tot[0] += x; tot[1] += y; tot[2] += z;
     }
-    atomicMax(&a.grounds[lo], a.round + 1);
+    a = pa + ia - a;
+    b = pb + ib - b;
+    c = pc + ic - c;
 }
 
-// round 0: the vertices [vbegin, vbegin + vcount); a vertex with a candidate has cnbr != NIL
-__global__ void __launch_bounds__(256) k_vertex_all(const VertexArgs a) {
-    const uint32_t n = a.nvert;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < a.vcount; base += stride) {
-        const uint32_t v = a.vbegin + base + threadIdx.x;
-        bool m = false;
-        if (base + threadIdx.x < a.vcount && v < n) {
-            const uint32_t u = a.cnbr[v];
-            if (u != NIL) {
-                if (u >= n) set_err(a.st, ERR_BOUNDS, u);
-                else if (a.cnbr[u] == v) {
-                    a.mate[v] = u;
-                    a.dead[v] = 1;
-                    m = true;
-                    note_round(a, v);
-                }
-            }
-        }
-        count_matched(a.st, m);
-    }
-}
-
-// rounds >= 1: the live rows of the compacted arrays
-__global__ void __launch_bounds__(256) k_vertex_live(const VertexArgs a) {
+__global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
+    __shared__ uint32_t s_tmp[3 * (VT / 32)];
+    __shared__ uint32_t s_base[3];
+    __shared__ unsigned long long s_red[3 * (VT / 32)];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     DevState* st = a.st;
-    const uint32_t R = ld_volatile_u32(&st->cnt[a.in_buf][1]);
-    const uint32_t E = ld_volatile_u32(&st->cnt[a.in_buf][0]);
-    if (R == 0) return;
-    const uint32_t ntiles = (E + SWEEP_T - 1) / SWEEP_T;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < R; base += stride) {
-        const uint32_t i = base + threadIdx.x;
-        bool m = false;
-        if (i < R) {
-            const uint32_t v = a.vid[i];
-            if (v >= a.nvert) {
-                set_err(st, ERR_BOUNDS, v);
-            } else {
-                const uint32_t u = a.cnbr[v];
-                if (u >= a.nvert) set_err(st, ERR_BOUNDS, u);
-                else if (a.cnbr[u] == v) {
-                    a.mate[v] = u;
-                    a.dead[v] = 1;
-                    m = true;
-                    note_round(a, v);
+    const VertexArrays& va = a.va;
+    const uint32_t par = a.par;
+
+    uint32_t nT = 0, nM = 0, nC = 0, total;
+    if (a.vlist || !a.in.cnt) {
+        total = a.nvlist;
+    } else {
+        nT = ld_volatile_u32(&a.in.cnt[0]);
+        nM = ld_volatile_u32(&a.in.cnt[1]);
+        nC = ld_volatile_u32(&a.in.cnt[2]);
+        total = nC + nM + nT;
+    }
+    unsigned long long my_rows = 0, my_ent = 0, my_match = 0;
+
+    for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
+        uint32_t vv[VI], LL[VI], cls[VI];
+        uint32_t cT = 0, cM = 0, cC = 0;
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            const uint32_t idx = base + i * VT + tid;
+            uint32_t v = NIL, L = 0;
+            cls[i] = 0;
+            if (idx < total) {
+                if (a.vlist) {
+                    v = a.vlist[idx] + a.vlist_base;
+                    if (v < va.nvert) {
+                        if (a.deg0) { L = a.deg0[idx]; va.len[par][v] = L; }
+                        else L = va.len[par][v];
+                    }
+                } else if (!a.in.cnt) {
+                    v = idx;  // dense range of vertices
+                    L = va.len[par][v];
+                } else if (idx < nC) {
+                    const uint2 c = a.in.C[idx];
+                    if (c.y == 0) { v = c.x; if (v < va.nvert) L = va.len[par][v]; }
+                } else if (idx < nC + nM) {
+                    v = a.in.M[idx - nC].x;
+                    if (v < va.nvert) L = va.len[par][v];
+                } else {
+                    v = a.in.T[idx - nC - nM].x;
+                    if (v < va.nvert) L = va.len[par][v];
+                }
+                if (v != NIL && v >= va.nvert) { set_err(st, ERR_BOUNDS, v); v = NIL; L = 0; }
+            }
+            bool open_row = false;
+            if (v != NIL && L > 0) {
+                my_rows++;
+                my_ent += L;
+                bool matched = false;
+                if (a.match) {
+                    const uint32_t u = va.cnbr[v];
+                    if (u >= va.nvert) set_err(st, ERR_BOUNDS, u);
+                    else if (va.cnbr[u] == v) {
+                        va.mate[v] = u;
+                        va.dead[v] = 1;
+                        matched = true;
+                        my_match++;
+                    }
+                }
+                if (!matched) {
+                    open_row = true;
+                    if (L <= TINY_MAX) { cls[i] = 1; cT++; }
+                    else if (L <= CHUNK) { cls[i] = 2; cM++; }
+                    else {
+                        cls[i] = 3;
+                        cC += (L + CHUNK - 1) / CHUNK;
+                        if (a.match) va.len[par ^ 1][v] = 0;  // long rows gather their survivors atomically
+                    }
                 }
             }
-            const uint32_t lo = a.off[i], hi = a.off[i + 1];
-            for (uint32_t tt = (lo + SWEEP_T - 1) / SWEEP_T; tt < (hi + SWEEP_T - 1) / SWEEP_T; tt++) {
-                if (tt < a.tilemap_cap) a.tilemap[tt] = i;
-                else set_err(st, ERR_BOUNDS, tt);
+            // per-graph counters, aggregated over the lanes of a warp that share a graph
+            if (a.grounds) {
+                const uint32_t g = (v != NIL && L > 0) ? (va.gid ? va.gid[v] : 0u) : NIL;
+                const uint32_t same = __match_any_sync(FULL, g);
+                if (g != NIL && lane == __ffs(same) - 1) atomicMax(&a.grounds[g], a.round + 1);
             }
-            if (i == R - 1) {
-                if (ntiles < a.tilemap_cap) a.tilemap[ntiles] = R;
-                else set_err(st, ERR_BOUNDS, ntiles);
+            if (a.glive) {
+                const uint32_t g = open_row ? (va.gid ? va.gid[v] : 0u) : NIL;
+                const uint32_t same = __match_any_sync(FULL, g);
+                if (g != NIL && lane == __ffs(same) - 1) atomicAdd(&a.glive[g], (uint32_t)__popc(same));
+            }
+            vv[i] = v;
+            LL[i] = L;
+        }
+        // block-aggregated appends to the task lists
+        uint32_t tot[3];
+        block_excl_scan3(cT, cM, cC, s_tmp, tot);
+        if (tid == 0) {
+            s_base[0] = tot[0] ? atomicAdd(&a.out.cnt[0], tot[0]) : 0;
+            s_base[1] = tot[1] ? atomicAdd(&a.out.cnt[1], tot[1]) : 0;
+            s_base[2] = tot[2] ? atomicAdd(&a.out.cnt[2], tot[2]) : 0;
+        }
+        __syncthreads();
+        uint32_t pT = s_base[0] + cT, pM = s_base[1] + cM, pC = s_base[2] + cC;
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            if (cls[i] == 1) {
+                if (pT < a.out.capT) a.out.T[pT] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pT);
+                pT++;
+            } else if (cls[i] == 2) {
+                if (pM < a.out.capM) a.out.M[pM] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pM);
+                pM++;
+            } else if (cls[i] == 3) {
+                const uint32_t nch = (LL[i] + CHUNK - 1) / CHUNK;
+                for (uint32_t c = 0; c < nch; c++, pC++) {
+                    if (pC < a.out.capC) a.out.C[pC] = make_uint2(vv[i], c); else set_err(st, ERR_BOUNDS, pC);
+                }
             }
         }
-        count_matched(st, m);
+        __syncthreads();  // s_base / s_tmp reuse
+    }
+
+    // statistics of the round: live rows, live entries, matched vertices
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_rows += __shfl_xor_sync(FULL, my_rows, o);
+        my_ent += __shfl_xor_sync(FULL, my_ent, o);
+        my_match += __shfl_xor_sync(FULL, my_match, o);
+    }
+    if (lane == 0) { s_red[warp * 3] = my_rows; s_red[warp * 3 + 1] = my_ent; s_red[warp * 3 + 2] = my_match; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long r = 0, e = 0, mt = 0;
+        for (int w = 0; w < VT / 32; w++) { r += s_red[w * 3]; e += s_red[w * 3 + 1]; mt += s_red[w * 3 + 2]; }
+        if (a.match) {
+            if (r) atomicAdd(&st->live_rows, (uint32_t)r);
+            if (e) atomicAdd(&st->live_ent, e);
+            if (mt) atomicAdd(&st->matched2, mt);
+        }
+        // the last CTA closes the pass: consumed lists are emptied, round statistics recorded
+        __threadfence();
+        const uint32_t done = atomicAdd(&st->exit_v, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; st->lcnt[a.in_set][2] = 0; }
+            if (a.match) {
+                const uint32_t rows = ld_volatile_u32(&st->live_rows);
+                const unsigned long long ent = *reinterpret_cast<volatile unsigned long long*>(&st->live_ent);
+                if (a.round < 64) { st->ring_m[a.round] = ent / 2; st->ring_n[a.round] = rows; }
+                if (rows == 0 && !st->done) { st->done = 1; st->rounds = a.round; }
+                st->live_rows = 0;
+                st->live_ent = 0;
+            }
+            st->exit_v = 0;
+            __threadfence();
+        }
     }
 }
 
-// ---------------------------------------------------------------- init
-__global__ void k_init(uint32_t* mate, uint32_t* cnbr, uint8_t* dead, uint32_t n, DevState* st) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        if (mate) mate[v] = NIL;
-        cnbr[v] = NIL;
-        dead[v] = 0;
+// ---------------------------------------------------------------- sweep
+// Tasks: [0, nC) chunks of long rows, [nC, nC + nM) medium rows,
+// [nC + nM, ...) batches of 32 tiny rows.  Warps take tasks round-robin.
+constexpr int ST = 256;        // threads per CTA (8 independent warps)
+constexpr int SG = 4;          // groups of 32 entries loaded together
+
+struct Src {                   // where one row's entries come from
+    const uint32_t* nbr;
+    const uint32_t* eid;
+    const uint32_t* ordw;
+    const uint64_t* key;
+    uint32_t off;              // index of the row's entry 0 in those arrays
+    uint32_t vbase, k0, k1;
+};
+
+template <bool INPUT>
+__device__ __forceinline__ Src src_of(const SweepArgs& a, uint32_t v, uint32_t s0) {
+    Src s;
+    if (INPUT) {
+        const SegIn& g = a.segs[a.va.gid ? a.va.gid[v] : 0];
+        s.nbr = g.nbr; s.eid = g.eid; s.ordw = g.ordw; s.key = nullptr;
+        s.off = s0 - g.ebase; s.vbase = g.vbase; s.k0 = g.k0; s.k1 = g.k1;
+    } else {
+        s.nbr = a.in_nbr; s.eid = nullptr; s.ordw = nullptr; s.key = a.in_key;
+        s.off = s0; s.vbase = 0; s.k0 = 0; s.k1 = 0;
     }
-    if (st && blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) { st->ring_m[i] = 0; st->ring_n[i] = 0; }
-        if (threadIdx.x == 0) {
-            st->cnt[0][0] = st->cnt[0][1] = st->cnt[1][0] = st->cnt[1][1] = 0;
-            st->err = 0;
-            st->err_info = 0;
-            st->rounds = 0;
-            st->matched2 = 0;
+    return s;
+}
+
+// Loads SG groups of a row's entries [j, j + 32*SG) (valid below `end`),
+// applies the deletion test and yields (key, neighbour) per lane and group;
+// key = 0 for entries that are not live.
+template <bool INPUT, bool COMPACT>
+__device__ __forceinline__ void load_groups(const SweepArgs& a, const Src& s, uint32_t j, uint32_t end, int lane,
+                                            uint64_t key[SG], uint32_t u[SG]) {
+    uint32_t e[SG];
+#pragma unroll
+    for (int i = 0; i < SG; i++) {
+        const uint32_t q = j + i * 32 + lane;
+        u[i] = NIL;
+        key[i] = 0;
+        e[i] = 0;
+        if (q < end) {
+            u[i] = __ldcs(s.nbr + s.off + q);
+            if (INPUT) e[i] = __ldcs(s.eid + s.off + q);
+        }
+    }
+    bool keep[SG];
+#pragma unroll
+    for (int i = 0; i < SG; i++) {
+        keep[i] = u[i] != NIL;
+        if (keep[i]) {
+            if (INPUT) u[i] += s.vbase;
+            if (u[i] >= a.va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
+            else if (COMPACT) keep[i] = a.va.dead[u[i]] == 0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < SG; i++) {
+        if (keep[i]) {
+            const uint32_t q = j + i * 32 + lane;
+            if (INPUT) key[i] = ((uint64_t)__ldcs(s.ordw + s.off + q) << 32) | perm_seed(e[i], s.k0, s.k1);
+            else key[i] = __ldcs(s.key + s.off + q);
+        }
+    }
+}
+
+template <bool INPUT, bool COMPACT>
+__device__ void do_warp_row(const SweepArgs& a, uint32_t v, uint32_t L, uint32_t j_begin, uint32_t j_end,
+                            bool chunked, uint32_t task, int lane) {
+    const VertexArrays& va = a.va;
+    const uint32_t s0 = va.start[v];
+    if ((uint64_t)s0 + L > a.ecap) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); return; }
+    const Src s = src_of<INPUT>(a, v, s0);
+    uint32_t* len_next = va.len[a.par ^ 1u];
+    uint32_t cnt = 0;
+    uint64_t bk = 0;
+    uint32_t bu = NIL;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t j = j_begin; j < j_end; j += 32 * SG) {
+        uint64_t key[SG];
+        uint32_t u[SG];
+        load_groups<INPUT, COMPACT>(a, s, j, j_end, lane, key, u);
+        uint32_t ball[SG], sub = 0;
+#pragma unroll
+        for (int i = 0; i < SG; i++) {
+            ball[i] = __ballot_sync(FULL, key[i] != 0);
+            sub += __popc(ball[i]);
+            kv_max(bk, bu, key[i], u[i]);
+        }
+        if (COMPACT && sub) {
+            uint32_t base;
+            if (chunked) {
+                base = 0;
+                if (lane == 0) base = atomicAdd(&len_next[v], sub);
+                base = __shfl_sync(FULL, base, 0);
+            } else {
+                base = cnt;
+            }
+#pragma unroll
+            for (int i = 0; i < SG; i++) {
+                if (key[i] != 0) {
+                    const uint32_t pos = base + __popc(ball[i] & lt);
+                    a.out_key[s0 + pos] = key[i];
+                    a.out_nbr[s0 + pos] = u[i];
+                }
+                base += __popc(ball[i]);
+            }
+        }
+        cnt += sub;
+    }
+    warp_kv_max(bk, bu);
+    if (!chunked) {
+        if (lane == 0) {
+            if (COMPACT) len_next[v] = cnt;
+            if (bk) va.cnbr[v] = bu;
+        }
+        return;
+    }
+    // chunk of a long row: publish the partial maximum; the last chunk to finish
+    // combines all partials of the row
+    const uint32_t nch = (L + CHUNK - 1) / CHUNK;
+    const uint32_t cbase = task - j_begin / CHUNK;
+    uint32_t old = 0;
+    if (lane == 0) {
+        a.part[task] = make_ulonglong2(bk, bu);
+        __threadfence();
+        old = atomicAdd(&va.bcnt[v], 1u);
+    }
+    old = __shfl_sync(FULL, old, 0);
+    if (old != nch - 1) return;
+    __threadfence();
+    uint64_t k = 0;
+    uint32_t nb = NIL;
+    for (uint32_t q = lane; q < nch; q += 32) {
+        const ulonglong2 p = __ldcg(&a.part[cbase + q]);
+        kv_max(k, nb, p.x, (uint32_t)p.y);
+    }
+    warp_kv_max(k, nb);
+    if (lane == 0) {
+        va.bcnt[v] = 0;
+        if (k) va.cnbr[v] = nb;
+    }
+}
+
+template <bool INPUT, bool COMPACT>
+__device__ void do_tiny(const SweepArgs& a, uint32_t tb, uint32_t nT, int lane) {
+    const VertexArrays& va = a.va;
+    const uint32_t idx = tb * 32 + lane;
+    if (idx >= nT) return;
+    const uint2 tv = a.in.T[idx];
+    const uint32_t v = tv.x, L = tv.y;
+    if (v >= va.nvert || L > TINY_MAX) { set_err(a.st, ERR_BOUNDS, v); return; }
+    const uint32_t s0 = va.start[v];
+    if ((uint64_t)s0 + L > a.ecap) { set_err(a.st, ERR_BOUNDS, v); return; }
+    const Src s = src_of<INPUT>(a, v, s0);
+    uint32_t u[TINY_MAX], e[TINY_MAX];
+#pragma unroll
+    for (uint32_t i = 0; i < TINY_MAX; i++) {
+        u[i] = NIL;
+        e[i] = 0;
+        if (i < L) {
+            u[i] = s.nbr[s.off + i];
+            if (INPUT) e[i] = s.eid[s.off + i];
+        }
+    }
+    bool keep[TINY_MAX];
+#pragma unroll
+    for (uint32_t i = 0; i < TINY_MAX; i++) {
+        keep[i] = u[i] != NIL;
+        if (keep[i]) {
+            if (INPUT) u[i] += s.vbase;
+            if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
+            else if (COMPACT) keep[i] = va.dead[u[i]] == 0;
+        }
+    }
+    uint64_t key[TINY_MAX];
+#pragma unroll
+    for (uint32_t i = 0; i < TINY_MAX; i++) {
+        key[i] = 0;
+        if (keep[i]) {
+            if (INPUT) key[i] = ((uint64_t)s.ordw[s.off + i] << 32) | perm_seed(e[i], s.k0, s.k1);
+            else key[i] = s.key[s.off + i];
+        }
+    }
+    uint32_t cnt = 0;
+    uint64_t bk = 0;
+    uint32_t bu = NIL;
+#pragma unroll
+    for (uint32_t i = 0; i < TINY_MAX; i++) {
+        if (key[i]) {
+            if (COMPACT) {
+                a.out_key[s0 + cnt] = key[i];
+                a.out_nbr[s0 + cnt] = u[i];
+            }
+            cnt++;
+            kv_max(bk, bu, key[i], u[i]);
+        }
+    }
+    if (COMPACT) va.len[a.par ^ 1u][v] = cnt;
+    if (bk) va.cnbr[v] = bu;
+}
+
+template <bool INPUT, bool COMPACT>
+__global__ void __launch_bounds__(ST) k_sweep(const SweepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * ST + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * ST) >> 5;
+    const uint32_t nT = ld_volatile_u32(&a.in.cnt[0]);
+    const uint32_t nM = ld_volatile_u32(&a.in.cnt[1]);
+    const uint32_t nC = ld_volatile_u32(&a.in.cnt[2]);
+    if (nT > a.in.capT || nM > a.in.capM || nC > a.in.capC) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a.st, ERR_BOUNDS, nC);
+        return;
+    }
+    const uint32_t total = nC + nM + (nT + 31) / 32;
+    for (uint32_t t = gw; t < total; t += nw) {
+        if (t < nC) {
+            const uint2 c = a.in.C[t];
+            const uint32_t v = c.x;
+            if (v >= a.va.nvert) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); continue; }
+            const uint32_t L = a.va.len[a.par][v];
+            const uint32_t jb = c.y * CHUNK, je = min(L, jb + CHUNK);
+            if (jb >= L) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); continue; }
+            do_warp_row<INPUT, COMPACT>(a, v, L, jb, je, true, t, lane);
+        } else if (t < nC + nM) {
+            const uint2 mv = a.in.M[t - nC];
+            if (mv.x >= a.va.nvert || mv.y > CHUNK) { if (lane == 0) set_err(a.st, ERR_BOUNDS, mv.x); continue; }
+            do_warp_row<INPUT, COMPACT>(a, mv.x, mv.y, 0, mv.y, false, t, lane);
+        } else {
+            do_tiny<INPUT, COMPACT>(a, t - nC - nM, nT, lane);
         }
     }
 }
@@ -735,27 +547,48 @@ __global__ void k_nonzero_flags(const uint32_t* deg, uint32_t n, uint32_t* flags
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) flags[v] = deg[v] ? 1u : 0u;
 }
 
-__global__ void k_build_rows(const uint32_t* deg, const uint32_t* rowidx, const uint32_t* off_all, uint32_t n,
-                             uint32_t nrows, uint32_t nent, uint32_t* off0, uint32_t* vid0) {
+__global__ void k_build_rows(const uint32_t* deg, const uint32_t* rowidx, uint32_t n, uint32_t* vid0, uint32_t* rdeg0) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         if (deg[v]) {
             const uint32_t i = rowidx[v];
-            off0[i] = off_all[v];
             vid0[i] = v;
+            rdeg0[i] = deg[v];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) off0[nrows] = nent;
 }
 
-__global__ void k_build_tilemap(const uint32_t* off0, uint32_t nrows, uint32_t nent, uint32_t* tilemap) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t ntiles = (nent + SWEEP_T - 1) / SWEEP_T;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += stride) {
-        const uint32_t lo = off0[i], hi = off0[i + 1];
-        for (uint32_t tt = (lo + SWEEP_T - 1) / SWEEP_T; tt < (hi + SWEEP_T - 1) / SWEEP_T; tt++) tilemap[tt] = i;
+__device__ __forceinline__ uint32_t graph_of(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v) {
+    uint32_t lo = 0, hi = ngraphs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (gvbase[mid] <= v) lo = mid; else hi = mid - 1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) tilemap[ntiles] = nrows;
+    return lo;
+}
+
+__global__ void k_union_setup(const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
+                              uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nvert; v += stride) {
+        const uint32_t g = graph_of(gvbase, ngraphs, v);
+        const uint32_t i = v - gvbase[g];
+        const uint32_t* off = offs[g];
+        const uint32_t o0 = off[i], o1 = off[i + 1];
+        start[v] = ebase[g] + o0;
+        gid[v] = g;
+        len0[v] = o1 - o0;
+    }
+}
+
+// serving: vertices [vbase, vbase + n) of one request get their row starts and slot
+__global__ void k_req_setup(const uint32_t* off, uint32_t n, uint32_t vbase, uint32_t ebase, uint32_t slot,
+                            uint32_t* start, uint32_t* gid) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        start[vbase + i] = ebase + off[i];
+        gid[vbase + i] = slot;
+    }
 }
 
 __global__ void k_to_local(const uint32_t* mate_g, uint32_t vbase, uint32_t n, uint32_t* out,
@@ -774,15 +607,6 @@ __global__ void k_to_local(const uint32_t* mate_g, uint32_t vbase, uint32_t n, u
     }
 }
 
-__device__ __forceinline__ uint32_t graph_of(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v) {
-    uint32_t lo = 0, hi = ngraphs - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (gvbase[mid] <= v) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase, uint32_t ngraphs,
                                  uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert) {
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -794,14 +618,6 @@ __global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase,
         if (d) d[v - vb] = (x == NIL) ? NIL : x - vb;
         if (x != NIL && matched2) atomicAdd(&matched2[g], 1ull);
     }
-}
-
-__global__ void k_rows_per_graph(const uint32_t* vid, const DevState* st, uint32_t buf, const uint32_t* gvbase,
-                                 uint32_t ngraphs, uint32_t* rows_per) {
-    const uint32_t R = ld_volatile_u32(&st->cnt[buf][1]);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride)
-        atomicAdd(&rows_per[graph_of(gvbase, ngraphs, vid[i])], 1u);
 }
 
 // ---------------------------------------------------------------- exclusive scan (graph set-up only)
@@ -883,9 +699,8 @@ int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint3
 
 // ---------------------------------------------------------------- launchers
 static int g_sm_count[64];
-static int g_sweep_blocks[64];
 
-static int device_sms(int dev) {
+int device_sm_count(int dev) {
     if (dev < 0 || dev >= 64) return 1;
     if (!g_sm_count[dev]) {
         int c = 0;
@@ -895,71 +710,45 @@ static int device_sms(int dev) {
     return g_sm_count[dev];
 }
 
-template <bool I, bool C>
-static int prep_sweep() {
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<I, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(SweepSmem));
-        if (e != cudaSuccess) return (int)e;
-        done = true;
-    }
-    return 0;
-}
-
-int sweep_grid(int device) {
-    if (device < 0 || device >= 64) return 1;
-    if (!g_sweep_blocks[device]) {
-        prep_sweep<false, true>();
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<false, true>, SWEEP_THREADS, sizeof(SweepSmem));
-        if (per < 1) per = 1;
-        g_sweep_blocks[device] = per * device_sms(device);
-    }
-    return g_sweep_blocks[device];
-}
-
-int vertex_grid(int device) { return device_sms(device) * 8; }
-
-int launch_init(void* stream, uint32_t* mate, uint32_t* cnbr, uint8_t* dead, uint32_t n, DevState* st) {
+static int current_sms() {
     int dev = 0;
     cudaGetDevice(&dev);
-    uint32_t blocks = (n + 255) / 256;
-    const uint32_t cap = (uint32_t)device_sms(dev) * 16;
-    if (blocks > cap) blocks = cap;
-    if (blocks == 0) blocks = 1;
-    k_init<<<blocks, 256, 0, (cudaStream_t)stream>>>(mate, cnbr, dead, n, st);
-    return (int)cudaGetLastError();
+    return device_sm_count(dev);
 }
 
-template <bool I, bool C>
-static int launch_sweep_t(void* stream, const SweepArgs& a, int grid) {
-    int e = prep_sweep<I, C>();
-    if (e) return e;
-    k_sweep<I, C><<<grid, SWEEP_THREADS, sizeof(SweepSmem), (cudaStream_t)stream>>>(a);
-    return (int)cudaGetLastError();
-}
-int launch_sweep_input_cand(void* stream, const SweepArgs& a, int grid) { return launch_sweep_t<true, false>(stream, a, grid); }
-int launch_sweep_input_compact(void* stream, const SweepArgs& a, int grid) { return launch_sweep_t<true, true>(stream, a, grid); }
-int launch_sweep_live(void* stream, const SweepArgs& a, int grid) { return launch_sweep_t<false, true>(stream, a, grid); }
-
-int launch_vertex_all(void* stream, const VertexArgs& a, int grid) {
-    k_vertex_all<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    return (int)cudaGetLastError();
-}
-int launch_vertex_live(void* stream, const VertexArgs& a, int grid) {
-    k_vertex_live<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    return (int)cudaGetLastError();
-}
-
-static uint32_t grid_for(uint64_t n, uint32_t per_block) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t per_sm = 32) {
     uint64_t b = (n + per_block - 1) / per_block;
-    const uint64_t cap = (uint64_t)device_sms(dev) * 32;
+    const uint64_t cap = (uint64_t)current_sms() * per_sm;
     if (b > cap) b = cap;
     return b ? (uint32_t)b : 1u;
 }
+
+int launch_init(void* stream, uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n, DevState* st) {
+    k_init<<<grid_for(n, 256, 16), 256, 0, (cudaStream_t)stream>>>(mate, dead, bcnt, n, st);
+    return (int)cudaGetLastError();
+}
+
+int launch_vertex(void* stream, const VertexArgs& a) {
+    // a fixed grid: the pass iterates its rows block-strided (row counts live on the device)
+    const uint32_t grid = (uint32_t)current_sms() * 4;
+    k_vertex<<<grid, VT, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+template <bool I, bool C>
+static int launch_sweep_t(void* stream, const SweepArgs& a) {
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<I, C>, ST, 0);
+        blocks_per_sm = per > 0 ? per : 1;
+    }
+    k_sweep<I, C><<<current_sms() * blocks_per_sm, ST, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+int launch_sweep_cand(void* stream, const SweepArgs& a) { return launch_sweep_t<true, false>(stream, a); }
+int launch_sweep_input(void* stream, const SweepArgs& a) { return launch_sweep_t<true, true>(stream, a); }
+int launch_sweep_live(void* stream, const SweepArgs& a) { return launch_sweep_t<false, true>(stream, a); }
 
 int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n,
                          uint32_t m, uint32_t* deg, uint32_t* err) {
@@ -967,9 +756,7 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
     return (int)cudaGetLastError();
 }
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      const uint32_t* rowstart_all, uint32_t* cursor, uint32_t* nbr, uint32_t* eid,
-                      uint32_t* ordw) {
-    (void)rowstart_all;
+                      uint32_t* cursor, uint32_t* nbr, uint32_t* eid, uint32_t* ordw) {
     k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, eid, ordw);
     return (int)cudaGetLastError();
 }
@@ -977,14 +764,28 @@ int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t
     k_nonzero_flags<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, n, flags);
     return (int)cudaGetLastError();
 }
-int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, const uint32_t* off_all,
-                      uint32_t n, uint32_t nrows, uint32_t nent, uint32_t* off0, uint32_t* vid0) {
-    k_build_rows<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, rowidx_excl, off_all, n, nrows, nent,
-                                                                      off0, vid0);
+int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, uint32_t n, uint32_t* vid0,
+                      uint32_t* rdeg0) {
+    k_build_rows<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, rowidx_excl, n, vid0, rdeg0);
     return (int)cudaGetLastError();
 }
-int launch_build_tilemap(void* stream, const uint32_t* off0, uint32_t nrows, uint32_t nent, uint32_t* tilemap) {
-    k_build_tilemap<<<grid_for(nrows, 256), 256, 0, (cudaStream_t)stream>>>(off0, nrows, nent, tilemap);
+int launch_union_setup(void* stream, const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
+                       uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
+    if (nvert == 0 || ngraphs == 0) return 0;
+    k_union_setup<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(gvbase, ebase, offs, ngraphs, nvert, start,
+                                                                          gid, len0);
+    return (int)cudaGetLastError();
+}
+int launch_req_setup(void* stream, const uint32_t* off, uint32_t n, uint32_t vbase, uint32_t ebase, uint32_t slot,
+                     uint32_t* start, uint32_t* gid) {
+    if (n == 0) return 0;
+    k_req_setup<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(off, n, vbase, ebase, slot, start, gid);
+    return (int)cudaGetLastError();
+}
+int launch_to_local(void* stream, const uint32_t* mate_global, uint32_t vbase, uint32_t n, uint32_t* out,
+                    unsigned long long* matched2) {
+    if (n == 0) return 0;
+    k_to_local<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(mate_global, vbase, n, out, matched2);
     return (int)cudaGetLastError();
 }
 int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32_t* gvbase, uint32_t ngraphs,
@@ -992,18 +793,6 @@ int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32
     if (nvert == 0 || ngraphs == 0) return 0;
     k_to_local_batch<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(mate_union, gvbase, ngraphs, dst,
                                                                              matched2, nvert);
-    return (int)cudaGetLastError();
-}
-int launch_rows_per_graph(void* stream, const uint32_t* vid, const DevState* st, uint32_t buf,
-                          const uint32_t* gvbase, uint32_t ngraphs, uint32_t* rows_per, int grid) {
-    if (ngraphs == 0) return 0;
-    k_rows_per_graph<<<grid, 256, 0, (cudaStream_t)stream>>>(vid, st, buf, gvbase, ngraphs, rows_per);
-    return (int)cudaGetLastError();
-}
-int launch_to_local(void* stream, const uint32_t* mate_global, uint32_t vbase, uint32_t n, uint32_t* out,
-                    unsigned long long* matched2) {
-    if (n == 0) return 0;
-    k_to_local<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(mate_global, vbase, n, out, matched2);
     return (int)cudaGetLastError();
 }
 

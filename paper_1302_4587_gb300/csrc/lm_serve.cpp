@@ -2,17 +2,22 @@
 //
 // A scheduler thread owns an engine of its own (stream, device state and a
 // workspace sized from the context's HBM budget).  Each scheduler step runs
-// one local-max round for every request in flight, in the same launches:
-//   - requests admitted since the last step run their round 0 (candidate
-//     sweep over their own adjacency arrays, mutual choice, compacting sweep
-//     appended behind the survivors of the requests already in flight);
-//   - requests in flight run their next round on the shared live arrays.
-// A request joins between rounds as soon as its footprint (live entries,
-// rows, a contiguous range of union vertex ids) fits, FIFO, and leaves as
-// soon as it has no live row: its result is converted to local vertex ids
-// and written to the caller's buffer.  Every request keeps its own seed and
-// edge ids, and requests share no vertex, so a result does not depend on
-// what else is in flight.
+// one local-max round for every request in flight, in shared launches:
+//   - requests admitted since the last step run their round 0 (filing of
+//     their rows, candidate sweep over their own adjacency arrays, mutual
+//     choice, compacting sweep into their range of the shared entry space);
+//   - requests already in flight run their next round on the shared arrays.
+// A request joins between rounds as soon as its footprint (a contiguous
+// range of union vertex ids and one of union entries) fits and a slot is
+// free, in arrival order, and leaves after the first round in which it has no
+// live unmatched row: its result is converted to local vertex ids and written
+// to the caller's buffer.  Every request keeps its own seed and edge ids and
+// shares no vertex with another, so its result does not depend on what else
+// is in flight.
+//
+// List sets of the engine: 0 and 1 hold the rows of in-flight requests
+// (alternating by step parity), 2 the rows of fresh requests before their
+// candidate sweep, 3 the round-0 tasks of fresh requests.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,11 +41,46 @@ struct Request {
     uint64_t seed = 0;
     uint32_t* mate = nullptr;
     bool host_dst = false;
-    uint32_t vbase = 0;
+    uint32_t vbase = 0, ebase = 0, slot = 0;
     uint32_t rounds = 0;
     int state = 0;          // 0 queued, 1 in flight, 2 done
     int rc = LM_OK;
     uint64_t matched = 0;
+};
+
+// first-fit allocator of contiguous id ranges
+struct RangeAlloc {
+    std::map<uint32_t, uint32_t> free_;  // first id -> length
+    void init(uint32_t cap) { free_.clear(); if (cap) free_[0] = cap; }
+    bool alloc(uint32_t n, uint32_t* out) {
+        if (n == 0) { *out = 0; return true; }
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *out = it->first;
+                const uint32_t st = it->first + n, len = it->second - n;
+                free_.erase(it);
+                if (len) free_[st] = len;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint32_t start, uint32_t n) {
+        if (n == 0) return;
+        auto it = free_.emplace(start, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
 };
 
 struct ServeState {
@@ -54,48 +94,16 @@ struct ServeState {
     uint64_t next_ticket = 1;
     std::deque<Request*> queue;
     std::vector<Request*> active;
+    std::vector<uint32_t> free_slots;
     std::unordered_map<uint64_t, Request*> all;
-    uint32_t cap_v = 0, cap_e = 0, cap_r = 0, cap_t = 0;
-    uint64_t used_e = 0, used_r = 0;
-    std::map<uint32_t, uint32_t> free_v;  // first vertex -> length
-    uint32_t cur_buf = 0;
-    bool live_any = false;
+    uint32_t cap_v = 0, cap_e = 0;
+    RangeAlloc vspace, espace;
+    uint32_t step = 0;
 };
 
 namespace {
 
 constexpr size_t MAX_QUEUE = 1u << 20;
-
-bool alloc_range(ServeState* S, uint32_t n, uint32_t* out) {
-    if (n == 0) { *out = 0; return true; }
-    for (auto it = S->free_v.begin(); it != S->free_v.end(); ++it) {
-        if (it->second >= n) {
-            *out = it->first;
-            const uint32_t start = it->first + n, len = it->second - n;
-            S->free_v.erase(it);
-            if (len) S->free_v[start] = len;
-            return true;
-        }
-    }
-    return false;
-}
-
-void free_range(ServeState* S, uint32_t start, uint32_t n) {
-    if (n == 0) return;
-    auto it = S->free_v.emplace(start, n).first;
-    auto nx = std::next(it);
-    if (nx != S->free_v.end() && it->first + it->second == nx->first) {
-        it->second += nx->second;
-        S->free_v.erase(nx);
-    }
-    if (it != S->free_v.begin()) {
-        auto pv = std::prev(it);
-        if (pv->first + pv->second == it->first) {
-            pv->second += it->second;
-            S->free_v.erase(it);
-        }
-    }
-}
 
 // One scheduler step (see the file comment).  Returns LM_OK or an error code.
 int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*>& finished) {
@@ -103,100 +111,107 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     Engine& e = S->eng;
     Workspace& w = e.ws;
     cudaStream_t s = e.stream;
-    const uint32_t nvert = S->cap_v;
+    const uint32_t par = S->step & 1u;
+    const VertexArrays va = vertex_arrays(e, S->cap_v, nullptr, true, w.mate);
     LM_CK(ctx, cudaMemsetAsync(&e.st->err, 0, 2 * sizeof(uint32_t), s));
 
-    for (Request* r : fresh)
-        if (r->g->n) LM_CK(ctx, launch_init(s, w.mate + r->vbase, w.cnbr + r->vbase, w.dead + r->vbase, r->g->n, nullptr));
-    std::vector<SegDesc> segs;
-    uint32_t tb = 0;
-    for (Request* r : fresh) {
-        if (r->g->nent == 0) continue;
-        segs.push_back(seg_of(r->g, r->seed, r->vbase, tb));
-        tb += r->g->ntiles;
-    }
-    // active requests sorted by their vertex ranges (for the per-request row count)
-    std::vector<Request*> act = S->active;
-    std::sort(act.begin(), act.end(), [](const Request* a, const Request* b) { return a->vbase < b->vbase; });
-    const uint32_t na = (uint32_t)act.size();
-    const size_t seg_bytes = segs.size() * sizeof(SegDesc);
-    const size_t gv_off = (seg_bytes + 255) / 256 * 256;
-    int rc = ensure_pinned(ctx, e, gv_off + (size_t)(na + 1) * 4 + (size_t)na * 4 + 256);
+    // tables of the fresh requests
+    const uint32_t na = (uint32_t)S->active.size();
+    int rc = ensure_pinned(ctx, e, fresh.size() * sizeof(SegIn) + 16 + (size_t)ctx->max_slots * 8);
     if (rc) return rc;
-    char* pin = static_cast<char*>(e.pinned);
-    if (!segs.empty()) {
-        memcpy(pin, segs.data(), seg_bytes);
-        LM_CK(ctx, cudaMemcpyAsync(w.segs, pin, seg_bytes, cudaMemcpyHostToDevice, s));
+    for (Request* r : fresh) {
+        const SegIn sg = seg_of(r->g, r->seed, r->vbase, r->ebase);
+        memcpy(static_cast<char*>(e.pinned) + 0, &sg, sizeof sg);
+        LM_CK(ctx, cudaMemcpyAsync(&w.segs[r->slot], e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
+        // the pinned staging is reused: wait for this small copy before the next one
+        LM_CK(ctx, cudaStreamSynchronize(s));
+        LM_CK(ctx, launch_req_setup(s, r->g->off, r->g->n, r->vbase, r->ebase, r->slot, w.start, w.gid));
+        LM_CK(ctx, launch_init(s, w.mate + r->vbase, w.dead + r->vbase, w.bcnt + r->vbase, r->g->n, nullptr));
     }
-    uint32_t* gv = reinterpret_cast<uint32_t*>(pin + gv_off);
-    for (uint32_t i = 0; i < na; i++) gv[i] = act[i]->vbase;
-    gv[na] = nvert;
-    LM_CK(ctx, cudaMemcpyAsync(w.gvbase, gv, (size_t)(na + 1) * 4, cudaMemcpyHostToDevice, s));
-    LM_CK(ctx, cudaMemsetAsync(w.rows_per, 0, (size_t)std::max(na, 1u) * 4, s));
+    LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
+    LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
 
-    const uint32_t b = S->cur_buf, o = b ^ 1u;
-    SweepArgs in = base_sweep_args(e, nvert);
-    in.segs = w.segs;
-    in.nsegs = (uint32_t)segs.size();
-    in.ntiles_in = tb;
-    if (!segs.empty()) LM_CK(ctx, launch_sweep_input_cand(s, in, e.sweep_grid));
-    if (S->live_any) {
-        VertexArgs vl = base_vertex_args(e, nvert, w.mate);
-        vl.off = w.off[b];
-        vl.vid = w.vid[b];
-        vl.in_buf = b;
-        LM_CK(ctx, launch_vertex_live(s, vl, e.vertex_grid));
-    }
+    // fresh requests: file their rows (set 2) and find their candidates
+    bool any_fresh_edges = false;
     for (Request* r : fresh) {
         if (r->g->nent == 0) continue;
-        VertexArgs va = base_vertex_args(e, nvert, w.mate);
-        va.vbegin = r->vbase;
-        va.vcount = r->g->n;
-        LM_CK(ctx, launch_vertex_all(s, va, e.vertex_grid));
+        any_fresh_edges = true;
+        VertexArgs pre;
+        memset(&pre, 0, sizeof pre);
+        pre.va = va;
+        pre.in = lists_of(e, 2);
+        pre.in.cnt = nullptr;
+        pre.in_set = 4;
+        pre.vlist = r->g->vid;
+        pre.nvlist = r->g->nrows;
+        pre.vlist_base = r->vbase;
+        pre.deg0 = r->g->rdeg;
+        pre.out = lists_of(e, 2);
+        pre.out_set = 2;
+        pre.par = par;
+        pre.st = e.st;
+        LM_CK(ctx, launch_vertex(s, pre));
     }
-    if (S->live_any) {
-        SweepArgs l = base_sweep_args(e, nvert);
-        l.in_key = w.key[b];
-        l.in_nbr = w.nbr[b];
-        l.in_off = w.off[b];
-        l.in_vid = w.vid[b];
-        l.in_tilemap = w.tilemap;
-        l.in_buf = b;
-        l.out_key = w.key[o];
-        l.out_nbr = w.nbr[o];
-        l.out_off = w.off[o];
-        l.out_vid = w.vid[o];
-        l.out_buf = o;
-        LM_CK(ctx, launch_sweep_live(s, l, e.sweep_grid));
-    } else {
-        LM_CK(ctx, cudaMemsetAsync(&e.st->cnt[o][0], 0, 2 * sizeof(uint32_t), s));
-        LM_CK(ctx, cudaMemsetAsync(w.off[o], 0, sizeof(uint32_t), s));
+    SweepArgs sw;
+    memset(&sw, 0, sizeof sw);
+    sw.va = va;
+    sw.par = par;
+    sw.segs = w.segs;
+    sw.ecap = S->cap_e;
+    sw.part = w.part;
+    sw.st = e.st;
+    if (any_fresh_edges) {
+        sw.in = lists_of(e, 2);
+        LM_CK(ctx, launch_sweep_cand(s, sw));
     }
-    if (!segs.empty()) {
-        in.out_key = w.key[o];
-        in.out_nbr = w.nbr[o];
-        in.out_off = w.off[o];
-        in.out_vid = w.vid[o];
-        in.out_buf = o;
-        in.prefix_in = &e.st->cnt[o][0];
-        LM_CK(ctx, launch_sweep_input_compact(s, in, e.sweep_grid));
+    // mutual choice: in-flight rows (sets par and 3), then the fresh rows (set 2 -> set 3)
+    auto vpass = [&](int in_set, int out_set) -> int {
+        VertexArgs v;
+        memset(&v, 0, sizeof v);
+        v.va = va;
+        v.in = lists_of(e, in_set);
+        v.in_set = in_set;
+        v.out = lists_of(e, out_set);
+        v.out_set = out_set;
+        v.par = par;
+        v.round = S->step;
+        v.match = 1;
+        v.glive = w.glive;
+        v.grounds = w.grounds;
+        v.st = e.st;
+        return launch_vertex(s, v);
+    };
+    LM_CK(ctx, vpass(par, par ^ 1u));
+    LM_CK(ctx, vpass(3, par ^ 1u));
+    if (any_fresh_edges) LM_CK(ctx, vpass(2, 3));
+    // sweeps: in-flight rows from the live buffers, fresh rows from their own arrays
+    sw.out_key = w.key[par ^ 1u];
+    sw.out_nbr = w.nbr[par ^ 1u];
+    sw.in = lists_of(e, par ^ 1u);
+    sw.in_key = w.key[par];
+    sw.in_nbr = w.nbr[par];
+    LM_CK(ctx, launch_sweep_live(s, sw));
+    if (any_fresh_edges) {
+        sw.in = lists_of(e, 3);
+        LM_CK(ctx, launch_sweep_input(s, sw));
     }
-    if (na) LM_CK(ctx, launch_rows_per_graph(s, w.vid[o], e.st, o, w.gvbase, na, w.rows_per, e.vertex_grid));
-    uint32_t* rows_h = gv + na + 1;
-    if (na) LM_CK(ctx, cudaMemcpyAsync(rows_h, w.rows_per, (size_t)na * 4, cudaMemcpyDeviceToHost, s));
+    // which requests still have live rows
+    std::vector<uint32_t> glive(ctx->max_slots), gr(ctx->max_slots);
+    LM_CK(ctx, cudaMemcpyAsync(glive.data(), w.glive, (size_t)ctx->max_slots * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+    LM_CK(ctx, cudaMemcpyAsync(gr.data(), w.grounds, (size_t)ctx->max_slots * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaStreamSynchronize(s));
     if (e.st_host->err & ERR_BOUNDS) return fail(ctx, LM_ECUDA, "device index check failed (serving)");
-    if (e.st_host->err & ERR_TIMEOUT) return fail(ctx, LM_ETIMEOUT, "look-back wait timed out (serving)");
-    S->cur_buf = o;
-    S->live_any = e.st_host->cnt[o][0] > 0;
-
-    // requests without live rows are complete
+    if (e.st_host->err & ERR_TIMEOUT) return fail(ctx, LM_ETIMEOUT, "a bounded device wait gave up (serving)");
+    (void)na;
+    // a round counts for a request when it had live rows in this step's vertex passes;
+    // it is complete once no live row is left unmatched
     std::vector<Request*> done;
-    for (uint32_t i = 0; i < na; i++) {
-        Request* r = act[i];
-        if (r->g->nent > 0) r->rounds++;  // fresh requests ran round 0, the others their next round
-        if (rows_h[i] == 0) done.push_back(r);
+    for (Request* r : S->active) {
+        if (gr[r->slot]) r->rounds++;
+        if (glive[r->slot] == 0) done.push_back(r);
     }
     if (!done.empty()) {
         LM_CK(ctx, cudaMemsetAsync(w.gmatched, 0, done.size() * sizeof(unsigned long long), s));
@@ -214,6 +229,7 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         LM_CK(ctx, cudaStreamSynchronize(s));
         for (size_t k = 0; k < done.size(); k++) done[k]->matched = gm[k] / 2;
     }
+    S->step++;
     finished = done;
     return LM_OK;
 }
@@ -226,35 +242,40 @@ void scheduler(ServeState* S) {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
             if (S->stop) return;
-            while (!S->queue.empty() && S->active.size() < S->ctx->max_slots) {
+            while (!S->queue.empty() && !S->free_slots.empty()) {
                 Request* r = S->queue.front();
-                if (S->used_e + r->g->nent > S->cap_e || S->used_r + r->g->nrows > S->cap_r) break;
-                uint32_t vb = 0;
-                if (!alloc_range(S, r->g->n, &vb)) break;
+                uint32_t vb = 0, eb = 0;
+                if (!S->vspace.alloc(r->g->n, &vb)) break;
+                if (!S->espace.alloc(r->g->nent, &eb)) {
+                    S->vspace.release(vb, r->g->n);
+                    break;
+                }
                 S->queue.pop_front();
                 r->vbase = vb;
+                r->ebase = eb;
+                r->slot = S->free_slots.back();
+                S->free_slots.pop_back();
                 r->state = 1;
-                S->used_e += r->g->nent;
-                S->used_r += r->g->nrows;
                 S->active.push_back(r);
                 fresh.push_back(r);
             }
         }
         std::vector<Request*> finished;
-        int rc = S->fatal ? S->fatal : step(S, fresh, finished);
+        const int rc = S->fatal ? S->fatal : step(S, fresh, finished);
         std::lock_guard<std::mutex> lk(S->mu);
         if (rc) {
             // the shared live state is lost: fail every request in flight
             finished = S->active;
             for (Request* r : finished) r->rc = rc;
-            S->live_any = false;
             if (rc == LM_ECUDA) S->fatal = rc;
+            // start over with empty lists
+            cudaMemsetAsync(&S->eng.st->lcnt[0][0], 0, sizeof(S->eng.st->lcnt), S->eng.stream);
         }
         for (Request* r : finished) {
             r->state = 2;
-            free_range(S, r->vbase, r->g->n);
-            S->used_e -= r->g->nent;
-            S->used_r -= r->g->nrows;
+            S->vspace.release(r->vbase, r->g->n);
+            S->espace.release(r->ebase, r->g->nent);
+            S->free_slots.push_back(r->slot);
             S->active.erase(std::find(S->active.begin(), S->active.end(), r));
         }
         if (!finished.empty()) S->cv_done.notify_all();
@@ -273,21 +294,23 @@ int serve_start(lm_ctx* ctx) {
         cudaStreamDestroy(st);
         return rc;
     }
-    // capacities from the budget: live entries 24 B (two 12-byte buffers),
-    // vertices 9 B, rows 16 B, plus look-back records per tile
+    // capacities from the budget: per entry 24 B (two 12-byte buffers) + list and
+    // partial space; per vertex 9 words of vertex state and task lists
     const double B = (double)ctx->budget;
     const double lim = 4.0e9;
-    S->cap_e = (uint32_t)std::min(lim, B * 0.70 / 24.0);
-    S->cap_v = (uint32_t)std::min(lim, B * 0.15 / 9.0);
-    S->cap_r = (uint32_t)std::min((double)S->cap_v, std::min(lim, B * 0.12 / 16.0));
-    S->cap_t = S->cap_e / SWEEP_T + ctx->max_slots + 2;
-    rc = ensure_ws(ctx, S->eng, S->cap_v, S->cap_e, S->cap_r, S->cap_t, ctx->max_slots + 1);
+    S->cap_e = (uint32_t)std::min(lim, B * 0.80 / 25.0);
+    S->cap_v = (uint32_t)std::min(lim, B * 0.15 / 110.0);
+    rc = ensure_ws(ctx, S->eng, S->cap_v, S->cap_e, ctx->max_slots);
     if (rc) {
         engine_free(S->eng);
         cudaStreamDestroy(st);
         return rc;
     }
-    S->free_v[0] = S->cap_v;
+    LM_CK(ctx, cudaMemsetAsync(S->eng.st, 0, sizeof(DevState), st));
+    LM_CK(ctx, cudaStreamSynchronize(st));
+    S->vspace.init(S->cap_v);
+    S->espace.init(S->cap_e);
+    for (uint32_t i = 0; i < ctx->max_slots; i++) S->free_slots.push_back(ctx->max_slots - 1 - i);
     ServeState* raw = S.release();
     ctx->serve = raw;
     raw->th = std::thread(scheduler, raw);
@@ -323,30 +346,25 @@ int lm_submit(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, uin
     if (ctx->poisoned) return LM_ECUDA;
     if (!g || !mate || !ticket) return fail(ctx, LM_EINVAL, "null graph, mate or ticket");
     if (g->ctx->device != ctx->device) return fail(ctx, LM_EINVAL, "graph lives on another device");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != ctx->device) cudaSetDevice(ctx->device);
+    int rc;
     {
         std::lock_guard<std::mutex> lk(ctx->call_mu);
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (cur != ctx->device) cudaSetDevice(ctx->device);
-        int rc = serve_start(ctx);
-        if (cur >= 0 && cur != ctx->device) cudaSetDevice(cur);
-        if (rc) return rc;
+        rc = serve_start(ctx);
     }
+    const bool host_dst = rc == LM_OK && !is_device_ptr(mate);
+    if (cur >= 0 && cur != ctx->device) cudaSetDevice(cur);
+    if (rc) return rc;
     ServeState* S = ctx->serve;
     if (S->fatal) return S->fatal;
-    if (g->n > S->cap_v || g->nent > S->cap_e || g->nrows > S->cap_r)
-        return fail(ctx, LM_ENOMEM, "request exceeds the serving budget");
+    if (g->n > S->cap_v || g->nent > S->cap_e) return fail(ctx, LM_ENOMEM, "request exceeds the serving budget");
     std::unique_ptr<Request> r(new Request());
     r->g = g;
     r->seed = seed;
     r->mate = mate;
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (cur != ctx->device) cudaSetDevice(ctx->device);
-        r->host_dst = !is_device_ptr(mate);
-        if (cur >= 0 && cur != ctx->device) cudaSetDevice(cur);
-    }
+    r->host_dst = host_dst;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->queue.size() >= MAX_QUEUE) return LM_EAGAIN;
     r->ticket = S->next_ticket++;

@@ -11,14 +11,6 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1302_4587_gb300", "csrc")
 
 
-def test_segmented_aggregate_is_a_monoid(tmp_path):
-    exe = str(tmp_path / "agg_check")
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I" + CSRC, os.path.join(ROOT, "tests", "host", "agg_check.cpp"),
-                           "-o", exe])
-    out = subprocess.run([exe], capture_output=True, text=True)
-    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
-
-
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "lm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
