@@ -115,6 +115,8 @@ int engine_init(lm_ctx* ctx, Engine& e, cudaStream_t stream) {
     LM_CK(ctx, cudaMallocHost(&e.st_host, sizeof(DevState)));
     memset(e.st_host, 0, sizeof(DevState));
     LM_CK(ctx, cudaMemcpy(e.st, e.st_host, sizeof(DevState), cudaMemcpyHostToDevice));
+    LM_CK(ctx, cudaMalloc(&e.dargs, ARG_AREA));
+    LM_CK(ctx, cudaMallocHost(&e.hargs, ARG_AREA));
     e.sweep_grid = 0;
     e.vertex_grid = 0;
     return LM_OK;
@@ -127,6 +129,9 @@ void engine_free(Engine& e) {
     if (e.pinned) cudaFreeHost(e.pinned);
     if (e.st) cudaFree(e.st);
     if (e.st_host) cudaFreeHost(e.st_host);
+    if (e.dargs) cudaFree(e.dargs);
+    if (e.hargs) cudaFreeHost(e.hargs);
+    destroy_job_graph(e.graph);
     cudaGetLastError();
     e = Engine();
 }
@@ -263,97 +268,120 @@ static int check_err(lm_ctx* ctx, Engine& e) {
     return LM_OK;
 }
 
-// The local-max loop.  Expects: the segment table in e.ws.segs, the vertex
-// state initialised (launch_init with the DevState), and for batches the
-// union arrays (start, gid, len[0]) set up.  Round r's vertex pass reads list
-// set r & 1 and fills set (r + 1) & 1, which round r's sweep consumes; the
-// live entries alternate between buffers 1 and 0 (round 0 reads the graphs'
-// own arrays).  The host reads the device's "done" flag between chunks of
-// rounds.
+// The local-max loop of one job.  Expects the segment table in e.ws.segs
+// and, for batches, the union arrays (start, gid, len[0]) set up.  Round r's
+// vertex pass reads list set r & 1 and fills set (r + 1) & 1, which round
+// r's sweep consumes; live entries alternate between buffers 1 and 0 (round 0
+// reads the graphs' own arrays).  All kernel arguments are uploaded in one
+// block; by default an executable graph runs the whole job, its round loop a
+// conditional node that repeats while the device has not flagged the edge set
+// empty.  With profiling the same launches are issued one by one on the
+// stream, with events around each, and the host polls between rounds.
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     Workspace& w = e.ws;
     cudaStream_t s = e.stream;
-    if (job.nseg > 0) {
-        // round 0 -- file every row, candidate-only sweep over the input
-        VertexArgs pre;
-        memset(&pre, 0, sizeof pre);
-        pre.va = job.va;
-        pre.in = lists_of(e, 0);
-        pre.in.cnt = nullptr;
-        pre.in_set = 4;
-        pre.vlist = job.vlist;
-        pre.nvlist = job.nvlist;
-        pre.deg0 = job.rdeg;
-        pre.out = lists_of(e, 0);
-        pre.out_set = 0;
-        pre.par = 0;
-        pre.match = 0;
-        pre.st = e.st;
-        prof.begin(LM_K_VERTEX);
-        LM_CK(ctx, launch_vertex(s, pre));
-        prof.end();
-        SweepArgs sw;
-        memset(&sw, 0, sizeof sw);
-        sw.va = job.va;
-        sw.in = lists_of(e, 0);
-        sw.par = 0;
-        sw.segs = w.segs;
-        sw.ecap = job.ecap;
-        sw.part = w.part;
-        sw.st = e.st;
-        prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_cand(s, sw));
-        prof.end();
+    static_assert(sizeof(JobArgs) <= ARG_AREA, "argument area too small");
+    JobArgs& A = *reinterpret_cast<JobArgs*>(e.hargs);
+    memset(&A, 0, sizeof A);
+    A.init.mate = job.va.mate;
+    A.init.dead = job.va.dead;
+    A.init.bcnt = job.va.bcnt;
+    A.init.n = job.va.nvert;
+    A.init.max_rounds = job.nedges + 2;
+    A.init.st = e.st;
+    auto vargs = [&](VertexArgs& v, int in_set, int out_set, uint32_t par, uint32_t match) {
+        v.va = job.va;
+        v.in = lists_of(e, in_set < 4 ? in_set : 0);
+        if (in_set >= 4) v.in.cnt = nullptr;
+        v.in_set = (uint32_t)in_set;
+        v.out = lists_of(e, out_set);
+        v.out_set = (uint32_t)out_set;
+        v.par = par;
+        v.match = match;
+        v.grounds = match ? job.grounds : nullptr;
+        v.st = e.st;
+    };
+    auto sargs = [&](SweepArgs& c, int in_set, uint32_t par, bool input) {
+        c.va = job.va;
+        c.in = lists_of(e, in_set);
+        c.in_set = (uint32_t)in_set;
+        c.par = par;
+        if (input) c.segs = w.segs;
+        else { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
+        c.out_key = w.key[par ^ 1u];
+        c.out_nbr = w.nbr[par ^ 1u];
+        c.ecap = job.ecap;
+        c.part = w.part;
+        c.st = e.st;
+    };
+    // round 0: file every row (set 0), candidates, match (set 0 -> 1), compaction
+    vargs(A.v[0], 4, 0, 0, 0);
+    A.v[0].vlist = job.vlist;
+    A.v[0].nvlist = job.nvlist;
+    A.v[0].deg0 = job.rdeg;
+    sargs(A.s[0], 0, 0, true);
+    vargs(A.v[1], 0, 1, 0, 1);
+    A.v[1].round = 0;
+    sargs(A.s[1], 1, 0, true);
+    // rounds of parity 1 (set 1 -> 0, buffer 1 -> 0) and 0 (set 0 -> 1, buffer 0 -> 1)
+    vargs(A.v[2], 1, 0, 1, 1);
+    A.v[2].round_from_state = 1;
+    sargs(A.s[2], 0, 1, false);
+    vargs(A.v[3], 0, 1, 0, 1);
+    A.v[3].round_from_state = 1;
+    sargs(A.s[3], 1, 0, false);
+    JobArgs* D = reinterpret_cast<JobArgs*>(e.dargs);
+    LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
 
-        uint32_t r = 0, chunk = 4;
-        for (;;) {
-            for (uint32_t k = 0; k < chunk; k++, r++) {
-                const uint32_t par = r & 1u;
-                VertexArgs v;
-                memset(&v, 0, sizeof v);
-                v.va = job.va;
-                v.in = lists_of(e, par);
-                v.in_set = par;
-                v.out = lists_of(e, par ^ 1u);
-                v.out_set = par ^ 1u;
-                v.par = par;
-                v.round = r;
-                v.match = 1;
-                v.grounds = job.grounds;
-                v.st = e.st;
+    if (job.nseg == 0) {
+        prof.begin(LM_K_INIT);
+        LM_CK(ctx, launch_init(s, &D->init));
+        prof.end();
+    } else if (!prof.on) {
+        if (!e.graph) LM_CK(ctx, build_job_graph(D, e.st, &e.graph));
+        LM_CK(ctx, launch_job_graph(e.graph, s));
+        // launches of one job: init, 4 for round 0, then 5 per pair of rounds
+        prof.launches[LM_K_INIT] += 1;
+    } else {
+        prof.begin(LM_K_INIT);
+        LM_CK(ctx, launch_init(s, &D->init));
+        prof.end();
+        prof.begin(LM_K_VERTEX);
+        LM_CK(ctx, launch_vertex(s, &D->v[0]));
+        prof.end();
+        prof.begin(LM_K_SWEEP);
+        LM_CK(ctx, launch_sweep_cand(s, &D->s[0]));
+        prof.end();
+        prof.begin(LM_K_VERTEX);
+        LM_CK(ctx, launch_vertex(s, &D->v[1]));
+        prof.end();
+        prof.begin(LM_K_SWEEP);
+        LM_CK(ctx, launch_sweep_input(s, &D->s[1]));
+        prof.end();
+        for (uint32_t pair = 0;; pair++) {
+            for (int k = 2; k < 4; k++) {
                 prof.begin(LM_K_VERTEX);
-                LM_CK(ctx, launch_vertex(s, v));
+                LM_CK(ctx, launch_vertex(s, &D->v[k]));
                 prof.end();
-                SweepArgs c;
-                memset(&c, 0, sizeof c);
-                c.va = job.va;
-                c.in = lists_of(e, par ^ 1u);
-                c.in_set = par ^ 1u;
-                c.par = par;
-                c.out_key = w.key[par ^ 1u];
-                c.out_nbr = w.nbr[par ^ 1u];
-                c.ecap = job.ecap;
-                c.part = w.part;
-                c.st = e.st;
                 prof.begin(LM_K_SWEEP);
-                if (r == 0) {
-                    c.segs = w.segs;
-                    LM_CK(ctx, launch_sweep_input(s, c));
-                } else {
-                    c.in_key = w.key[par];
-                    c.in_nbr = w.nbr[par];
-                    LM_CK(ctx, launch_sweep_live(s, c));
-                }
+                LM_CK(ctx, launch_sweep_live(s, &D->s[k]));
                 prof.end();
             }
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
-            chunk = std::min<uint32_t>(chunk * 2, 64);
+            if (e.st_host->round > job.nedges + 2) return fail(ctx, LM_ETIMEOUT, "round cap reached");
         }
     }
     LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaStreamSynchronize(s));
+    if (job.nseg && !prof.on) {
+        // kernels the graph ran: round 0 (4), then per pair of rounds 2 vertex + 2 sweep + 1 check
+        const uint32_t pairs = (e.st_host->round >= 1) ? (e.st_host->round - 1) / 2 : 0;
+        prof.launches[LM_K_VERTEX] += 2 + 2 * pairs;
+        prof.launches[LM_K_SWEEP] += 2 + 2 * pairs;
+        prof.launches[LM_K_OTHER] += pairs;
+    }
     return check_err(ctx, e);
 }
 
@@ -567,6 +595,7 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     Job job;
     uint32_t* mate_d = dev_out ? mate : e.ws.mate;
     job.va = vertex_arrays(e, g->n, g->off, false, mate_d);
+    job.nedges = g->m;
     job.ecap = g->nent;
     job.vlist = g->vid;
     job.rdeg = g->rdeg;
@@ -578,9 +607,6 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
         LM_CK(ctx, cudaMemcpyAsync(e.ws.segs, e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
     }
     Prof prof(ctx, s);
-    prof.begin(LM_K_INIT);
-    LM_CK(ctx, launch_init(s, mate_d, e.ws.dead, e.ws.bcnt, g->n, e.st));
-    prof.end();
     rc = run_job(ctx, e, job, prof);
     if (rc) return rc;
     if (!dev_out && g->n > 0) {
@@ -658,11 +684,9 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     prof.begin(LM_K_OTHER);
     LM_CK(ctx, launch_union_setup(s, w.gvbase, w.gebase, w.goff, count, (uint32_t)nv, w.start, w.gid, w.len[0]));
     prof.end();
-    prof.begin(LM_K_INIT);
-    LM_CK(ctx, launch_init(s, w.mate, w.dead, w.bcnt, (uint32_t)nv, e.st));
-    prof.end();
     Job job;
     job.va = vertex_arrays(e, (uint32_t)nv, nullptr, true, w.mate);
+    job.nedges = (uint32_t)(ne / 2);
     job.ecap = (uint32_t)ne;
     job.vlist = nullptr;
     job.rdeg = nullptr;

@@ -48,6 +48,7 @@ struct Workspace {
 };
 
 // Device state + workspace + the stream they are used on.
+constexpr size_t ARG_AREA = 1 << 16;  // bytes of kernel arguments uploaded per call / step
 struct Engine {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -55,6 +56,9 @@ struct Engine {
     DevState* st_host = nullptr;     // pinned mirror
     void* pinned = nullptr;          // pinned staging for tables
     size_t pinned_bytes = 0;
+    char* dargs = nullptr;           // [ARG_AREA] kernel arguments (device)
+    char* hargs = nullptr;           // [ARG_AREA] their pinned staging
+    void* graph = nullptr;           // executable job graph (device-driven round loop)
     Workspace ws;
     int sweep_grid = 0, vertex_grid = 0;
 };
@@ -118,6 +122,7 @@ VertexArrays vertex_arrays(Engine& e, uint32_t nvert, const uint32_t* start, boo
 // The local-max loop over prepared union arrays (see lm_api.cpp).
 struct Job {
     VertexArrays va;
+    uint32_t nedges = 0;             // total edges (the device loop's round cap)
     uint32_t nseg = 0;               // graphs with edges (segment table already on the device)
     uint32_t ecap = 0;               // union entries
     const uint32_t* vlist = nullptr; // round-0 rows: explicit list (single graph) ...

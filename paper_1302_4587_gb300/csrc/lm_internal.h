@@ -28,8 +28,14 @@ namespace lm {
 
 constexpr uint32_t NIL = 0xFFFFFFFFu;
 
-constexpr uint32_t TINY_MAX = 8;     // rows up to this length: one lane per row
-constexpr uint32_t CHUNK = 512;      // rows longer than this are split into chunks of this size
+#ifndef LM_TINY_MAX
+#define LM_TINY_MAX 8
+#endif
+#ifndef LM_CHUNK
+#define LM_CHUNK 512
+#endif
+constexpr uint32_t TINY_MAX = LM_TINY_MAX;  // rows up to this length: one lane per row
+constexpr uint32_t CHUNK = LM_CHUNK;        // rows longer than this are split into chunks of this size
 
 // error bits written to DevState::err by kernels
 constexpr uint32_t ERR_TIMEOUT = 1u;    // a bounded device wait gave up
@@ -59,7 +65,10 @@ struct DevState {
     uint32_t rounds;          // set to r by the vertex pass of round r that found no live row
     uint32_t done;            // 1 once the edge set is empty
     uint32_t live_rows;       // live rows seen by the running vertex pass
-    uint32_t pad;
+    uint32_t round;           // next round of the device-driven loop
+    uint32_t max_rounds;      // the device-driven loop stops (ERR_TIMEOUT) beyond this round ...
+    uint32_t pad2;
+    unsigned long long t0_ns; // ... or LOOP_LIMIT_NS after the job started
     unsigned long long live_ent;   // live entries seen by the running vertex pass
     unsigned long long matched2;   // matched vertices (= 2 |M|)
     uint64_t ring_m[64];      // live edges at the start of round r
@@ -103,6 +112,7 @@ struct VertexArgs {
     uint32_t par;             // round parity: lengths in va.len[par], next ones in va.len[par ^ 1]
     uint32_t round;
     uint32_t match;           // 0 = classification only (before the candidate sweep)
+    uint32_t round_from_state; // 1: the round index is DevState::round (advanced by this pass)
     uint32_t* grounds;        // per-graph rounds: max(round + 1) over graphs with a live row, NULL = none
     uint32_t* glive;          // live unmatched rows per graph seen by this pass, NULL = none
     DevState* st;
@@ -128,15 +138,40 @@ struct SweepArgs {
     DevState* st;
 };
 
+// Arguments of a whole job in device memory, for the device-driven loop:
+// v[0]/s[0] file the rows and find the round-0 candidates, v[1]/s[1] run
+// round 0, v[2]/s[2] and v[3]/s[3] run rounds of parity 1 and 0.
+struct InitArgs {
+    uint32_t* mate;
+    uint8_t* dead;
+    uint32_t* bcnt;
+    uint32_t n;
+    uint32_t max_rounds;
+    DevState* st;
+};
+struct JobArgs {
+    InitArgs init;
+    VertexArgs v[4];
+    SweepArgs s[4];
+};
+constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
+
 // ---------------------------------------------------------------------------
 // Host-callable launchers (defined in lm_kernels.cu).  All return a
 // cudaError_t value as int.
-int launch_init(void* stream, uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n, DevState* st);
-int launch_vertex(void* stream, const VertexArgs& a);
-int launch_sweep_cand(void* stream, const SweepArgs& a);      // round 0, all entries live, candidates only
-int launch_sweep_input(void* stream, const SweepArgs& a);     // round 0 compaction from the input arrays
-int launch_sweep_live(void* stream, const SweepArgs& a);      // rounds >= 1
+// kernel arguments are passed as pointers to device memory
+int launch_init(void* stream, const InitArgs* dargs);
+int launch_vertex(void* stream, const VertexArgs* dargs);
+int launch_sweep_cand(void* stream, const SweepArgs* dargs);   // round 0, all entries live, candidates only
+int launch_sweep_input(void* stream, const SweepArgs* dargs);  // round 0 compaction from the input arrays
+int launch_sweep_live(void* stream, const SweepArgs* dargs);   // rounds >= 1
 int device_sm_count(int device);
+// executable graph that runs a whole job from its arguments in device memory
+// (init, round 0, then a conditional loop of rounds until the device's done
+// flag is set); returns a cudaError_t value
+int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out);
+int launch_job_graph(void* exec, void* stream);
+void destroy_job_graph(void* exec);
 
 // graph construction
 int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n,

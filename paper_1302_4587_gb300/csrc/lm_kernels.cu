@@ -24,6 +24,7 @@
 // from (ord(weight), edge id) on the fly.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 #include "lm_internal.h"
 
 namespace lm {
@@ -80,7 +81,19 @@ __device__ __forceinline__ void warp_kv_max(uint64_t& k, uint32_t& u) {
 }
 
 // ---------------------------------------------------------------- init
-__global__ void k_init(uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n, DevState* st) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_init(const InitArgs* __restrict__ pa) {
+    const InitArgs& A = *pa;
+    uint32_t* mate = A.mate;
+    uint8_t* dead = A.dead;
+    uint32_t* bcnt = A.bcnt;
+    const uint32_t n = A.n;
+    DevState* st = A.st;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         if (mate) mate[v] = NIL;
@@ -93,6 +106,9 @@ __global__ void k_init(uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n
         if (threadIdx.x == 0) {
             st->err = 0; st->err_info = 0; st->rounds = 0; st->done = 0;
             st->live_rows = 0; st->live_ent = 0; st->matched2 = 0;
+            st->round = 1;
+            st->max_rounds = A.max_rounds;
+            st->t0_ns = globaltimer_ns();
         }
     }
 }
@@ -122,7 +138,8 @@ __device__ __forceinline__ void block_excl_scan3(uint32_t& a, uint32_t& b, uint3
     c = pc + ic - c;
 }
 
-__global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
+__global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pav) {
+    const VertexArgs& a = *pav;
     __shared__ uint32_t s_tmp[3 * (VT / 32)];
     __shared__ uint32_t s_base[3];
     __shared__ unsigned long long s_red[3 * (VT / 32)];
@@ -130,6 +147,7 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
     DevState* st = a.st;
     const VertexArrays& va = a.va;
     const uint32_t par = a.par;
+    const uint32_t round = a.round_from_state ? ld_volatile_u32(&st->round) : a.round;
 
     uint32_t nT = 0, nM = 0, nC = 0, total;
     if (a.vlist || !a.in.cnt) {
@@ -143,51 +161,61 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
     unsigned long long my_rows = 0, my_ent = 0, my_match = 0;
 
     for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
-        uint32_t vv[VI], LL[VI], cls[VI];
+        uint32_t vv[VI], LL[VI], cls[VI], uu[VI];
         uint32_t cT = 0, cM = 0, cC = 0;
+        // phase 1: the row's vertex
 #pragma unroll
         for (int i = 0; i < VI; i++) {
             const uint32_t idx = base + i * VT + tid;
             uint32_t v = NIL, L = 0;
-            cls[i] = 0;
             if (idx < total) {
                 if (a.vlist) {
                     v = a.vlist[idx] + a.vlist_base;
-                    if (v < va.nvert) {
-                        if (a.deg0) { L = a.deg0[idx]; va.len[par][v] = L; }
-                        else L = va.len[par][v];
-                    }
+                    if (a.deg0) L = a.deg0[idx];
                 } else if (!a.in.cnt) {
                     v = idx;  // dense range of vertices
-                    L = va.len[par][v];
                 } else if (idx < nC) {
                     const uint2 c = a.in.C[idx];
-                    if (c.y == 0) { v = c.x; if (v < va.nvert) L = va.len[par][v]; }
+                    if (c.y == 0) v = c.x;
                 } else if (idx < nC + nM) {
                     v = a.in.M[idx - nC].x;
-                    if (v < va.nvert) L = va.len[par][v];
                 } else {
                     v = a.in.T[idx - nC - nM].x;
-                    if (v < va.nvert) L = va.len[par][v];
                 }
-                if (v != NIL && v >= va.nvert) { set_err(st, ERR_BOUNDS, v); v = NIL; L = 0; }
+                if (v != NIL && v >= va.nvert) { set_err(st, ERR_BOUNDS, v); v = NIL; }
             }
+            vv[i] = v;
+            LL[i] = L;
+        }
+        // phase 2: its live length
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            if (vv[i] == NIL) continue;
+            if (a.vlist && a.deg0) va.len[par][vv[i]] = LL[i];
+            else LL[i] = va.len[par][vv[i]];
+        }
+        // phase 3: the mutual-choice test (two dependent gathers)
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            uu[i] = NIL;
+            if (a.match && vv[i] != NIL && LL[i] > 0) uu[i] = va.cnbr[vv[i]];
+        }
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            cls[i] = 0;
+            if (uu[i] != NIL && uu[i] >= va.nvert) { set_err(st, ERR_BOUNDS, uu[i]); uu[i] = NIL; }
+            const uint32_t back = (uu[i] != NIL) ? va.cnbr[uu[i]] : NIL;
+            const uint32_t v = vv[i], L = LL[i];
             bool open_row = false;
             if (v != NIL && L > 0) {
                 my_rows++;
                 my_ent += L;
-                bool matched = false;
-                if (a.match) {
-                    const uint32_t u = va.cnbr[v];
-                    if (u >= va.nvert) set_err(st, ERR_BOUNDS, u);
-                    else if (va.cnbr[u] == v) {
-                        va.mate[v] = u;
-                        va.dead[v] = 1;
-                        matched = true;
-                        my_match++;
-                    }
-                }
-                if (!matched) {
+                const bool matched = a.match && back == v;
+                if (matched) {
+                    va.mate[v] = uu[i];
+                    va.dead[v] = 1;
+                    my_match++;
+                } else {
                     open_row = true;
                     if (L <= TINY_MAX) { cls[i] = 1; cT++; }
                     else if (L <= CHUNK) { cls[i] = 2; cM++; }
@@ -202,15 +230,13 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
             if (a.grounds) {
                 const uint32_t g = (v != NIL && L > 0) ? (va.gid ? va.gid[v] : 0u) : NIL;
                 const uint32_t same = __match_any_sync(FULL, g);
-                if (g != NIL && lane == __ffs(same) - 1) atomicMax(&a.grounds[g], a.round + 1);
+                if (g != NIL && lane == __ffs(same) - 1) atomicMax(&a.grounds[g], round + 1);
             }
             if (a.glive) {
                 const uint32_t g = open_row ? (va.gid ? va.gid[v] : 0u) : NIL;
                 const uint32_t same = __match_any_sync(FULL, g);
                 if (g != NIL && lane == __ffs(same) - 1) atomicAdd(&a.glive[g], (uint32_t)__popc(same));
             }
-            vv[i] = v;
-            LL[i] = L;
         }
         // block-aggregated appends to the task lists
         uint32_t tot[3];
@@ -266,10 +292,11 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
             if (a.match) {
                 const uint32_t rows = ld_volatile_u32(&st->live_rows);
                 const unsigned long long ent = *reinterpret_cast<volatile unsigned long long*>(&st->live_ent);
-                if (a.round < 64) { st->ring_m[a.round] = ent / 2; st->ring_n[a.round] = rows; }
-                if (rows == 0 && !st->done) { st->done = 1; st->rounds = a.round; }
+                if (round < 64) { st->ring_m[round] = ent / 2; st->ring_n[round] = rows; }
+                if (rows == 0 && !st->done) { st->done = 1; st->rounds = round; }
                 st->live_rows = 0;
                 st->live_ent = 0;
+                if (a.round_from_state) st->round = round + 1;
             }
             st->exit_v = 0;
             __threadfence();
@@ -280,8 +307,14 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs a) {
 // ---------------------------------------------------------------- sweep
 // Tasks: [0, nC) chunks of long rows, [nC, nC + nM) medium rows,
 // [nC + nM, ...) batches of 32 tiny rows.  Warps take tasks round-robin.
+#ifndef LM_SG
+#define LM_SG 4
+#endif
+#ifndef LM_SWEEP_MINB
+#define LM_SWEEP_MINB 1
+#endif
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
-constexpr int SG = 4;          // groups of 32 entries loaded together
+constexpr int SG = LM_SG;      // groups of 32 entries loaded together by a warp
 
 struct Src {                   // where one row's entries come from
     const uint32_t* nbr;
@@ -312,16 +345,21 @@ __device__ __forceinline__ Src src_of(const SweepArgs& a, uint32_t v, uint32_t s
 template <bool INPUT, bool COMPACT>
 __device__ __forceinline__ void load_groups(const SweepArgs& a, const Src& s, uint32_t j, uint32_t end, int lane,
                                             uint64_t key[SG], uint32_t u[SG]) {
-    uint32_t e[SG];
+    uint32_t e[SG], o[SG];
+    // independent loads first: neighbours, and for round 0 the edge ids (and,
+    // without a deletion test, the weights too)
 #pragma unroll
     for (int i = 0; i < SG; i++) {
         const uint32_t q = j + i * 32 + lane;
         u[i] = NIL;
         key[i] = 0;
         e[i] = 0;
+        o[i] = 0;
         if (q < end) {
             u[i] = __ldcs(s.nbr + s.off + q);
             if (INPUT) e[i] = __ldcs(s.eid + s.off + q);
+            if (INPUT && !COMPACT) o[i] = __ldcs(s.ordw + s.off + q);
+            if (!INPUT && !COMPACT) key[i] = __ldcs(s.key + s.off + q);
         }
     }
     bool keep[SG];
@@ -334,12 +372,19 @@ __device__ __forceinline__ void load_groups(const SweepArgs& a, const Src& s, ui
             else if (COMPACT) keep[i] = a.va.dead[u[i]] == 0;
         }
     }
+    // keys of the surviving entries
 #pragma unroll
     for (int i = 0; i < SG; i++) {
         if (keep[i]) {
             const uint32_t q = j + i * 32 + lane;
-            if (INPUT) key[i] = ((uint64_t)__ldcs(s.ordw + s.off + q) << 32) | perm_seed(e[i], s.k0, s.k1);
-            else key[i] = __ldcs(s.key + s.off + q);
+            if (INPUT) {
+                const uint32_t ow = COMPACT ? __ldcs(s.ordw + s.off + q) : o[i];
+                key[i] = ((uint64_t)ow << 32) | perm_seed(e[i], s.k0, s.k1);
+            } else if (COMPACT) {
+                key[i] = __ldcs(s.key + s.off + q);
+            }
+        } else {
+            key[i] = 0;
         }
     }
 }
@@ -481,7 +526,8 @@ __device__ void do_tiny(const SweepArgs& a, uint32_t tb, uint32_t nT, int lane) 
 }
 
 template <bool INPUT, bool COMPACT>
-__global__ void __launch_bounds__(ST) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __restrict__ pav) {
+    const SweepArgs& a = *pav;
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * ST + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * ST) >> 5;
@@ -723,32 +769,38 @@ static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t per_sm = 32) {
     return b ? (uint32_t)b : 1u;
 }
 
-int launch_init(void* stream, uint32_t* mate, uint8_t* dead, uint32_t* bcnt, uint32_t n, DevState* st) {
-    k_init<<<grid_for(n, 256, 16), 256, 0, (cudaStream_t)stream>>>(mate, dead, bcnt, n, st);
+int launch_init(void* stream, const InitArgs* dargs) {
+    k_init<<<current_sms() * 16, 256, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
 
-int launch_vertex(void* stream, const VertexArgs& a) {
+static uint32_t vertex_grid() { return (uint32_t)current_sms() * 4; }
+
+int launch_vertex(void* stream, const VertexArgs* dargs) {
     // a fixed grid: the pass iterates its rows block-strided (row counts live on the device)
-    const uint32_t grid = (uint32_t)current_sms() * 4;
-    k_vertex<<<grid, VT, 0, (cudaStream_t)stream>>>(a);
+    k_vertex<<<vertex_grid(), VT, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
 
 template <bool I, bool C>
-static int launch_sweep_t(void* stream, const SweepArgs& a) {
+static uint32_t sweep_grid() {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<I, C>, ST, 0);
         blocks_per_sm = per > 0 ? per : 1;
     }
-    k_sweep<I, C><<<current_sms() * blocks_per_sm, ST, 0, (cudaStream_t)stream>>>(a);
+    return (uint32_t)(current_sms() * blocks_per_sm);
+}
+
+template <bool I, bool C>
+static int launch_sweep_t(void* stream, const SweepArgs* dargs) {
+    k_sweep<I, C><<<sweep_grid<I, C>(), ST, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
-int launch_sweep_cand(void* stream, const SweepArgs& a) { return launch_sweep_t<true, false>(stream, a); }
-int launch_sweep_input(void* stream, const SweepArgs& a) { return launch_sweep_t<true, true>(stream, a); }
-int launch_sweep_live(void* stream, const SweepArgs& a) { return launch_sweep_t<false, true>(stream, a); }
+int launch_sweep_cand(void* stream, const SweepArgs* d) { return launch_sweep_t<true, false>(stream, d); }
+int launch_sweep_input(void* stream, const SweepArgs* d) { return launch_sweep_t<true, true>(stream, d); }
+int launch_sweep_live(void* stream, const SweepArgs* d) { return launch_sweep_t<false, true>(stream, d); }
 
 int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n,
                          uint32_t m, uint32_t* deg, uint32_t* err) {
@@ -794,6 +846,102 @@ int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32
     k_to_local_batch<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(mate_union, gvbase, ngraphs, dst,
                                                                              matched2, nvert);
     return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- device-driven loop
+// Decides whether the conditional loop of a job graph runs another pair of
+// rounds: not once the edge set is empty or an error was recorded; after the
+// round cap or LOOP_LIMIT_NS it records ERR_TIMEOUT and stops.
+__global__ void k_loop_check(DevState* st, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    unsigned int go = 1;
+    if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) go = 0;
+    else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
+             globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+        set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, void* func, dim3 grid,
+                              dim3 block, void** params) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = func;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = params;
+    return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out) {
+    *exec_out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return (int)e;
+    cudaGraphNode_t prev = nullptr, node = nullptr;
+    // kernel parameters: one pointer to the arguments in device memory
+    const InitArgs* p_init = &dargs->init;
+    const VertexArgs* pv[4] = {&dargs->v[0], &dargs->v[1], &dargs->v[2], &dargs->v[3]};
+    const SweepArgs* ps[4] = {&dargs->s[0], &dargs->s[1], &dargs->s[2], &dargs->s[3]};
+    void* init_params[1] = {&p_init};
+    void* vparams[4][1], *sparams[4][1];
+    for (int k = 0; k < 4; k++) {
+        vparams[k][0] = &pv[k];
+        sparams[k][0] = &ps[k];
+    }
+    const dim3 vgrid(vertex_grid()), vblock(VT), sblock(ST);
+    do {
+        if ((e = add_kernel(g, &node, prev, (void*)k_init, dim3(current_sms() * 16), dim3(256), init_params))) break;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[0]))) break;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, false>, dim3(sweep_grid<true, false>()), sblock,
+                            sparams[0]))) break;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[1]))) break;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, true>, dim3(sweep_grid<true, true>()), sblock,
+                            sparams[1]))) break;
+        prev = node;
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault))) break;
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        memset(cp_raw, 0, sizeof cp_raw);
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&node, g, &prev, nullptr, 1, &cp))) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t bp = nullptr, bn = nullptr;
+        for (int k = 2; k < 4 && e == cudaSuccess; k++) {
+            if ((e = add_kernel(body, &bn, bp, (void*)k_vertex, vgrid, vblock, vparams[k]))) break;
+            bp = bn;
+            if ((e = add_kernel(body, &bn, bp, (void*)k_sweep<false, true>, dim3(sweep_grid<false, true>()), sblock,
+                                sparams[k]))) break;
+            bp = bn;
+        }
+        if (e) break;
+        void* cparams[2] = {&st, &h};
+        if ((e = add_kernel(body, &bn, bp, (void*)k_loop_check, dim3(1), dim3(32), cparams))) break;
+        cudaGraphExec_t ex = nullptr;
+        if ((e = cudaGraphInstantiate(&ex, g, 0))) break;
+        *exec_out = ex;
+    } while (0);
+    cudaGraphDestroy(g);
+    return (int)e;
+}
+
+int launch_job_graph(void* exec, void* stream) {
+    return (int)cudaGraphLaunch((cudaGraphExec_t)exec, (cudaStream_t)stream);
+}
+
+void destroy_job_graph(void* exec) {
+    if (exec) cudaGraphExecDestroy((cudaGraphExec_t)exec);
 }
 
 }  // namespace lm

@@ -105,6 +105,15 @@ namespace {
 
 constexpr size_t MAX_QUEUE = 1u << 20;
 
+constexpr uint32_t MAX_FRESH = 64;  // admissions per step (kernel arguments of one step fit the argument area)
+
+struct StepArgs {
+    InitArgs init[MAX_FRESH];
+    VertexArgs pre[MAX_FRESH];
+    VertexArgs v_live, v_prev_fresh, v_fresh;
+    SweepArgs cand, s_live, s_fresh;
+};
+
 // One scheduler step (see the file comment).  Returns LM_OK or an error code.
 int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*>& finished) {
     lm_ctx* ctx = S->ctx;
@@ -113,31 +122,29 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     cudaStream_t s = e.stream;
     const uint32_t par = S->step & 1u;
     const VertexArrays va = vertex_arrays(e, S->cap_v, nullptr, true, w.mate);
+    static_assert(sizeof(StepArgs) <= ARG_AREA, "argument area too small");
+    StepArgs& A = *reinterpret_cast<StepArgs*>(e.hargs);
+    StepArgs* D = reinterpret_cast<StepArgs*>(e.dargs);
+    memset(&A, 0, sizeof A);
     LM_CK(ctx, cudaMemsetAsync(&e.st->err, 0, 2 * sizeof(uint32_t), s));
 
     // tables of the fresh requests
     const uint32_t na = (uint32_t)S->active.size();
-    int rc = ensure_pinned(ctx, e, fresh.size() * sizeof(SegIn) + 16 + (size_t)ctx->max_slots * 8);
+    int rc = ensure_pinned(ctx, e, MAX_FRESH * sizeof(SegIn));
     if (rc) return rc;
-    for (Request* r : fresh) {
-        const SegIn sg = seg_of(r->g, r->seed, r->vbase, r->ebase);
-        memcpy(static_cast<char*>(e.pinned) + 0, &sg, sizeof sg);
-        LM_CK(ctx, cudaMemcpyAsync(&w.segs[r->slot], e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
-        // the pinned staging is reused: wait for this small copy before the next one
-        LM_CK(ctx, cudaStreamSynchronize(s));
+    SegIn* segs_h = static_cast<SegIn*>(e.pinned);
+    for (size_t k = 0; k < fresh.size(); k++) {
+        Request* r = fresh[k];
+        segs_h[k] = seg_of(r->g, r->seed, r->vbase, r->ebase);
+        LM_CK(ctx, cudaMemcpyAsync(&w.segs[r->slot], &segs_h[k], sizeof(SegIn), cudaMemcpyHostToDevice, s));
         LM_CK(ctx, launch_req_setup(s, r->g->off, r->g->n, r->vbase, r->ebase, r->slot, w.start, w.gid));
-        LM_CK(ctx, launch_init(s, w.mate + r->vbase, w.dead + r->vbase, w.bcnt + r->vbase, r->g->n, nullptr));
-    }
-    LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
-    LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
-
-    // fresh requests: file their rows (set 2) and find their candidates
-    bool any_fresh_edges = false;
-    for (Request* r : fresh) {
-        if (r->g->nent == 0) continue;
-        any_fresh_edges = true;
-        VertexArgs pre;
-        memset(&pre, 0, sizeof pre);
+        InitArgs& ia = A.init[k];
+        ia.mate = w.mate + r->vbase;
+        ia.dead = w.dead + r->vbase;
+        ia.bcnt = w.bcnt + r->vbase;
+        ia.n = r->g->n;
+        ia.st = nullptr;
+        VertexArgs& pre = A.pre[k];
         pre.va = va;
         pre.in = lists_of(e, 2);
         pre.in.cnt = nullptr;
@@ -150,24 +157,8 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         pre.out_set = 2;
         pre.par = par;
         pre.st = e.st;
-        LM_CK(ctx, launch_vertex(s, pre));
     }
-    SweepArgs sw;
-    memset(&sw, 0, sizeof sw);
-    sw.va = va;
-    sw.par = par;
-    sw.segs = w.segs;
-    sw.ecap = S->cap_e;
-    sw.part = w.part;
-    sw.st = e.st;
-    if (any_fresh_edges) {
-        sw.in = lists_of(e, 2);
-        LM_CK(ctx, launch_sweep_cand(s, sw));
-    }
-    // mutual choice: in-flight rows (sets par and 3), then the fresh rows (set 2 -> set 3)
-    auto vpass = [&](int in_set, int out_set) -> int {
-        VertexArgs v;
-        memset(&v, 0, sizeof v);
+    auto vpass = [&](VertexArgs& v, int in_set, int out_set) {
         v.va = va;
         v.in = lists_of(e, in_set);
         v.in_set = in_set;
@@ -179,22 +170,46 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         v.glive = w.glive;
         v.grounds = w.grounds;
         v.st = e.st;
-        return launch_vertex(s, v);
     };
-    LM_CK(ctx, vpass(par, par ^ 1u));
-    LM_CK(ctx, vpass(3, par ^ 1u));
-    if (any_fresh_edges) LM_CK(ctx, vpass(2, 3));
-    // sweeps: in-flight rows from the live buffers, fresh rows from their own arrays
-    sw.out_key = w.key[par ^ 1u];
-    sw.out_nbr = w.nbr[par ^ 1u];
-    sw.in = lists_of(e, par ^ 1u);
-    sw.in_key = w.key[par];
-    sw.in_nbr = w.nbr[par];
-    LM_CK(ctx, launch_sweep_live(s, sw));
-    if (any_fresh_edges) {
-        sw.in = lists_of(e, 3);
-        LM_CK(ctx, launch_sweep_input(s, sw));
+    vpass(A.v_live, par, par ^ 1u);
+    vpass(A.v_prev_fresh, 3, par ^ 1u);
+    vpass(A.v_fresh, 2, 3);
+    auto sargs = [&](SweepArgs& c, int in_set, bool input) {
+        c.va = va;
+        c.in = lists_of(e, in_set);
+        c.in_set = in_set;
+        c.par = par;
+        c.segs = w.segs;
+        if (!input) { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
+        c.out_key = w.key[par ^ 1u];
+        c.out_nbr = w.nbr[par ^ 1u];
+        c.ecap = S->cap_e;
+        c.part = w.part;
+        c.st = e.st;
+    };
+    sargs(A.cand, 2, true);
+    sargs(A.s_live, par ^ 1u, false);
+    sargs(A.s_fresh, 3, true);
+    LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
+    LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
+    LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
+
+    // fresh requests: reset their vertex state, file their rows (set 2), find their candidates
+    bool any_fresh_edges = false;
+    for (size_t k = 0; k < fresh.size(); k++) {
+        if (fresh[k]->g->n) LM_CK(ctx, launch_init(s, &D->init[k]));
+        if (fresh[k]->g->nent == 0) continue;
+        any_fresh_edges = true;
+        LM_CK(ctx, launch_vertex(s, &D->pre[k]));
     }
+    if (any_fresh_edges) LM_CK(ctx, launch_sweep_cand(s, &D->cand));
+    // mutual choice: in-flight rows (sets par and 3), then the fresh rows (set 2 -> set 3)
+    LM_CK(ctx, launch_vertex(s, &D->v_live));
+    LM_CK(ctx, launch_vertex(s, &D->v_prev_fresh));
+    if (any_fresh_edges) LM_CK(ctx, launch_vertex(s, &D->v_fresh));
+    // sweeps: in-flight rows from the live buffers, fresh rows from their own arrays
+    LM_CK(ctx, launch_sweep_live(s, &D->s_live));
+    if (any_fresh_edges) LM_CK(ctx, launch_sweep_input(s, &D->s_fresh));
     // which requests still have live rows
     std::vector<uint32_t> glive(ctx->max_slots), gr(ctx->max_slots);
     LM_CK(ctx, cudaMemcpyAsync(glive.data(), w.glive, (size_t)ctx->max_slots * sizeof(uint32_t),
@@ -242,7 +257,7 @@ void scheduler(ServeState* S) {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
             if (S->stop) return;
-            while (!S->queue.empty() && !S->free_slots.empty()) {
+            while (!S->queue.empty() && !S->free_slots.empty() && fresh.size() < MAX_FRESH) {
                 Request* r = S->queue.front();
                 uint32_t vb = 0, eb = 0;
                 if (!S->vspace.alloc(r->g->n, &vb)) break;
