@@ -94,13 +94,23 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase) {
+SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase, uint32_t tile_begin) {
     SegIn d;
     memset(&d, 0, sizeof d);
     const uint64_t z = splitmix64_first(seed);
     d.nbr = g->nbr;
-    d.eid = g->eid;
-    d.ordw = g->ordw;
+    d.pk = g->pk;
+    d.edges = g->edges;
+    d.roff = g->roff;
+    d.rvid = g->vid;
+    d.tmap = g->tmap;
+    d.rbits = g->rbits;
+    d.tdesc = g->tdesc;
+    d.m = g->m;
+    d.nrows = g->nrows;
+    d.nent = g->nent;
+    d.ntiles = g->ntiles;
+    d.tile_begin = tile_begin;
     d.ebase = ebase;
     d.vbase = vbase;
     d.k0 = (uint32_t)z;
@@ -156,12 +166,11 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     c.add(&nw.dead, V);
     c.add(&nw.mate, V);
     c.add(&nw.bcnt, V);
+    c.add(&nw.bkey, V);
     for (int k = 0; k < 4; k++) {
-        c.add(&nw.T[k], V);
-        c.add(&nw.M[k], V);
+        c.add(&nw.R[k], V);
         c.add(&nw.C[k], C);
     }
-    c.add(&nw.part, C);
     for (int b = 0; b < 2; b++) {
         c.add(&nw.key[b], E);
         c.add(&nw.nbr[b], E);
@@ -189,8 +198,9 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     nw.block = p;
     nw.bytes = c.total;
     e.ws = nw;
-    // finished-chunk counters start at zero (every sweep leaves them at zero)
+    // long-row slots start at zero (every sweep leaves them at zero)
     LM_CK(ctx, cudaMemsetAsync(e.ws.bcnt, 0, V * sizeof(uint32_t), e.stream));
+    LM_CK(ctx, cudaMemsetAsync(e.ws.bkey, 0, V * sizeof(unsigned long long), e.stream));
     return LM_OK;
 }
 
@@ -208,11 +218,9 @@ int ensure_pinned(lm_ctx* ctx, Engine& e, size_t bytes) {
 
 Lists lists_of(Engine& e, int k) {
     Lists l;
-    l.T = e.ws.T[k];
-    l.M = e.ws.M[k];
+    l.R = e.ws.R[k];
     l.C = e.ws.C[k];
-    l.capT = e.ws.cap_v;
-    l.capM = e.ws.cap_v;
+    l.capR = e.ws.cap_v;
     l.capC = e.ws.cap_c;
     l.cnt = &e.st->lcnt[k][0];
     return l;
@@ -227,6 +235,7 @@ VertexArrays vertex_arrays(Engine& e, uint32_t nvert, const uint32_t* start, boo
     va.dead = e.ws.dead;
     va.mate = mate;
     va.bcnt = e.ws.bcnt;
+    va.bkey = e.ws.bkey;
     va.gid = with_gid ? e.ws.gid : nullptr;
     va.nvert = nvert;
     return va;
@@ -286,6 +295,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     A.init.mate = job.va.mate;
     A.init.dead = job.va.dead;
     A.init.bcnt = job.va.bcnt;
+    A.init.bkey = job.va.bkey;
     A.init.n = job.va.nvert;
     A.init.max_rounds = job.nedges + 2;
     A.init.st = e.st;
@@ -306,30 +316,39 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         c.in = lists_of(e, in_set);
         c.in_set = (uint32_t)in_set;
         c.par = par;
-        if (input) c.segs = w.segs;
-        else { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
+        c.segs = w.segs;
+        c.nsegs = job.nseg;
+        c.task_ctr = &e.st->task[0];
+        if (!input) { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
         c.out_key = w.key[par ^ 1u];
         c.out_nbr = w.nbr[par ^ 1u];
         c.ecap = job.ecap;
-        c.part = w.part;
         c.st = e.st;
     };
-    // round 0: file every row (set 0), candidates, match (set 0 -> 1), compaction
-    vargs(A.v[0], 4, 0, 0, 0);
+    // round 0: candidates over the graphs' own arrays in tiles; match, open rows
+    // filed in set 1; compaction from the input arrays into buffer 1
+    A.r0.va = job.va;
+    A.r0.segs = w.segs;
+    A.r0.nsegs = job.nseg;
+    A.r0.ntiles = job.ntiles;
+    A.r0.st = e.st;
+    vargs(A.v[0], 4, 1, 0, 1);
     A.v[0].vlist = job.vlist;
     A.v[0].nvlist = job.nvlist;
     A.v[0].deg0 = job.rdeg;
-    sargs(A.s[0], 0, 0, true);
-    vargs(A.v[1], 0, 1, 0, 1);
-    A.v[1].round = 0;
-    sargs(A.s[1], 1, 0, true);
-    // rounds of parity 1 (set 1 -> 0, buffer 1 -> 0) and 0 (set 0 -> 1, buffer 0 -> 1)
-    vargs(A.v[2], 1, 0, 1, 1);
+    A.v[0].round = 0;
+    sargs(A.s[0], 1, 0, true);
+    // round 1: set 1 -> 0, buffer 1 -> 0
+    vargs(A.v[1], 1, 0, 1, 1);
+    A.v[1].round_from_state = 1;
+    sargs(A.s[1], 0, 1, false);
+    // rounds of parity 0 (set 0 -> 1, buffer 0 -> 1) and 1 (set 1 -> 0, buffer 1 -> 0)
+    vargs(A.v[2], 0, 1, 0, 1);
     A.v[2].round_from_state = 1;
-    sargs(A.s[2], 0, 1, false);
-    vargs(A.v[3], 0, 1, 0, 1);
+    sargs(A.s[2], 1, 0, false);
+    vargs(A.v[3], 1, 0, 1, 1);
     A.v[3].round_from_state = 1;
-    sargs(A.s[3], 1, 0, false);
+    sargs(A.s[3], 0, 1, false);
     JobArgs* D = reinterpret_cast<JobArgs*>(e.dargs);
     LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
 
@@ -346,17 +365,23 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         prof.begin(LM_K_INIT);
         LM_CK(ctx, launch_init(s, &D->init));
         prof.end();
+        prof.begin(LM_K_SWEEP);
+        LM_CK(ctx, launch_round0(s, &D->r0));
+        prof.end();
+        prof.begin(LM_K_OTHER);
+        LM_CK(ctx, launch_round0_cut(s, &D->r0));
+        prof.end();
         prof.begin(LM_K_VERTEX);
         LM_CK(ctx, launch_vertex(s, &D->v[0]));
         prof.end();
         prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_cand(s, &D->s[0]));
+        LM_CK(ctx, launch_sweep_input(s, &D->s[0]));
         prof.end();
         prof.begin(LM_K_VERTEX);
         LM_CK(ctx, launch_vertex(s, &D->v[1]));
         prof.end();
         prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_input(s, &D->s[1]));
+        LM_CK(ctx, launch_sweep_live(s, &D->s[1]));
         prof.end();
         for (uint32_t pair = 0;; pair++) {
             for (int k = 2; k < 4; k++) {
@@ -370,17 +395,19 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
-            if (e.st_host->round > job.nedges + 2) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            if (e.st_host->round > job.nedges + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
         }
     }
     LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaStreamSynchronize(s));
     if (job.nseg && !prof.on) {
-        // kernels the graph ran: round 0 (4), then per pair of rounds 2 vertex + 2 sweep + 1 check
-        const uint32_t pairs = (e.st_host->round >= 1) ? (e.st_host->round - 1) / 2 : 0;
+        // kernels the graph ran: rounds 0 and 1 (tile candidates + cut rows, 2 vertex passes,
+        // 2 sweeps), then per pair of rounds 2 vertex passes + 2 sweeps + 1 check; round 1
+        // leaves DevState::round at 2 and every later vertex pass advances it
+        const uint32_t pairs = (e.st_host->round >= 2) ? (e.st_host->round - 2) / 2 : 0;
         prof.launches[LM_K_VERTEX] += 2 + 2 * pairs;
-        prof.launches[LM_K_SWEEP] += 2 + 2 * pairs;
-        prof.launches[LM_K_OTHER] += pairs;
+        prof.launches[LM_K_SWEEP] += 3 + 2 * pairs;
+        prof.launches[LM_K_OTHER] += 1 + pairs;
     }
     return check_err(ctx, e);
 }
@@ -538,11 +565,17 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
 
     Carver gc;
     gc.add(&g->off, nn);
-    gc.add(&g->vid, (size_t)g->nrows + 1);
+    // round-0 tiles copy rows [r & ~3, ...) of vid / roff in whole 16-byte words: pad both
+    g->ntiles = (g->nent + TILE0 - 1) / TILE0;
+    gc.add(&g->vid, (size_t)g->nrows + 8);
     gc.add(&g->rdeg, (size_t)g->nrows + 1);
+    gc.add(&g->roff, (size_t)g->nrows + 8);
+    gc.add(&g->tmap, (size_t)g->ntiles + 1);
+    gc.add(&g->rbits, (size_t)g->ntiles * (TILE0 / 32) + 8);
+    gc.add(&g->tdesc, (size_t)g->ntiles + 1);
     gc.add(&g->nbr, (size_t)g->nent + 4);
-    gc.add(&g->eid, (size_t)g->nent + 4);
-    gc.add(&g->ordw, (size_t)g->nent + 4);
+    gc.add(&g->pk, (size_t)g->nent + 4);
+    gc.add(&g->edges, (size_t)g->m + 2);
     ce = cudaMalloc(&g->block, gc.total);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
     gc.assign(g->block);
@@ -550,9 +583,13 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
     if (m > 0) {
         LM_CK(ctx, cudaMemcpyAsync(cursor, g->off, nn * 4, cudaMemcpyDeviceToDevice, s));
-        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->eid, g->ordw));
+        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges));
     }
-    LM_CK(ctx, launch_build_rows(s, deg, rowidx, n, g->vid, g->rdeg));
+    LM_CK(ctx, launch_build_rows(s, deg, rowidx, g->off, n, g->nrows, g->nent, g->vid, g->rdeg, g->roff));
+    if (g->nrows) {
+        LM_CK(ctx, cudaMemsetAsync(g->rbits, 0, ((size_t)g->ntiles * (TILE0 / 32) + 8) * 4, s));
+        LM_CK(ctx, launch_build_tilemap(s, g->roff, g->nrows, g->nent, g->tmap, g->rbits, g->tdesc));
+    }
     LM_CK(ctx, cudaStreamSynchronize(s));
     *out = g.release();
     return LM_OK;
@@ -601,8 +638,9 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     job.rdeg = g->rdeg;
     job.nvlist = g->nrows;
     job.nseg = g->nent > 0 ? 1 : 0;
+    job.ntiles = g->ntiles;
     if (job.nseg) {
-        const SegIn sg = seg_of(g, seed, 0, 0);
+        const SegIn sg = seg_of(g, seed, 0, 0, 0);
         memcpy(e.pinned, &sg, sizeof sg);
         LM_CK(ctx, cudaMemcpyAsync(e.ws.segs, e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
     }
@@ -649,12 +687,13 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     std::vector<SegIn> segs(count);
     std::vector<uint32_t*> dst(count);
     std::vector<char> host_dst(count);
-    uint32_t vb = 0, eb = 0;
+    uint32_t vb = 0, eb = 0, tb = 0;
     for (uint32_t i = 0; i < count; i++) {
         gvb[i] = vb;
         geb[i] = eb;
         goff[i] = gs[i]->off;
-        segs[i] = seg_of(gs[i], seeds[i], vb, eb);
+        segs[i] = seg_of(gs[i], seeds[i], vb, eb, tb);
+        tb += gs[i]->ntiles;
         host_dst[i] = !is_device_ptr(mates[i]);
         dst[i] = host_dst[i] ? w.cnbr + vb : mates[i];  // host results are staged in the cnbr array
         vb += gs[i]->n;
@@ -692,6 +731,7 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     job.rdeg = nullptr;
     job.nvlist = (uint32_t)nv;
     job.nseg = ne > 0 ? count : 0;
+    job.ntiles = tb;
     job.grounds = w.grounds;
     rc = run_job(ctx, e, job, prof);
     if (rc) return rc;

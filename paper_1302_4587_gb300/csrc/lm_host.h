@@ -28,11 +28,10 @@ struct Workspace {
     uint8_t* dead = nullptr;         // [cap_v] matched flag
     uint32_t* mate = nullptr;        // [cap_v] union result / staging
     uint32_t* bcnt = nullptr;        // [cap_v] finished chunks of long rows
-    // task lists: four sets, each T and M [cap_v] and C [cap_c]
-    uint2* T[4] = {nullptr, nullptr, nullptr, nullptr};
-    uint2* M[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned long long* bkey = nullptr;  // [cap_v] heaviest surviving key of long rows
+    // task lists: four sets, each R [cap_v] and C [cap_c]
+    uint2* R[4] = {nullptr, nullptr, nullptr, nullptr};
     uint2* C[4] = {nullptr, nullptr, nullptr, nullptr};
-    ulonglong2* part = nullptr;      // [cap_c] partial maxima of chunks
     // live entries (ping-pong), union entry space
     uint64_t* key[2] = {nullptr, nullptr};   // [cap_e]
     uint32_t* nbr[2] = {nullptr, nullptr};   // [cap_e]
@@ -83,20 +82,25 @@ struct lm_ctx {
     lm::ServeState* serve = nullptr;
 };
 
-// A device graph (Sec. 2 representation): per-vertex offsets into the
-// adjacency array, whose entries carry the neighbour, the edge index and the
-// order-preserving image of the edge weight.
+// A device graph (Sec. 2 representation): per-vertex offsets V into the
+// adjacency array A, whose entries carry the neighbour and a word with the
+// order-preserving image of the edge weight and the edge index, plus the
+// edge records E (both endpoints of every edge).
 struct lm_graph {
     lm_ctx* ctx = nullptr;
-    uint32_t n = 0, m = 0, nrows = 0, nent = 0;
+    uint32_t n = 0, m = 0, nrows = 0, nent = 0, ntiles = 0;
     void* block = nullptr;
     size_t bytes = 0;
     uint32_t* off = nullptr;         // [n + 1] row offsets of all vertices
-    uint32_t* vid = nullptr;         // [nrows] vertices with at least one edge
+    uint32_t* vid = nullptr;         // [nrows] vertices with at least one edge (the rows)
     uint32_t* rdeg = nullptr;        // [nrows] their degrees
+    uint32_t* roff = nullptr;        // [nrows + 1] entry offset of each row
+    uint32_t* tmap = nullptr;        // [ntiles + 1] row holding entry t * TILE0 (round-0 tiles)
+    uint32_t* rbits = nullptr;       // [ntiles * TILE0 / 32 + 8] row-start bit per entry
+    uint4* tdesc = nullptr;          // [ntiles] round-0 tile descriptors
     uint32_t* nbr = nullptr;         // [2m] neighbour of each entry
-    uint32_t* eid = nullptr;         // [2m] edge index of each entry
-    uint32_t* ordw = nullptr;        // [2m] ord(weight) of each entry
+    uint64_t* pk = nullptr;          // [2m] ord(weight) << 32 | edge index, per entry
+    uint64_t* edges = nullptr;       // [m] edge records eu | ev << 32
 };
 
 namespace lm {
@@ -105,9 +109,10 @@ int fail(lm_ctx* ctx, int code, const char* fmt, ...);
 int cuda_fail(lm_ctx* ctx, cudaError_t e, const char* where);
 bool is_device_ptr(const void* p);
 uint64_t splitmix64_first(uint64_t seed);
-SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase);
-// chunk-list capacity for a union entry space of `ne` entries
-inline uint32_t chunks_cap(uint64_t ne) { return (uint32_t)(2 * (ne / CHUNK) + 64); }
+SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase, uint32_t tile_begin);
+// chunk-list capacity for a union entry space of `ne` entries: every row longer
+// than RMAX adds at most one partial chunk to its ne / CHUNK full ones
+inline uint32_t chunks_cap(uint64_t ne) { return (uint32_t)(ne / CHUNK + ne / (RMAX + 1) + 64); }
 
 int engine_init(lm_ctx* ctx, Engine& e, cudaStream_t stream);
 void engine_free(Engine& e);
@@ -125,9 +130,10 @@ struct Job {
     uint32_t nedges = 0;             // total edges (the device loop's round cap)
     uint32_t nseg = 0;               // graphs with edges (segment table already on the device)
     uint32_t ecap = 0;               // union entries
-    const uint32_t* vlist = nullptr; // round-0 rows: explicit list (single graph) ...
+    const uint32_t* vlist = nullptr; // rows: explicit list (single graph) ...
     const uint32_t* rdeg = nullptr;
     uint32_t nvlist = 0;             // ... or, with vlist == NULL, the dense range [0, nvlist)
+    uint32_t ntiles = 0;             // round-0 tiles of all graphs
     uint32_t* grounds = nullptr;
 };
 // Per-kernel CUDA-event timing of one call (LM_F_PROFILE); NULL-safe helpers.

@@ -8,10 +8,13 @@
 //     graph's entry base.  The row never moves: in every round its surviving
 //     entries are compacted to the front of the same range of the other
 //     ping-pong buffer, and len[round & 1][v] says how many there are.
-//   * a round works from three task lists built by the vertex pass:
-//       T  rows with 1..TINY_MAX live entries   (one lane per row)
-//       M  rows with TINY_MAX+1..CHUNK entries  (one warp per row)
-//       C  chunks of CHUNK entries of longer rows (one warp per chunk)
+//   * a round works from two task lists built by the vertex pass:
+//       R  rows with 1..RMAX live entries (a warp takes 32 rows and walks
+//          their entries as one flattened sequence)
+//       C  chunks of up to CHUNK entries of longer rows (one warp per chunk)
+//   * a row keeps only the heaviest surviving key; the neighbour over that
+//     edge is recovered from the key itself: its low half is perm_seed(e),
+//     which is inverted to the edge index e, whose record holds both ends.
 #pragma once
 #include <stdint.h>
 #include <stddef.h>
@@ -28,14 +31,18 @@ namespace lm {
 
 constexpr uint32_t NIL = 0xFFFFFFFFu;
 
-#ifndef LM_TINY_MAX
-#define LM_TINY_MAX 8
-#endif
 #ifndef LM_CHUNK
 #define LM_CHUNK 512
 #endif
-constexpr uint32_t TINY_MAX = LM_TINY_MAX;  // rows up to this length: one lane per row
-constexpr uint32_t CHUNK = LM_CHUNK;        // rows longer than this are split into chunks of this size
+#ifndef LM_RMAX
+#define LM_RMAX 64
+#endif
+constexpr uint32_t CHUNK = LM_CHUNK;        // long rows are split into chunks of this size
+#ifndef LM_TILE0
+#define LM_TILE0 1024
+#endif
+constexpr uint32_t TILE0 = LM_TILE0;        // round 0 streams the input adjacency in tiles of this many entries
+constexpr uint32_t RMAX = LM_RMAX;          // rows up to this length are batched 32 to a warp
 
 // error bits written to DevState::err by kernels
 constexpr uint32_t ERR_TIMEOUT = 1u;    // a bounded device wait gave up
@@ -46,20 +53,20 @@ LM_HD void kv_max(uint64_t& k, uint32_t& u, uint64_t k2, uint32_t u2) {
     if (k2 > k) { k = k2; u = u2; }
 }
 
-// Task lists of one round: T and M hold (vertex, live length) pairs, C holds
+// Task lists of one round: R holds (vertex, live length) pairs, C holds
 // (vertex, chunk index) pairs; a row's chunks are consecutive in C.
 struct Lists {
-    uint2* T;
-    uint2* M;
+    uint2* R;
     uint2* C;
-    uint32_t capT, capM, capC;
-    uint32_t* cnt;            // device counters {nT, nM, nC}
+    uint32_t capR, capC;
+    uint32_t* cnt;            // device counters {nR, nC}
 };
 
 // Device-side control block (one per engine).
 struct DevState {
-    uint32_t lcnt[4][4];      // counters {nT, nM, nC, -} of the four list sets
+    uint32_t lcnt[4][4];      // counters {nR, nC, -, -} of the four list sets
     uint32_t exit_v, exit_s;  // CTAs of the running vertex pass / sweep that have finished
+    uint32_t task[4];         // task counters of the sweeps that follow a vertex pass
     uint32_t err;             // ERR_* bits
     uint32_t err_info;        // first failing index (debug aid)
     uint32_t rounds;          // set to r by the vertex pass of round r that found no live row
@@ -75,11 +82,20 @@ struct DevState {
     uint64_t ring_n[64];      // live vertices at the start of round r
 };
 
-// Input adjacency arrays of one graph (read by round 0).
+// Arrays of one graph: round 0 reads its adjacency entries, every round
+// recovers candidate neighbours from its edge records.
 struct SegIn {
     const uint32_t* nbr;      // [2m] neighbour (local id) of each entry of the graph's CSR
-    const uint32_t* eid;      // [2m] edge index of each entry
-    const uint32_t* ordw;     // [2m] ord(weight) of each entry
+    const uint64_t* pk;       // [2m] ord(weight) << 32 | edge index, per entry
+    const uint64_t* edges;    // [m] edge records: eu | ev << 32 (local ids)
+    const uint32_t* roff;     // [nrows + 1] entry offset of each row (rows = vertices with edges)
+    const uint32_t* rvid;     // [nrows] local vertex id of each row
+    const uint32_t* tmap;     // [ntiles + 1] row containing entry t * TILE0; [ntiles] = nrows
+    const uint32_t* rbits;    // [ntiles * TILE0 / 32 + 8] bit j set: a row starts at entry j
+    const uint4* tdesc;       // [ntiles] per round-0 tile: first row, rows touched, first row's offset
+    uint32_t m;               // edges
+    uint32_t nrows, nent;     // rows, entries (2m)
+    uint32_t ntiles, tile_begin;  // round-0 tiles of the graph and the job-wide index of the first
     uint32_t ebase;           // union entry index of the graph's entry 0
     uint32_t vbase;           // union id of the graph's vertex 0
     uint32_t k0, k1;          // perm_seed keys of the graph's seed
@@ -93,6 +109,7 @@ struct VertexArrays {
     uint8_t* dead;            // [N] 1 once matched
     uint32_t* mate;           // [N] result (union ids)
     uint32_t* bcnt;           // [N] chunks of a long row finished in the running sweep
+    unsigned long long* bkey; // [N] heaviest surviving key of a long row (0 between sweeps)
     const uint32_t* gid;      // [N] graph of each vertex (NULL: single graph 0)
     uint32_t nvert;           // N
 };
@@ -127,32 +144,43 @@ struct SweepArgs {
     // LIVE source (rounds >= 1): buffers of the previous round
     const uint64_t* in_key;
     const uint32_t* in_nbr;
-    // INPUT source (round 0): graphs' own adjacency arrays
+    // the graphs' own arrays (round 0 entries; every round: edge records)
     const SegIn* segs;
+    uint32_t nsegs;
+    uint32_t* task_ctr;       // dynamic task counter (zeroed by the preceding vertex pass)
     // destination (compacting sweeps)
     uint64_t* out_key;
     uint32_t* out_nbr;
     uint32_t ecap;            // entries in the union entry space
-    // chunk partial maxima, indexed like in.C
-    ulonglong2* part;
+    DevState* st;
+};
+
+// Round-0 candidates over the graphs' own adjacency arrays in tiles of TILE0 entries.
+struct Round0Args {
+    VertexArrays va;
+    const SegIn* segs;
+    uint32_t nsegs, ntiles;   // graphs, tiles of all graphs
     DevState* st;
 };
 
 // Arguments of a whole job in device memory, for the device-driven loop:
-// v[0]/s[0] file the rows and find the round-0 candidates, v[1]/s[1] run
-// round 0, v[2]/s[2] and v[3]/s[3] run rounds of parity 1 and 0.
+// r0 finds the round-0 candidates, v[0] matches round 0 and files the open
+// rows, s[0] compacts from the input arrays, v[1]/s[1] run round 1, and
+// v[2]/s[2], v[3]/s[3] run rounds of parity 0 and 1.
 struct InitArgs {
     uint32_t* mate;
     uint8_t* dead;
     uint32_t* bcnt;
+    unsigned long long* bkey;
     uint32_t n;
     uint32_t max_rounds;
     DevState* st;
 };
 struct JobArgs {
     InitArgs init;
-    VertexArgs v[4];
-    SweepArgs s[4];
+    Round0Args r0;            // round-0 candidates
+    VertexArgs v[4];          // round 0, round 1, loop rounds of parity 0 and 1
+    SweepArgs s[4];           // round-0 compaction, round 1, loop rounds of parity 0 and 1
 };
 constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
 
@@ -165,6 +193,8 @@ int launch_vertex(void* stream, const VertexArgs* dargs);
 int launch_sweep_cand(void* stream, const SweepArgs* dargs);   // round 0, all entries live, candidates only
 int launch_sweep_input(void* stream, const SweepArgs* dargs);  // round 0 compaction from the input arrays
 int launch_sweep_live(void* stream, const SweepArgs* dargs);   // rounds >= 1
+int launch_round0(void* stream, const Round0Args* dargs);      // round-0 candidates in TMA-fed tiles
+int launch_round0_cut(void* stream, const Round0Args* dargs);  // candidates of rows cut by tile boundaries
 int device_sm_count(int device);
 // executable graph that runs a whole job from its arguments in device memory
 // (init, round 0, then a conditional loop of rounds until the device's done
@@ -180,9 +210,11 @@ int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint3
                           size_t tmp_words);
 size_t exclusive_scan_tmp_words(uint32_t count);
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint32_t* eid, uint32_t* ordw);
-int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, uint32_t n, uint32_t* vid0,
-                      uint32_t* rdeg0);
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges);
+int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, const uint32_t* off,
+                      uint32_t n, uint32_t nrows, uint32_t nent, uint32_t* vid0, uint32_t* rdeg0, uint32_t* roff);
+int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uint32_t nent, uint32_t* tmap,
+                         uint32_t* rbits, uint4* tdesc);
 int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t* flags);
 // union set-up of a batch: for every graph g (vertices [gvbase[g], gvbase[g+1])):
 // start[v] = ebase[g] + off_g[v - gvbase[g]], gid[v] = g, len0[v] = degree

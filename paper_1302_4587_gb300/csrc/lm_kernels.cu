@@ -10,18 +10,20 @@
 //             step 3).  Every other live row is filed into this round's task
 //             lists by its length.  Rows of matched vertices are never read
 //             again: deleting a vertex's edges costs nothing (steps 4-6).
-//   k_sweep   one warp per task: reads the row's live entries, keeps an entry
-//             when its neighbour is unmatched, writes the survivors to the
-//             front of the row's range in the other buffer, and takes the
-//             maximum key of the survivors -- the row's candidate for the
-//             next round (step 2 of the next round; the segmented maximum of
-//             Lemma "broadcast" restricted to one row).
+//   k_sweep   warps take tasks (32 rows walked as one flattened sequence of
+//             entries, or one chunk of a long row): an entry survives when its
+//             neighbour is unmatched; survivors go to the front of the row's
+//             range in the other buffer, and the heaviest surviving key of the
+//             row is its candidate for the next round (step 2 of the next
+//             round; the segmented maximum of Lemma "broadcast" restricted to
+//             one row).  The candidate's neighbour is recovered from the key:
+//             its low half is perm_seed(e), inverted to the edge index e.
 //
 // Round 0 first files every row (k_vertex without matching), runs a
 // candidate-only sweep over the graphs' own arrays, then the match and a
 // compacting sweep that builds the 64-bit keys
 //     K(e) = ord(w_e) << 32 | perm_seed(e)
-// from (ord(weight), edge id) on the fly.
+// from the per-entry word ord(weight) << 32 | edge id on the fly.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -43,6 +45,30 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 }
 __device__ __forceinline__ uint32_t perm_seed(uint32_t e, uint32_t k0, uint32_t k1) {
     return fmix32(fmix32(e ^ k0) ^ k1);
+}
+// inverse of x -> x * a (mod 2^32) for odd a, by Newton's iteration
+__host__ __device__ constexpr uint32_t inv_mul(uint32_t a) {
+    uint32_t x = a;  // correct to 3 bits for odd a
+    x *= 2u - a * x;
+    x *= 2u - a * x;
+    x *= 2u - a * x;
+    x *= 2u - a * x;
+    x *= 2u - a * x;
+    return x;
+}
+constexpr uint32_t INV_M1 = inv_mul(0x85EBCA6Bu), INV_M2 = inv_mul(0xC2B2AE35u);
+static_assert(0x85EBCA6Bu * INV_M1 == 1u && 0xC2B2AE35u * INV_M2 == 1u, "modular inverses");
+__device__ __forceinline__ uint32_t fmix32_inv(uint32_t h) {
+    h ^= h >> 16;                       // h ^ (h >> 16) is its own inverse on 32 bits
+    h *= INV_M2;
+    h ^= (h >> 13) ^ (h >> 26);         // inverse of h ^= h >> 13
+    h *= INV_M1;
+    h ^= h >> 16;
+    return h;
+}
+// e = perm_seed^-1(x)
+__device__ __forceinline__ uint32_t perm_seed_inv(uint32_t x, uint32_t k0, uint32_t k1) {
+    return fmix32_inv(fmix32_inv(x) ^ k1) ^ k0;
 }
 // monotone float32 -> uint32 (-0 == +0); NaN is rejected before this runs
 __device__ __forceinline__ uint32_t ord_of_bits(uint32_t b) {
@@ -92,6 +118,7 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
     uint32_t* mate = A.mate;
     uint8_t* dead = A.dead;
     uint32_t* bcnt = A.bcnt;
+    unsigned long long* bkey = A.bkey;
     const uint32_t n = A.n;
     DevState* st = A.st;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -99,10 +126,12 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
         if (mate) mate[v] = NIL;
         dead[v] = 0;
         bcnt[v] = 0;
+        bkey[v] = 0;
     }
     if (st && blockIdx.x == 0) {
         for (int i = threadIdx.x; i < 64; i += blockDim.x) { st->ring_m[i] = 0; st->ring_n[i] = 0; }
         if (threadIdx.x < 16) (&st->lcnt[0][0])[threadIdx.x] = 0;
+        if (threadIdx.x < 4) st->task[threadIdx.x] = 0;
         if (threadIdx.x == 0) {
             st->err = 0; st->err_info = 0; st->rounds = 0; st->done = 0;
             st->live_rows = 0; st->live_ent = 0; st->matched2 = 0;
@@ -115,7 +144,7 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
 
 // ---------------------------------------------------------------- vertex pass
 constexpr int VT = 256;  // threads
-constexpr int VI = 8;    // rows per thread per block iteration
+constexpr int VI = 4;    // rows per thread per block iteration
 
 // exclusive scan of three counters over the block (a, b, c become their
 // prefixes; tot receives the block totals)
@@ -138,7 +167,7 @@ __device__ __forceinline__ void block_excl_scan3(uint32_t& a, uint32_t& b, uint3
     c = pc + ic - c;
 }
 
-__global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pav) {
+__global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__ pav) {
     const VertexArgs& a = *pav;
     __shared__ uint32_t s_tmp[3 * (VT / 32)];
     __shared__ uint32_t s_base[3];
@@ -149,20 +178,19 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
     const uint32_t par = a.par;
     const uint32_t round = a.round_from_state ? ld_volatile_u32(&st->round) : a.round;
 
-    uint32_t nT = 0, nM = 0, nC = 0, total;
+    uint32_t nR = 0, nC = 0, total;
     if (a.vlist || !a.in.cnt) {
         total = a.nvlist;
     } else {
-        nT = ld_volatile_u32(&a.in.cnt[0]);
-        nM = ld_volatile_u32(&a.in.cnt[1]);
-        nC = ld_volatile_u32(&a.in.cnt[2]);
-        total = nC + nM + nT;
+        nR = ld_volatile_u32(&a.in.cnt[0]);
+        nC = ld_volatile_u32(&a.in.cnt[1]);
+        total = nC + nR;
     }
     unsigned long long my_rows = 0, my_ent = 0, my_match = 0;
 
     for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
         uint32_t vv[VI], LL[VI], cls[VI], uu[VI];
-        uint32_t cT = 0, cM = 0, cC = 0;
+        uint32_t cR = 0, cC = 0, cX = 0;
         // phase 1: the row's vertex
 #pragma unroll
         for (int i = 0; i < VI; i++) {
@@ -177,10 +205,8 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
                 } else if (idx < nC) {
                     const uint2 c = a.in.C[idx];
                     if (c.y == 0) v = c.x;
-                } else if (idx < nC + nM) {
-                    v = a.in.M[idx - nC].x;
                 } else {
-                    v = a.in.T[idx - nC - nM].x;
+                    v = a.in.R[idx - nC].x;
                 }
                 if (v != NIL && v >= va.nvert) { set_err(st, ERR_BOUNDS, v); v = NIL; }
             }
@@ -217,10 +243,9 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
                     my_match++;
                 } else {
                     open_row = true;
-                    if (L <= TINY_MAX) { cls[i] = 1; cT++; }
-                    else if (L <= CHUNK) { cls[i] = 2; cM++; }
+                    if (L <= RMAX) { cls[i] = 1; cR++; }
                     else {
-                        cls[i] = 3;
+                        cls[i] = 2;
                         cC += (L + CHUNK - 1) / CHUNK;
                         if (a.match) va.len[par ^ 1][v] = 0;  // long rows gather their survivors atomically
                     }
@@ -240,23 +265,19 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
         }
         // block-aggregated appends to the task lists
         uint32_t tot[3];
-        block_excl_scan3(cT, cM, cC, s_tmp, tot);
+        block_excl_scan3(cR, cC, cX, s_tmp, tot);
         if (tid == 0) {
             s_base[0] = tot[0] ? atomicAdd(&a.out.cnt[0], tot[0]) : 0;
             s_base[1] = tot[1] ? atomicAdd(&a.out.cnt[1], tot[1]) : 0;
-            s_base[2] = tot[2] ? atomicAdd(&a.out.cnt[2], tot[2]) : 0;
         }
         __syncthreads();
-        uint32_t pT = s_base[0] + cT, pM = s_base[1] + cM, pC = s_base[2] + cC;
+        uint32_t pR = s_base[0] + cR, pC = s_base[1] + cC;
 #pragma unroll
         for (int i = 0; i < VI; i++) {
             if (cls[i] == 1) {
-                if (pT < a.out.capT) a.out.T[pT] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pT);
-                pT++;
+                if (pR < a.out.capR) a.out.R[pR] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pR);
+                pR++;
             } else if (cls[i] == 2) {
-                if (pM < a.out.capM) a.out.M[pM] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pM);
-                pM++;
-            } else if (cls[i] == 3) {
                 const uint32_t nch = (LL[i] + CHUNK - 1) / CHUNK;
                 for (uint32_t c = 0; c < nch; c++, pC++) {
                     if (pC < a.out.capC) a.out.C[pC] = make_uint2(vv[i], c); else set_err(st, ERR_BOUNDS, pC);
@@ -288,7 +309,8 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
         const uint32_t done = atomicAdd(&st->exit_v, 1u);
         if (done == gridDim.x - 1) {
             __threadfence();
-            if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; st->lcnt[a.in_set][2] = 0; }
+            if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; }
+            st->task[0] = 0; st->task[1] = 0; st->task[2] = 0; st->task[3] = 0;
             if (a.match) {
                 const uint32_t rows = ld_volatile_u32(&st->live_rows);
                 const unsigned long long ent = *reinterpret_cast<volatile unsigned long long*>(&st->live_ent);
@@ -305,255 +327,592 @@ __global__ void __launch_bounds__(VT) k_vertex(const VertexArgs* __restrict__ pa
 }
 
 // ---------------------------------------------------------------- sweep
-// Tasks: [0, nC) chunks of long rows, [nC, nC + nM) medium rows,
-// [nC + nM, ...) batches of 32 tiny rows.  Warps take tasks round-robin.
+// Tasks: [0, nC) chunks of long rows, then batches of 32 rows of R.
+// Warps take tasks round-robin and never synchronise with each other.
 #ifndef LM_SG
 #define LM_SG 4
 #endif
 #ifndef LM_SWEEP_MINB
-#define LM_SWEEP_MINB 1
+#define LM_SWEEP_MINB 4
 #endif
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
-constexpr int SG = LM_SG;      // groups of 32 entries loaded together by a warp
+constexpr int SG = LM_SG;      // groups of 32 entries a warp keeps in flight
 
-struct Src {                   // where one row's entries come from
-    const uint32_t* nbr;
-    const uint32_t* eid;
-    const uint32_t* ordw;
-    const uint64_t* key;
-    uint32_t off;              // index of the row's entry 0 in those arrays
-    uint32_t vbase, k0, k1;
+struct WarpRows {              // one warp's batch of rows
+    unsigned long long rkey[32];   // heaviest surviving key per row
+    uint32_t rcnt[32];             // survivors per row
+    uint32_t pre[33];              // exclusive prefix of the rows' lengths
+    uint32_t roff[32];             // source index of the row's entry 0
+    uint32_t rstart[32];           // union entry index of the row (output base)
+    uint32_t rseg[32];             // graph of the row
 };
 
+// neighbour of v over the edge with key K (the edge is incident to v): the key's
+// low half is perm_seed(e); its inverse gives e, whose record holds both ends
+__device__ __forceinline__ uint32_t recover_nbr_seg(const SegIn& sg, DevState* st, uint32_t v, uint64_t K) {
+    const uint32_t e = perm_seed_inv((uint32_t)K, sg.k0, sg.k1);
+    if (e >= sg.m) { set_err(st, ERR_BOUNDS, e); return NIL; }
+    const uint64_t rec = sg.edges[e];
+    const uint32_t x = (uint32_t)rec, y = (uint32_t)(rec >> 32), vl = v - sg.vbase;
+    if (x != vl && y != vl) { set_err(st, ERR_BOUNDS, e); return NIL; }
+    return (x == vl ? y : x) + sg.vbase;
+}
+__device__ __forceinline__ uint32_t recover_nbr(const SweepArgs& a, uint32_t v, uint32_t g, uint64_t K) {
+    return recover_nbr_seg(a.segs[g], a.st, v, K);
+}
+
+// key of entry q of a row: the live buffer's key, or ord(w) << 32 | perm_seed(edge id) from the input word
 template <bool INPUT>
-__device__ __forceinline__ Src src_of(const SweepArgs& a, uint32_t v, uint32_t s0) {
-    Src s;
+__device__ __forceinline__ uint64_t entry_key(const SweepArgs& a, uint32_t g, uint32_t q) {
     if (INPUT) {
-        const SegIn& g = a.segs[a.va.gid ? a.va.gid[v] : 0];
-        s.nbr = g.nbr; s.eid = g.eid; s.ordw = g.ordw; s.key = nullptr;
-        s.off = s0 - g.ebase; s.vbase = g.vbase; s.k0 = g.k0; s.k1 = g.k1;
-    } else {
-        s.nbr = a.in_nbr; s.eid = nullptr; s.ordw = nullptr; s.key = a.in_key;
-        s.off = s0; s.vbase = 0; s.k0 = 0; s.k1 = 0;
+        const SegIn& sg = a.segs[g];
+        const uint64_t w = __ldcs(sg.pk + q);
+        return (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, sg.k0, sg.k1);
     }
-    return s;
+    return __ldcs(a.in_key + q);
+}
+template <bool INPUT>
+__device__ __forceinline__ uint32_t entry_nbr(const SweepArgs& a, uint32_t g, uint32_t q) {
+    if (INPUT) {
+        const SegIn& sg = a.segs[g];
+        return __ldcs(sg.nbr + q) + sg.vbase;
+    }
+    return __ldcs(a.in_nbr + q);
 }
 
-// Loads SG groups of a row's entries [j, j + 32*SG) (valid below `end`),
-// applies the deletion test and yields (key, neighbour) per lane and group;
-// key = 0 for entries that are not live.
+// One row batch: 32 rows of R walked as one flattened sequence.
 template <bool INPUT, bool COMPACT>
-__device__ __forceinline__ void load_groups(const SweepArgs& a, const Src& s, uint32_t j, uint32_t end, int lane,
-                                            uint64_t key[SG], uint32_t u[SG]) {
-    uint32_t e[SG], o[SG];
-    // independent loads first: neighbours, and for round 0 the edge ids (and,
-    // without a deletion test, the weights too)
-#pragma unroll
-    for (int i = 0; i < SG; i++) {
-        const uint32_t q = j + i * 32 + lane;
-        u[i] = NIL;
-        key[i] = 0;
-        e[i] = 0;
-        o[i] = 0;
-        if (q < end) {
-            u[i] = __ldcs(s.nbr + s.off + q);
-            if (INPUT) e[i] = __ldcs(s.eid + s.off + q);
-            if (INPUT && !COMPACT) o[i] = __ldcs(s.ordw + s.off + q);
-            if (!INPUT && !COMPACT) key[i] = __ldcs(s.key + s.off + q);
-        }
-    }
-    bool keep[SG];
-#pragma unroll
-    for (int i = 0; i < SG; i++) {
-        keep[i] = u[i] != NIL;
-        if (keep[i]) {
-            if (INPUT) u[i] += s.vbase;
-            if (u[i] >= a.va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-            else if (COMPACT) keep[i] = a.va.dead[u[i]] == 0;
-        }
-    }
-    // keys of the surviving entries
-#pragma unroll
-    for (int i = 0; i < SG; i++) {
-        if (keep[i]) {
-            const uint32_t q = j + i * 32 + lane;
-            if (INPUT) {
-                const uint32_t ow = COMPACT ? __ldcs(s.ordw + s.off + q) : o[i];
-                key[i] = ((uint64_t)ow << 32) | perm_seed(e[i], s.k0, s.k1);
-            } else if (COMPACT) {
-                key[i] = __ldcs(s.key + s.off + q);
-            }
-        } else {
-            key[i] = 0;
-        }
-    }
-}
-
-template <bool INPUT, bool COMPACT>
-__device__ void do_warp_row(const SweepArgs& a, uint32_t v, uint32_t L, uint32_t j_begin, uint32_t j_end,
-                            bool chunked, uint32_t task, int lane) {
+__device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR, int lane) {
     const VertexArrays& va = a.va;
-    const uint32_t s0 = va.start[v];
-    if ((uint64_t)s0 + L > a.ecap) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); return; }
-    const Src s = src_of<INPUT>(a, v, s0);
-    uint32_t* len_next = va.len[a.par ^ 1u];
-    uint32_t cnt = 0;
-    uint64_t bk = 0;
-    uint32_t bu = NIL;
+    const uint32_t idx = b * 32 + lane;
+    uint32_t v = NIL, L = 0, s0 = 0, g = 0;
+    if (idx < nR) {
+        const uint2 rv = a.in.R[idx];
+        v = rv.x;
+        L = rv.y;
+        if (v >= va.nvert || L > RMAX) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
+        else {
+            s0 = va.start[v];
+            g = va.gid ? va.gid[v] : 0u;
+            if ((uint64_t)s0 + L > a.ecap || g >= a.nsegs) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
+        }
+    }
+    W.rkey[lane] = 0;
+    W.rcnt[lane] = 0;
+    W.rstart[lane] = s0;
+    W.rseg[lane] = g;
+    W.roff[lane] = INPUT ? s0 - a.segs[g].ebase : s0;
+    const uint32_t incl = warp_incl_scan(L, lane);
+    W.pre[lane + 1] = incl;
+    if (lane == 0) W.pre[0] = 0;
+    const uint32_t F = __shfl_sync(FULL, incl, 31);
+    __syncwarp();
     const uint32_t lt = lanemask_lt();
-    for (uint32_t j = j_begin; j < j_end; j += 32 * SG) {
+    for (uint32_t f0 = 0; f0 < F; f0 += 32 * SG) {
+        uint32_t r[SG], q[SG], u[SG];
         uint64_t key[SG];
+#pragma unroll
+        for (int i = 0; i < SG; i++) {
+            const uint32_t f = f0 + i * 32 + lane;
+            r[i] = 32;
+            q[i] = 0;
+            u[i] = NIL;
+            key[i] = 0;
+            if (f < F) {
+                uint32_t rr = 0;
+#pragma unroll
+                for (uint32_t step = 16; step > 0; step >>= 1)
+                    if (W.pre[rr + step] <= f) rr += step;
+                r[i] = rr;
+                q[i] = W.roff[rr] + (f - W.pre[rr]);
+            }
+        }
+        // neighbours (deletion test) or, without deletion, the keys directly
+#pragma unroll
+        for (int i = 0; i < SG; i++) {
+            if (r[i] == 32) continue;
+            if (COMPACT) u[i] = entry_nbr<INPUT>(a, W.rseg[r[i]], q[i]);
+            else key[i] = entry_key<INPUT>(a, W.rseg[r[i]], q[i]);
+        }
+        if (COMPACT) {
+            bool keep[SG];
+#pragma unroll
+            for (int i = 0; i < SG; i++) {
+                keep[i] = r[i] != 32;
+                if (keep[i]) {
+                    if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
+                    else keep[i] = va.dead[u[i]] == 0;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < SG; i++)
+                if (keep[i]) key[i] = entry_key<INPUT>(a, W.rseg[r[i]], q[i]);
+        }
+        // per row: compaction slots and maximum, aggregated over the lanes of a row
+#pragma unroll
+        for (int i = 0; i < SG; i++) {
+            const bool surv = key[i] != 0;
+            const uint32_t grp = __match_any_sync(FULL, surv ? r[i] : 64u + lane);
+            if (surv) {
+                const int leader = __ffs(grp) - 1;
+                const uint32_t hi = __reduce_max_sync(grp, (uint32_t)(key[i] >> 32));
+                const uint32_t lo = __reduce_max_sync(grp, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
+                uint32_t base = 0;
+                if (lane == leader) {
+                    if (COMPACT) base = atomicAdd(&W.rcnt[r[i]], (uint32_t)__popc(grp));
+                    atomicMax(&W.rkey[r[i]], ((unsigned long long)hi << 32) | lo);
+                }
+                if (COMPACT) {
+                    base = __shfl_sync(grp, base, leader);
+                    const uint32_t pos = W.rstart[r[i]] + base + __popc(grp & lt);
+                    a.out_key[pos] = key[i];
+                    a.out_nbr[pos] = u[i];
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (v != NIL) {
+        if (COMPACT) va.len[a.par ^ 1u][v] = W.rcnt[lane];
+        const uint64_t K = W.rkey[lane];
+        if (K) va.cnbr[v] = recover_nbr(a, v, g, K);
+    }
+    __syncwarp();
+}
+
+// One chunk of a long row (all lanes on the same row).
+template <bool INPUT, bool COMPACT>
+__device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
+    const VertexArrays& va = a.va;
+    const uint2 c = a.in.C[t];
+    const uint32_t v = c.x;
+    if (v >= va.nvert) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); return; }
+    const uint32_t L = va.len[a.par][v];
+    const uint32_t jb = c.y * CHUNK, je = min(L, jb + CHUNK);
+    const uint32_t s0 = va.start[v];
+    const uint32_t g = va.gid ? va.gid[v] : 0u;
+    if (jb >= L || (uint64_t)s0 + L > a.ecap || g >= a.nsegs) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); return; }
+    const uint32_t off = INPUT ? s0 - a.segs[g].ebase : s0;
+    uint32_t* len_next = va.len[a.par ^ 1u];
+    uint64_t bk = 0;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t j = jb; j < je; j += 32 * SG) {
         uint32_t u[SG];
-        load_groups<INPUT, COMPACT>(a, s, j, j_end, lane, key, u);
+        uint64_t key[SG];
+#pragma unroll
+        for (int i = 0; i < SG; i++) {
+            const uint32_t jj = j + i * 32 + lane;
+            u[i] = NIL;
+            key[i] = 0;
+            if (jj < je) {
+                if (COMPACT) u[i] = entry_nbr<INPUT>(a, g, off + jj);
+                else key[i] = entry_key<INPUT>(a, g, off + jj);
+            }
+        }
+        if (COMPACT) {
+            bool keep[SG];
+#pragma unroll
+            for (int i = 0; i < SG; i++) {
+                keep[i] = u[i] != NIL;
+                if (keep[i]) {
+                    if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
+                    else keep[i] = va.dead[u[i]] == 0;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < SG; i++)
+                if (keep[i]) key[i] = entry_key<INPUT>(a, g, off + j + i * 32 + lane);
+        }
         uint32_t ball[SG], sub = 0;
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             ball[i] = __ballot_sync(FULL, key[i] != 0);
             sub += __popc(ball[i]);
-            kv_max(bk, bu, key[i], u[i]);
+            if (key[i] > bk) bk = key[i];
         }
         if (COMPACT && sub) {
-            uint32_t base;
-            if (chunked) {
-                base = 0;
-                if (lane == 0) base = atomicAdd(&len_next[v], sub);
-                base = __shfl_sync(FULL, base, 0);
-            } else {
-                base = cnt;
-            }
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&len_next[v], sub);
+            base = __shfl_sync(FULL, base, 0);
 #pragma unroll
             for (int i = 0; i < SG; i++) {
                 if (key[i] != 0) {
-                    const uint32_t pos = base + __popc(ball[i] & lt);
-                    a.out_key[s0 + pos] = key[i];
-                    a.out_nbr[s0 + pos] = u[i];
+                    const uint32_t pos = s0 + base + __popc(ball[i] & lt);
+                    a.out_key[pos] = key[i];
+                    a.out_nbr[pos] = u[i];
                 }
                 base += __popc(ball[i]);
             }
         }
-        cnt += sub;
     }
-    warp_kv_max(bk, bu);
-    if (!chunked) {
-        if (lane == 0) {
-            if (COMPACT) len_next[v] = cnt;
-            if (bk) va.cnbr[v] = bu;
-        }
-        return;
-    }
-    // chunk of a long row: publish the partial maximum; the last chunk to finish
-    // combines all partials of the row
-    const uint32_t nch = (L + CHUNK - 1) / CHUNK;
-    const uint32_t cbase = task - j_begin / CHUNK;
-    uint32_t old = 0;
+    // chunk maximum into the row's slot; the last chunk of the row to finish
+    // reads the row maximum and recovers its neighbour
+    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(bk >> 32));
+    const uint32_t lo = __reduce_max_sync(FULL, ((uint32_t)(bk >> 32) == hi) ? (uint32_t)bk : 0u);
     if (lane == 0) {
-        a.part[task] = make_ulonglong2(bk, bu);
+        const uint64_t K = ((uint64_t)hi << 32) | lo;
+        if (K) atomicMax(&va.bkey[v], (unsigned long long)K);
         __threadfence();
-        old = atomicAdd(&va.bcnt[v], 1u);
-    }
-    old = __shfl_sync(FULL, old, 0);
-    if (old != nch - 1) return;
-    __threadfence();
-    uint64_t k = 0;
-    uint32_t nb = NIL;
-    for (uint32_t q = lane; q < nch; q += 32) {
-        const ulonglong2 p = __ldcg(&a.part[cbase + q]);
-        kv_max(k, nb, p.x, (uint32_t)p.y);
-    }
-    warp_kv_max(k, nb);
-    if (lane == 0) {
-        va.bcnt[v] = 0;
-        if (k) va.cnbr[v] = nb;
-    }
-}
-
-template <bool INPUT, bool COMPACT>
-__device__ void do_tiny(const SweepArgs& a, uint32_t tb, uint32_t nT, int lane) {
-    const VertexArrays& va = a.va;
-    const uint32_t idx = tb * 32 + lane;
-    if (idx >= nT) return;
-    const uint2 tv = a.in.T[idx];
-    const uint32_t v = tv.x, L = tv.y;
-    if (v >= va.nvert || L > TINY_MAX) { set_err(a.st, ERR_BOUNDS, v); return; }
-    const uint32_t s0 = va.start[v];
-    if ((uint64_t)s0 + L > a.ecap) { set_err(a.st, ERR_BOUNDS, v); return; }
-    const Src s = src_of<INPUT>(a, v, s0);
-    uint32_t u[TINY_MAX], e[TINY_MAX];
-#pragma unroll
-    for (uint32_t i = 0; i < TINY_MAX; i++) {
-        u[i] = NIL;
-        e[i] = 0;
-        if (i < L) {
-            u[i] = s.nbr[s.off + i];
-            if (INPUT) e[i] = s.eid[s.off + i];
+        const uint32_t nch = (L + CHUNK - 1) / CHUNK;
+        const uint32_t old = atomicAdd(&va.bcnt[v], 1u);
+        if (old == nch - 1) {
+            __threadfence();
+            const uint64_t R = *reinterpret_cast<volatile unsigned long long*>(&va.bkey[v]);
+            va.bkey[v] = 0;
+            va.bcnt[v] = 0;
+            if (R) va.cnbr[v] = recover_nbr(a, v, g, R);
         }
     }
-    bool keep[TINY_MAX];
-#pragma unroll
-    for (uint32_t i = 0; i < TINY_MAX; i++) {
-        keep[i] = u[i] != NIL;
-        if (keep[i]) {
-            if (INPUT) u[i] += s.vbase;
-            if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-            else if (COMPACT) keep[i] = va.dead[u[i]] == 0;
-        }
-    }
-    uint64_t key[TINY_MAX];
-#pragma unroll
-    for (uint32_t i = 0; i < TINY_MAX; i++) {
-        key[i] = 0;
-        if (keep[i]) {
-            if (INPUT) key[i] = ((uint64_t)s.ordw[s.off + i] << 32) | perm_seed(e[i], s.k0, s.k1);
-            else key[i] = s.key[s.off + i];
-        }
-    }
-    uint32_t cnt = 0;
-    uint64_t bk = 0;
-    uint32_t bu = NIL;
-#pragma unroll
-    for (uint32_t i = 0; i < TINY_MAX; i++) {
-        if (key[i]) {
-            if (COMPACT) {
-                a.out_key[s0 + cnt] = key[i];
-                a.out_nbr[s0 + cnt] = u[i];
-            }
-            cnt++;
-            kv_max(bk, bu, key[i], u[i]);
-        }
-    }
-    if (COMPACT) va.len[a.par ^ 1u][v] = cnt;
-    if (bk) va.cnbr[v] = bu;
 }
 
 template <bool INPUT, bool COMPACT>
 __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __restrict__ pav) {
+    __shared__ WarpRows s_rows[ST / 32];
     const SweepArgs& a = *pav;
     const int lane = threadIdx.x & 31;
+    WarpRows& W = s_rows[threadIdx.x >> 5];
     const uint32_t gw = (blockIdx.x * ST + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * ST) >> 5;
-    const uint32_t nT = ld_volatile_u32(&a.in.cnt[0]);
-    const uint32_t nM = ld_volatile_u32(&a.in.cnt[1]);
-    const uint32_t nC = ld_volatile_u32(&a.in.cnt[2]);
-    if (nT > a.in.capT || nM > a.in.capM || nC > a.in.capC) {
+    const uint32_t nR = ld_volatile_u32(&a.in.cnt[0]);
+    const uint32_t nC = ld_volatile_u32(&a.in.cnt[1]);
+    if (nR > a.in.capR || nC > a.in.capC) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a.st, ERR_BOUNDS, nC);
         return;
     }
-    const uint32_t total = nC + nM + (nT + 31) / 32;
-    for (uint32_t t = gw; t < total; t += nw) {
-        if (t < nC) {
-            const uint2 c = a.in.C[t];
-            const uint32_t v = c.x;
-            if (v >= a.va.nvert) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); continue; }
-            const uint32_t L = a.va.len[a.par][v];
-            const uint32_t jb = c.y * CHUNK, je = min(L, jb + CHUNK);
-            if (jb >= L) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); continue; }
-            do_warp_row<INPUT, COMPACT>(a, v, L, jb, je, true, t, lane);
-        } else if (t < nC + nM) {
-            const uint2 mv = a.in.M[t - nC];
-            if (mv.x >= a.va.nvert || mv.y > CHUNK) { if (lane == 0) set_err(a.st, ERR_BOUNDS, mv.x); continue; }
-            do_warp_row<INPUT, COMPACT>(a, mv.x, mv.y, 0, mv.y, false, t, lane);
-        } else {
-            do_tiny<INPUT, COMPACT>(a, t - nC - nM, nT, lane);
+    const uint32_t total = nC + (nR + 31) / 32;
+    (void)gw; (void)nw;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.task_ctr, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= total) break;
+        if (t < nC) do_chunk<INPUT, COMPACT>(a, t, lane);
+        else do_rows<INPUT, COMPACT>(a, W, t - nC, nR, lane);
+    }
+}
+
+// ---------------------------------------------------------------- round-0 candidates in TMA-fed tiles
+// Round 0's candidate pass reads every graph's own adjacency array once, front
+// to back, in tiles of TILE0 entries; a CTA owns tiles blockIdx.x, +gridDim.x,
+// ...  One producer thread copies a tile's entry words and neighbours, the
+// vertices of the rows it touches and its slice of the graph's row-start
+// bitmap into a shared-memory stage with bulk asynchronous copies completed on
+// the stage's "full" mbarrier; tile descriptors (precomputed per graph) are
+// loaded R0AHEAD tiles early and the copies run up to R0S stages ahead of the
+// consumers.  The consumer warps derive each entry's row from the bitmap
+// (prefix counts of row starts), maximise keys per row in shared memory, and
+// let the entry holding a row's maximum name the row's candidate.  Only the
+// first and the last row of a tile can be cut by a tile boundary: their maxima
+// meet in bkey[] and k_round0_cut resolves them after the pass.  A stage goes
+// back to the producer through its "empty" mbarrier; every wait is bounded.
+
+#ifndef LM_R0S
+#define LM_R0S 2
+#endif
+#ifndef LM_R0C
+#define LM_R0C 256
+#endif
+#ifndef LM_R0MINB
+#define LM_R0MINB 3
+#endif
+constexpr int R0S = LM_R0S;                         // pipeline stages
+constexpr int R0C = LM_R0C;                         // consumer threads
+constexpr int R0T = R0C + 32;                       // and one producer warp (one thread of it works)
+constexpr int R0G = (int)TILE0 / R0C;               // 32-entry groups per consumer warp
+constexpr int R0RPT = ((int)TILE0 + 1 + R0C - 1) / R0C;  // rows per consumer thread when finishing
+constexpr int R0W = (int)TILE0 / 32;                // bitmap words of a tile
+constexpr int R0WPL = R0W / 32;                     // bitmap words per lane in the consumers' scan
+constexpr int R0AHEAD = 4;                          // tile descriptors in flight ahead of the copies
+static_assert(TILE0 % 1024 == 0, "tile size: a multiple of 1024 entries");
+static_assert(R0C % 32 == 0 && TILE0 % R0C == 0 && R0G >= 1, "consumer warps must split the tile in 32-entry groups");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+constexpr unsigned long long R0_WAIT_NS = 1000000000ull;
+// wait for the phase of the given parity to complete; false after R0_WAIT_NS
+__device__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > R0_WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// barrier of the consumer warps only (the producer warp never joins it)
+__device__ __forceinline__ void cbar() {
+    asm volatile("bar.sync 1, %0;" :: "n"(R0C) : "memory");
+}
+__device__ __forceinline__ bool cbar_or(bool p) {
+    uint32_t r;
+    asm volatile("{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, 1, %2, p; selp.u32 %0, 1, 0, q; }"
+                 : "=r"(r) : "r"((uint32_t)p), "n"(R0C) : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+struct alignas(16) R0Stage {
+    unsigned long long pk[TILE0];     // entry words (first member: 16-byte aligned)
+    uint32_t nbr[TILE0];              // neighbours
+    uint32_t rvid[TILE0 + 8];         // row vertices from row (r_lo & ~3)
+    uint32_t bits[R0W + 4];           // row-start bits of the tile, then of the next tile's first entries
+    // written by the producer before the copies are issued
+    uint32_t valid, seg, j0, nent, shift;
+};
+struct R0Smem {
+    R0Stage stage[R0S];
+    unsigned long long kmax[TILE0 + 1];   // per row of the current tile: heaviest key
+    uint32_t knbr[TILE0 + 1];             // per row: neighbour over that entry
+    unsigned long long full[R0S], empty[R0S];
+};
+
+__device__ __forceinline__ uint32_t seg_of_tile(const Round0Args& a, uint32_t t) {
+    uint32_t lo = 0, hi = a.nsegs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// where tile t lies: its graph and its descriptor (loaded, not yet used)
+struct R0Desc {
+    const SegIn* g;
+    uint32_t t, seg, lt;
+    uint4 d;                  // first row, rows touched, first row's offset
+};
+__device__ __forceinline__ R0Desc r0_desc(const Round0Args& a, uint32_t t) {
+    R0Desc d;
+    d.t = t;
+    d.g = nullptr;
+    d.seg = d.lt = 0;
+    d.d = make_uint4(0, 0, 0, 0);
+    if (t < a.ntiles) {
+        d.seg = seg_of_tile(a, t);
+        d.g = &a.segs[d.seg];
+        d.lt = t - d.g->tile_begin;
+        if (d.lt < d.g->ntiles) d.d = d.g->tdesc[d.lt];
+    }
+    return d;
+}
+
+__device__ void r0_producer(R0Smem& s, const Round0Args& a) {
+    DevState* st = a.st;
+    const uint32_t step = gridDim.x;
+    R0Desc q0 = r0_desc(a, blockIdx.x), q1 = r0_desc(a, blockIdx.x + step);
+    R0Desc q2 = r0_desc(a, blockIdx.x + 2 * step), q3 = r0_desc(a, blockIdx.x + 3 * step);
+    static_assert(R0AHEAD == 4, "shift chain of four descriptors");
+    for (uint32_t j = 0;; j++) {
+        const int k = (int)(j % R0S);
+        const uint32_t use = j / R0S;
+        R0Stage& S = s.stage[k];
+        const R0Desc d = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = r0_desc(a, blockIdx.x + (j + R0AHEAD) * step);
+        bool valid = d.g != nullptr;
+        uint32_t j0 = 0, nent = 0;
+        if (valid) {
+            const SegIn* g = d.g;
+            j0 = d.lt * TILE0;
+            valid = d.lt < g->ntiles && d.d.y >= 1 && d.d.y <= TILE0 + 1 && d.d.x + d.d.y <= g->nrows;
+            if (valid) nent = min(TILE0, g->nent - j0);
+            else set_err(st, ERR_BOUNDS, d.t);
+        }
+        // the stage must be free: its consumers released it after their last use
+        if (use > 0 && !mbar_wait(&s.empty[k], (use - 1) & 1u)) {
+            set_err(st, ERR_TIMEOUT, 0x10000000u | j);
+            return;
+        }
+        if (!valid) {
+            S.valid = 0;
+            mbar_arrive(&s.full[k]);
+            return;
+        }
+        const SegIn* g = d.g;
+        const uint32_t r_lo = d.d.x, nload = d.d.y;
+        const uint32_t a0 = r_lo & ~3u, shift = r_lo - a0;
+        S.valid = 1;
+        S.seg = d.seg;
+        S.j0 = j0;
+        S.nent = nent;
+        S.shift = shift;
+        const uint32_t b_pk = round16(nent * 8u);
+        const uint32_t b_nbr = round16(nent * 4u);
+        const uint32_t b_vid = round16((shift + nload) * 4u);
+        const uint32_t b_bits = (uint32_t)(R0W + 4) * 4u;
+        // order the consumers' earlier reads of this stage before the copies' writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&s.full[k], b_pk + b_nbr + b_vid + b_bits);
+        bulk_g2s(S.pk, g->pk + j0, b_pk, &s.full[k]);
+        bulk_g2s(S.nbr, g->nbr + j0, b_nbr, &s.full[k]);
+        bulk_g2s(S.rvid, g->rvid + a0, b_vid, &s.full[k]);
+        bulk_g2s(S.bits, g->rbits + j0 / 32, b_bits, &s.full[k]);
+    }
+}
+
+__device__ void r0_consumer(R0Smem& s, const Round0Args& a, int tid) {
+    const int lane = tid & 31, warp = tid >> 5;
+    const VertexArrays& va = a.va;
+    DevState* st = a.st;
+    for (uint32_t i = 0;; i++) {
+        const int k = (int)(i % R0S);
+        const uint32_t use = i / R0S;
+        const bool ok = mbar_wait(&s.full[k], use & 1u);
+        if (cbar_or(!ok)) {
+            if (tid == 0) set_err(st, ERR_TIMEOUT, 0x30000000u | i);
+            return;
+        }
+        R0Stage& S = s.stage[k];
+        if (!S.valid) return;
+        const uint32_t j0 = S.j0, nent = S.nent, shift = S.shift;
+        const SegIn& g = a.segs[S.seg];
+        const uint32_t vbase = g.vbase, k0 = g.k0, k1 = g.k1;
+
+        // row structure from the bitmap: every warp scans the tile's words itself
+        uint32_t wex[R0WPL], sum = 0;
+#pragma unroll
+        for (int q = 0; q < R0WPL; q++) {
+            wex[q] = sum;
+            sum += __popc(S.bits[lane * R0WPL + q]);
+        }
+        const uint32_t incl = warp_incl_scan(sum, lane);
+#pragma unroll
+        for (int q = 0; q < R0WPL; q++) wex[q] += incl - sum;
+        const uint32_t starts = __shfl_sync(FULL, incl, 31);
+        const uint32_t b0 = S.bits[0] & 1u;
+        const uint32_t nrt = starts + 1u - b0;  // rows with entries in the tile
+        const bool cutL = (j0 + nent < g.nent) && !(S.bits[R0W] & 1u);
+        const bool cut0 = !b0 || (nrt == 1 && cutL);
+
+        // entries: R0G groups of 32 per warp
+        uint64_t key[R0G];
+        uint32_t lr[R0G], u[R0G], word[R0G];
+#pragma unroll
+        for (int i2 = 0; i2 < R0G; i2++) {
+            const int grp = warp * R0G + i2;  // warp-uniform
+            const uint32_t q = (uint32_t)grp * 32u + lane;
+            const int src = grp / R0WPL, sub = grp % R0WPL;
+            uint32_t pre = 0;
+#pragma unroll
+            for (int qq = 0; qq < R0WPL; qq++) {
+                const uint32_t p1 = __shfl_sync(FULL, wex[qq], src);
+                if (qq == sub) pre = p1;
+            }
+            word[i2] = S.bits[grp];
+            lr[i2] = pre + __popc(word[i2] & (FULL >> (31 - lane))) - b0;
+            key[i2] = 0;
+            u[i2] = NIL;
+            if (q < nent) {
+                const unsigned long long w = S.pk[q];
+                key[i2] = (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, k0, k1);
+                u[i2] = S.nbr[q] + vbase;
+            }
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < R0G; i2++) {
+            if ((word[i2] & 0xFFFFFFFEu) == 0) {
+                // the whole group lies in one row
+                if (__any_sync(FULL, key[i2] != 0)) {
+                    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i2] >> 32));
+                    const uint32_t lo =
+                        __reduce_max_sync(FULL, ((uint32_t)(key[i2] >> 32) == hi) ? (uint32_t)key[i2] : 0u);
+                    if (lane == 0) atomicMax(&s.kmax[lr[i2]], ((unsigned long long)hi << 32) | lo);
+                }
+            } else if (key[i2]) {
+                atomicMax(&s.kmax[lr[i2]], (unsigned long long)key[i2]);
+            }
+        }
+        cbar();
+        // the entry that holds its row's maximum names the row's candidate (keys are distinct)
+#pragma unroll
+        for (int i2 = 0; i2 < R0G; i2++)
+            if (key[i2] && key[i2] == s.kmax[lr[i2]]) s.knbr[lr[i2]] = u[i2];
+        cbar();
+
+        // rows: candidates
+#pragma unroll
+        for (int q = 0; q < R0RPT; q++) {
+            const uint32_t r = (uint32_t)(tid + q * R0C);
+            if (r < nrt) {
+                const uint32_t v = S.rvid[shift + r] + vbase;
+                const unsigned long long K = s.kmax[r];
+                s.kmax[r] = 0;
+                if (v >= va.nvert) {
+                    set_err(st, ERR_BOUNDS, v);
+                    continue;
+                }
+                const bool cut = (r == 0 && cut0) || (r == nrt - 1 && cutL);
+                if (!cut) va.cnbr[v] = s.knbr[r];
+                else atomicMax(&va.bkey[v], K);
+            }
+        }
+        cbar();
+        if (tid == 0) mbar_arrive(&s.empty[k]);
+    }
+}
+
+__global__ void __launch_bounds__(R0T, LM_R0MINB) k_round0(const Round0Args* __restrict__ pa) {
+    extern __shared__ __align__(128) unsigned char r0_raw[];
+    R0Smem& s = *reinterpret_cast<R0Smem*>(r0_raw);
+    const Round0Args& a = *pa;
+    const int tid = threadIdx.x;
+    for (uint32_t r = tid; r <= TILE0; r += R0T) s.kmax[r] = 0;
+    if (tid == 0) {
+        for (int k = 0; k < R0S; k++) {
+            mbar_init(&s.full[k], 1);
+            mbar_init(&s.empty[k], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (a.ntiles == 0 || a.nsegs == 0) return;
+    if (tid == R0C) r0_producer(s, a);
+    else if (tid < R0C) r0_consumer(s, a, tid);
+}
+
+// Candidates of rows that tile boundaries cut: each such row is visited once,
+// at the first boundary inside it, and recovers its neighbour from the maximum
+// its pieces left in bkey[] (which goes back to zero).
+__global__ void k_round0_cut(const Round0Args* __restrict__ pa) {
+    const Round0Args& a = *pa;
+    const VertexArrays& va = a.va;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += stride) {
+        const SegIn& g = a.segs[seg_of_tile(a, t)];
+        const uint32_t lt = t - g.tile_begin;
+        if (lt == 0 || lt >= g.ntiles) continue;
+        const uint32_t r = g.tmap[lt];
+        if (r >= g.nrows) { set_err(a.st, ERR_BOUNDS, t); continue; }
+        const uint32_t o0 = g.roff[r];
+        if (o0 >= lt * TILE0 || o0 < (lt - 1) * TILE0) continue;
+        const uint32_t v = g.rvid[r] + g.vbase;
+        if (v >= va.nvert) { set_err(a.st, ERR_BOUNDS, v); continue; }
+        const unsigned long long K = va.bkey[v];
+        if (K) {
+            va.bkey[v] = 0;
+            va.cnbr[v] = recover_nbr_seg(g, a.st, v, K);
         }
     }
 }
@@ -576,15 +935,16 @@ __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const fl
 }
 
 __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                             uint32_t* cursor, uint32_t* nbr, uint32_t* eid, uint32_t* ordw) {
+                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const uint32_t u = eu[e], v = ev[e];
-        const uint32_t o = ord_of_bits(__float_as_uint(w[e]));
+        const uint64_t word = ((uint64_t)ord_of_bits(__float_as_uint(w[e])) << 32) | e;
+        edges[e] = (uint64_t)u | ((uint64_t)v << 32);
         const uint32_t pu = atomicAdd(&cursor[u], 1u);
-        nbr[pu] = v; eid[pu] = e; ordw[pu] = o;
+        nbr[pu] = v; pk[pu] = word;
         const uint32_t pv = atomicAdd(&cursor[v], 1u);
-        nbr[pv] = u; eid[pv] = e; ordw[pv] = o;
+        nbr[pv] = u; pk[pv] = word;
     }
 }
 
@@ -593,14 +953,39 @@ __global__ void k_nonzero_flags(const uint32_t* deg, uint32_t n, uint32_t* flags
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) flags[v] = deg[v] ? 1u : 0u;
 }
 
-__global__ void k_build_rows(const uint32_t* deg, const uint32_t* rowidx, uint32_t n, uint32_t* vid0, uint32_t* rdeg0) {
+__global__ void k_build_rows(const uint32_t* deg, const uint32_t* rowidx, const uint32_t* off, uint32_t n,
+                             uint32_t nrows, uint32_t nent, uint32_t* vid0, uint32_t* rdeg0, uint32_t* roff) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         if (deg[v]) {
             const uint32_t i = rowidx[v];
             vid0[i] = v;
             rdeg0[i] = deg[v];
+            roff[i] = off[v];
         }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) roff[nrows] = nent;
+}
+
+__global__ void k_build_tilemap(const uint32_t* roff, uint32_t nrows, uint32_t nent, uint32_t* tmap,
+                                uint32_t* rbits) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t ntiles = (nent + TILE0 - 1) / TILE0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += stride) {
+        const uint32_t lo = roff[i], hi = roff[i + 1];
+        for (uint32_t t = (lo + TILE0 - 1) / TILE0; t < (hi + TILE0 - 1) / TILE0; t++) tmap[t] = i;
+        atomicOr(&rbits[lo >> 5], 1u << (lo & 31));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tmap[ntiles] = nrows;
+}
+
+// per tile: first row r_lo, rows touched (r_lo .. min(tmap[t + 1], nrows - 1)), offset of row r_lo
+__global__ void k_build_tiledesc(const uint32_t* roff, const uint32_t* tmap, uint32_t nrows, uint32_t ntiles,
+                                 uint4* tdesc) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += stride) {
+        const uint32_t r_lo = tmap[t], r_cap = min(tmap[t + 1], nrows - 1);
+        tdesc[t] = make_uint4(r_lo, r_cap - r_lo + 1, roff[r_lo], 0);
     }
 }
 
@@ -798,6 +1183,37 @@ static int launch_sweep_t(void* stream, const SweepArgs* dargs) {
     k_sweep<I, C><<<sweep_grid<I, C>(), ST, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
+static int round0_blocks_per_sm() {
+    static int per = 0;
+    if (!per) {
+        cudaError_t e = cudaFuncSetAttribute(k_round0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(R0Smem));
+        if (e != cudaSuccess) return -(int)e;
+        int p = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k_round0, R0T, sizeof(R0Smem));
+        if (e != cudaSuccess) return -(int)e;
+        per = p > 0 ? p : 1;
+    }
+    return per;
+}
+// persistent: as many CTAs as fit, tiles strided over the grid
+static int round0_grid(uint32_t* grid) {
+    const int per = round0_blocks_per_sm();
+    if (per < 0) return -per;
+    *grid = (uint32_t)(current_sms() * per);
+    return 0;
+}
+int launch_round0(void* stream, const Round0Args* d) {
+    uint32_t grid = 0;
+    const int e = round0_grid(&grid);
+    if (e) return e;
+    k_round0<<<grid, R0T, sizeof(R0Smem), (cudaStream_t)stream>>>(d);
+    return (int)cudaGetLastError();
+}
+static uint32_t round0_cut_grid() { return (uint32_t)current_sms() * 2; }
+int launch_round0_cut(void* stream, const Round0Args* d) {
+    k_round0_cut<<<round0_cut_grid(), 256, 0, (cudaStream_t)stream>>>(d);
+    return (int)cudaGetLastError();
+}
 int launch_sweep_cand(void* stream, const SweepArgs* d) { return launch_sweep_t<true, false>(stream, d); }
 int launch_sweep_input(void* stream, const SweepArgs* d) { return launch_sweep_t<true, true>(stream, d); }
 int launch_sweep_live(void* stream, const SweepArgs* d) { return launch_sweep_t<false, true>(stream, d); }
@@ -808,17 +1224,26 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
     return (int)cudaGetLastError();
 }
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint32_t* eid, uint32_t* ordw) {
-    k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, eid, ordw);
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges) {
+    k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, pk, edges);
     return (int)cudaGetLastError();
 }
 int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t* flags) {
     k_nonzero_flags<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, n, flags);
     return (int)cudaGetLastError();
 }
-int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, uint32_t n, uint32_t* vid0,
-                      uint32_t* rdeg0) {
-    k_build_rows<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, rowidx_excl, n, vid0, rdeg0);
+int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, const uint32_t* off,
+                      uint32_t n, uint32_t nrows, uint32_t nent, uint32_t* vid0, uint32_t* rdeg0, uint32_t* roff) {
+    k_build_rows<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(deg, rowidx_excl, off, n, nrows, nent, vid0,
+                                                                     rdeg0, roff);
+    return (int)cudaGetLastError();
+}
+int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uint32_t nent, uint32_t* tmap,
+                         uint32_t* rbits, uint4* tdesc) {
+    k_build_tilemap<<<grid_for(nrows + 1, 256), 256, 0, (cudaStream_t)stream>>>(roff, nrows, nent, tmap, rbits);
+    const uint32_t ntiles = (nent + TILE0 - 1) / TILE0;
+    if (ntiles) k_build_tiledesc<<<grid_for(ntiles, 256), 256, 0, (cudaStream_t)stream>>>(roff, tmap, nrows, ntiles,
+                                                                                         tdesc);
     return (int)cudaGetLastError();
 }
 int launch_union_setup(void* stream, const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
@@ -865,46 +1290,55 @@ __global__ void k_loop_check(DevState* st, cudaGraphConditionalHandle h) {
 }
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, void* func, dim3 grid,
-                              dim3 block, void** params) {
+                              dim3 block, void** params, unsigned smem = 0) {
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof kp);
     kp.func = func;
     kp.gridDim = grid;
     kp.blockDim = block;
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = smem;
     kp.kernelParams = params;
     return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
 
+// init -> round-0 candidate tiles (+ cut rows) -> round-0 match -> round-0
+// compaction from the input arrays -> round 1 -> while (live) { two rounds }
 int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out) {
     *exec_out = nullptr;
+    uint32_t rgrid = 0;
+    if (int pe = round0_grid(&rgrid)) return pe;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return (int)e;
     cudaGraphNode_t prev = nullptr, node = nullptr;
     // kernel parameters: one pointer to the arguments in device memory
     const InitArgs* p_init = &dargs->init;
+    const Round0Args* pr = &dargs->r0;
     const VertexArgs* pv[4] = {&dargs->v[0], &dargs->v[1], &dargs->v[2], &dargs->v[3]};
     const SweepArgs* ps[4] = {&dargs->s[0], &dargs->s[1], &dargs->s[2], &dargs->s[3]};
     void* init_params[1] = {&p_init};
+    void* rparams[1] = {&pr};
     void* vparams[4][1], *sparams[4][1];
     for (int k = 0; k < 4; k++) {
         vparams[k][0] = &pv[k];
         sparams[k][0] = &ps[k];
     }
-    const dim3 vgrid(vertex_grid()), vblock(VT), sblock(ST);
+    const dim3 vgrid(vertex_grid()), vblock(VT), sblock(ST), rblock(R0T), cgrid(round0_cut_grid());
+    const dim3 lgrid(sweep_grid<false, true>()), igrid(sweep_grid<true, true>());
     do {
         if ((e = add_kernel(g, &node, prev, (void*)k_init, dim3(current_sms() * 16), dim3(256), init_params))) break;
         prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_round0, dim3(rgrid), rblock, rparams, sizeof(R0Smem)))) break;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, (void*)k_round0_cut, cgrid, dim3(256), rparams))) break;
+        prev = node;
         if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[0]))) break;
         prev = node;
-        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, false>, dim3(sweep_grid<true, false>()), sblock,
-                            sparams[0]))) break;
+        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, true>, igrid, sblock, sparams[0]))) break;
         prev = node;
         if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[1]))) break;
         prev = node;
-        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, true>, dim3(sweep_grid<true, true>()), sblock,
-                            sparams[1]))) break;
+        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<false, true>, lgrid, sblock, sparams[1]))) break;
         prev = node;
         cudaGraphConditionalHandle h;
         if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault))) break;
@@ -921,8 +1355,7 @@ int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out) {
         for (int k = 2; k < 4 && e == cudaSuccess; k++) {
             if ((e = add_kernel(body, &bn, bp, (void*)k_vertex, vgrid, vblock, vparams[k]))) break;
             bp = bn;
-            if ((e = add_kernel(body, &bn, bp, (void*)k_sweep<false, true>, dim3(sweep_grid<false, true>()), sblock,
-                                sparams[k]))) break;
+            if ((e = add_kernel(body, &bn, bp, (void*)k_sweep<false, true>, lgrid, sblock, sparams[k]))) break;
             bp = bn;
         }
         if (e) break;

@@ -135,13 +135,14 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     SegIn* segs_h = static_cast<SegIn*>(e.pinned);
     for (size_t k = 0; k < fresh.size(); k++) {
         Request* r = fresh[k];
-        segs_h[k] = seg_of(r->g, r->seed, r->vbase, r->ebase);
+        segs_h[k] = seg_of(r->g, r->seed, r->vbase, r->ebase, 0);
         LM_CK(ctx, cudaMemcpyAsync(&w.segs[r->slot], &segs_h[k], sizeof(SegIn), cudaMemcpyHostToDevice, s));
         LM_CK(ctx, launch_req_setup(s, r->g->off, r->g->n, r->vbase, r->ebase, r->slot, w.start, w.gid));
         InitArgs& ia = A.init[k];
         ia.mate = w.mate + r->vbase;
         ia.dead = w.dead + r->vbase;
         ia.bcnt = w.bcnt + r->vbase;
+        ia.bkey = w.bkey + r->vbase;
         ia.n = r->g->n;
         ia.st = nullptr;
         VertexArgs& pre = A.pre[k];
@@ -180,16 +181,20 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         c.in_set = in_set;
         c.par = par;
         c.segs = w.segs;
+        c.nsegs = ctx->max_slots;
         if (!input) { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
         c.out_key = w.key[par ^ 1u];
         c.out_nbr = w.nbr[par ^ 1u];
         c.ecap = S->cap_e;
-        c.part = w.part;
         c.st = e.st;
     };
     sargs(A.cand, 2, true);
     sargs(A.s_live, par ^ 1u, false);
     sargs(A.s_fresh, 3, true);
+    // each sweep its own task counter; the vertex pass before each zeroes them
+    A.cand.task_ctr = &e.st->task[0];
+    A.s_live.task_ctr = &e.st->task[1];
+    A.s_fresh.task_ctr = &e.st->task[2];
     LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
     LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
     LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
