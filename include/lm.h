@@ -162,6 +162,39 @@ int  lm_poll(lm_ctx* ctx, uint64_t ticket, int* done, lm_stats* stats);
  * ticket stays valid).  Does not release the ticket: call lm_poll after. */
 int  lm_wait(lm_ctx* ctx, uint64_t ticket, uint32_t timeout_ms);
 
+/* Small graphs without allocation.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory while they run,
+ * for example a host loop that keeps a fixed device footprint or hands all
+ * free memory to another allocator, and so cannot let lm_create /
+ * lm_graph_create reserve buffers.  It matches one graph of at most
+ * LM_NOALLOC_MAX_N vertices and LM_NOALLOC_MAX_M edges by local max under the
+ * same order K as lm_match (same seed, same edge ids: the result equals
+ * lm_match's on that graph), in one kernel launch on `stream`, and returns
+ * once the launch is queued.  Its only scratch is one static device array of
+ * LM_NOALLOC_SCRATCH_BYTES in the library itself; nothing is allocated or
+ * freed, on the device or on the host.
+ *   n, m      : vertex and edge counts, n <= LM_NOALLOC_MAX_N, m <= LM_NOALLOC_MAX_M
+ *   eu, ev, w : device arrays uint32[m], uint32[m], float32[m] as in lm_graph_create
+ *   mate      : device uint32[n]; when the kernel ends, v's partner or LM_NIL
+ *   status    : device uint32[1]; when the kernel ends, 0 = ok, 1 = an edge had an
+ *               endpoint >= n, a self loop or a NaN weight (then every mate[v]
+ *               is LM_NIL), 2 = round cap exceeded (not expected)
+ *   stream    : cudaStream_t, NULL = the default stream
+ * Nothing needs to start at zero: each call initialises the scratch it reads.
+ * There is one scratch per device, so two calls on one device whose kernels
+ * can overlap (different streams, or threads without ordering) race on it and
+ * corrupt each other's results: order them, e.g. issue them on one stream.
+ * The first call on a device resolves the scratch's address there (with that
+ * device current); make that first call before any stream capture on it.
+ * Errors (returned at once): LM_EINVAL (n or m beyond the limits, a null
+ * pointer, current device index >= 64), LM_ECUDA (the address lookup or the
+ * launch failed). */
+#define LM_NOALLOC_MAX_N 65536u
+#define LM_NOALLOC_MAX_M 262144u
+#define LM_NOALLOC_SCRATCH_BYTES (9ull * LM_NOALLOC_MAX_N + 8ull * LM_NOALLOC_MAX_M)
+int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
+                            uint64_t seed, uint32_t* mate, uint32_t* status, void* stream);
+
 /* Static description of an error code. */
 const char* lm_strerror(int code);
 

@@ -24,7 +24,9 @@ LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_TAIL, LM_K_OTHER, LM_K_COUNT = range(6)
 
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
-           "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error")
+           "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error",
+           "lm_match_small_noalloc")
+LM_NOALLOC_MAX_N, LM_NOALLOC_MAX_M = 65536, 262144
 
 
 class LmConfig(ctypes.Structure):
@@ -86,6 +88,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.lm_strerror.restype = ctypes.c_char_p
         lib.lm_last_error.argtypes = [vp]
         lib.lm_last_error.restype = ctypes.c_char_p
+        lib.lm_match_small_noalloc.argtypes = [u32, u32, vp, vp, vp, u64, vp, vp, vp]
         _LIB = lib
         return lib
 
@@ -240,3 +243,26 @@ def lm_wait(ctx, ticket: int, timeout_ms: int) -> bool:
 
 def lm_strerror(code: int) -> str:
     return load().lm_strerror(code).decode()
+
+
+def lm_match_small_noalloc(n: int, eu, ev, w, seed: int, mate, status, stream=None) -> None:
+    """Queue local max of one small device-resident graph (n <= LM_NOALLOC_MAX_N,
+    m <= LM_NOALLOC_MAX_M) on `stream` without any allocation by the library.
+    eu / ev (int32 or uint32), w (float32), mate (int32[n]) and status (int32[1])
+    are CUDA tensors; mate and status are written when the kernel ends.  Raises
+    LmError on rejected arguments (sizes beyond the limits, null pointers)."""
+    lib = load()
+    m = int(eu.numel())
+    if int(ev.numel()) != m or int(w.numel()) != m:
+        raise ValueError("eu, ev and w differ in length")
+    for t in (eu, ev, w, mate, status):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("lm_match_small_noalloc takes contiguous CUDA tensors")
+    if stream is None:
+        s = None
+    elif isinstance(stream, int):
+        s = stream
+    else:
+        s = stream.cuda_stream
+    _check(lib.lm_match_small_noalloc(n, m, eu.data_ptr(), ev.data_ptr(), w.data_ptr(), seed & (2**64 - 1),
+                                      mate.data_ptr(), status.data_ptr(), s))

@@ -196,6 +196,7 @@ int launch_sweep_live(void* stream, const SweepArgs* dargs);   // rounds >= 1
 int launch_round0(void* stream, const Round0Args* dargs);      // round-0 candidates in TMA-fed tiles
 int launch_round0_cut(void* stream, const Round0Args* dargs);  // candidates of rows cut by tile boundaries
 int device_sm_count(int device);
+uint64_t splitmix64_first(uint64_t seed);  // lm_api.cpp
 // executable graph that runs a whole job from its arguments in device memory
 // (init, round 0, then a conditional loop of rounds until the device's done
 // flag is set); returns a cudaError_t value

@@ -27,6 +27,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+#include <mutex>
+
+#include "../../include/lm.h"
 #include "lm_internal.h"
 
 namespace lm {
@@ -1377,4 +1380,133 @@ void destroy_job_graph(void* exec) {
     if (exec) cudaGraphExecDestroy((cudaGraphExec_t)exec);
 }
 
+// ---------------------------------------------------------------- small graphs without allocation
+// lm_match_small_noalloc: local max for one small graph whose edge list is
+// already on the device, run by one CTA whose only scratch is the static
+// array below (no allocation at call time).  Each round every live edge
+// offers its key to both ends, an edge that is the heaviest offer at both ends
+// is matched, and edges with a matched end leave (Sec. 2, the phases of local
+// max, with the same order K as the main path).
+constexpr uint32_t NA_MAX_N = LM_NOALLOC_MAX_N, NA_MAX_M = LM_NOALLOC_MAX_M;
+struct NaScratch {
+    unsigned long long best[NA_MAX_N];   // heaviest offer at each vertex in the current round
+    uint32_t live[2][NA_MAX_M];          // live edge ids, alternating between rounds
+    uint8_t dead[NA_MAX_N];              // matched
+};
+static_assert(sizeof(NaScratch) == LM_NOALLOC_SCRATCH_BYTES, "scratch size as documented");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NaScratch)];
+
+constexpr int NA_T = 1024;
+__global__ void __launch_bounds__(NA_T, 1) k_match_small(uint32_t n, uint32_t m, const uint32_t* __restrict__ eu,
+                                                         const uint32_t* __restrict__ ev, const float* __restrict__ w,
+                                                         uint32_t k0, uint32_t k1, uint32_t* mate, uint32_t* status,
+                                                         NaScratch* sc) {
+    __shared__ uint32_t s_cnt[2], s_err;
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_err = 0;
+    }
+    for (uint32_t v = tid; v < n; v += NA_T) {
+        mate[v] = NIL;
+        sc->best[v] = 0;
+        sc->dead[v] = 0;
+    }
+    __syncthreads();
+    for (uint32_t e = tid; e < m; e += NA_T) {
+        const uint32_t u = eu[e], v = ev[e], wb = __float_as_uint(w[e]);
+        const bool nan = ((wb & 0x7F800000u) == 0x7F800000u) && (wb & 0x007FFFFFu);
+        if (u >= n || v >= n || u == v || nan) {
+            atomicOr(&s_err, 1u);
+            continue;
+        }
+        sc->live[0][atomicAdd(&s_cnt[0], 1u)] = e;
+    }
+    __syncthreads();
+    uint32_t cur = 0, count = s_err ? 0u : s_cnt[0];
+    auto key = [&](uint32_t e) -> unsigned long long {
+        return ((unsigned long long)ord_of_bits(__float_as_uint(w[e])) << 32) | perm_seed(e, k0, k1);
+    };
+    for (uint32_t round = 0; count > 0; round++) {
+        if (round > m) {  // every round matches at least one edge
+            if (tid == 0) s_err |= 2u;
+            break;
+        }
+        for (uint32_t i = tid; i < count; i += NA_T) {
+            const uint32_t e = __ldcg(&sc->live[cur][i]);
+            const unsigned long long K = key(e);
+            atomicMax(&sc->best[eu[e]], K);
+            atomicMax(&sc->best[ev[e]], K);
+        }
+        if (tid == 0) s_cnt[cur ^ 1u] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < count; i += NA_T) {
+            const uint32_t e = __ldcg(&sc->live[cur][i]);
+            const uint32_t u = eu[e], v = ev[e];
+            const unsigned long long K = key(e);
+            // read at L2, where the atomics of this round landed
+            if (__ldcg(&sc->best[u]) == K && __ldcg(&sc->best[v]) == K) {
+                mate[u] = v;
+                mate[v] = u;
+                sc->dead[u] = 1;
+                sc->dead[v] = 1;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < count; i += NA_T) {
+            const uint32_t e = __ldcg(&sc->live[cur][i]);
+            const uint32_t u = eu[e], v = ev[e];
+            sc->best[u] = 0;
+            sc->best[v] = 0;
+            if (!__ldcg(&sc->dead[u]) && !__ldcg(&sc->dead[v]))
+                sc->live[cur ^ 1u][atomicAdd(&s_cnt[cur ^ 1u], 1u)] = e;
+        }
+        __syncthreads();
+        count = s_cnt[cur ^ 1u];
+        cur ^= 1u;
+        __syncthreads();
+    }
+    if (tid == 0) *status = s_err;
+}
+
 }  // namespace lm
+
+// The scratch's address on each device, looked up once with that device current.
+namespace {
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mu;
+void* g_na_ptr[NA_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" int lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev,
+                                      const float* w, uint64_t seed, uint32_t* mate, uint32_t* status,
+                                      void* stream) {
+    if (n > LM_NOALLOC_MAX_N || m > LM_NOALLOC_MAX_M) return LM_EINVAL;
+    if (!status || (n > 0 && !mate) || (m > 0 && (!eu || !ev || !w))) return LM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return LM_ECUDA;
+    }
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return LM_EINVAL;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, lm::g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LM_ECUDA;
+            }
+            g_na_ptr[dev] = p;
+        }
+        scratch = g_na_ptr[dev];
+    }
+    const uint64_t z = lm::splitmix64_first(seed);
+    lm::k_match_small<<<1, lm::NA_T, 0, (cudaStream_t)stream>>>(n, m, eu, ev, w, (uint32_t)z, (uint32_t)(z >> 32),
+                                                               mate, status, static_cast<lm::NaScratch*>(scratch));
+    if (cudaGetLastError() != cudaSuccess) return LM_ECUDA;
+    return LM_OK;
+}
