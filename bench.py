@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "input edges/s to maximal matching"
 
+# dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match,
+# from one ncu capture of the same workload (None until taken for the current kernels)
+TRAFFIC = {}
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -136,20 +140,28 @@ def make_workload(name: str):
 
 
 def sweep_model_bytes(st: dict) -> int:
-    """Algorithmic HBM bytes of all sweep launches of one match, from the
-    per-round live counts: a compacting sweep over E_r entries / R_r rows
-    reads 16 B per entry (12 B entry + 4 B neighbour-state gather), writes
-    12 B per surviving entry, reads 8 B per row and writes 12 B per new row;
-    the candidate-only sweep of round 0 reads 16 B per entry, 8 B per row and
-    writes 4 B per row."""
+    """Algorithmic HBM bytes of the k_sweep launches of one match (round-0
+    compaction from the input arrays and every later round), from the per-round
+    live counts: a sweep over E_r entries / R_r rows reads 16 B per entry (12 B
+    entry + 4 B neighbour-state gather), writes 12 B per surviving entry, reads
+    8 B per row and writes 12 B per row of the next round."""
     rm, rn = st["round_m"], st["round_n"]
     R = len(rm)
     E = [2 * x for x in rm] + [0]
     N = list(rn) + [0]
-    b = 16 * E[0] + 12 * N[0] if R else 0
+    b = 0
     for r in range(R):
         b += 16 * E[r] + 12 * E[r + 1] + 8 * N[r] + 12 * N[r + 1]
     return b
+
+
+def cand_model_bytes(st: dict) -> int:
+    """Algorithmic HBM bytes of the round-0 candidate kernel: 12 B per input
+    entry (8 B weight/edge word + 4 B neighbour) and 8 B per row (row vertex
+    read, candidate written)."""
+    if not st["round_m"]:
+        return 0
+    return 12 * 2 * st["round_m"][0] + 8 * st["round_n"][0]
 
 
 def run_lm(args, ws, rank, local):
@@ -189,19 +201,26 @@ def run_lm(args, ws, rank, local):
 
     # per-kernel device times (CUDA events recorded by the library on its stream)
     pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE)
-    sweep_ms, sweep_n, total_ms, vert_ms = [], [], [], []
+    kms = {k: [] for k in range(lm.LM_K_COUNT)}
+    total_ms = []
     for i in range(max(args.warmup, 3) + args.steps):
         _, pst = lm.lm_match(pctx, h, seed, mate, stats=True)
         if i >= max(args.warmup, 3):
-            sweep_ms.append(pst["kernel_ms"][lm.LM_K_SWEEP])
-            vert_ms.append(pst["kernel_ms"][lm.LM_K_VERTEX])
-            sweep_n.append(pst["kernel_launches"][lm.LM_K_SWEEP])
+            for k in range(lm.LM_K_COUNT):
+                kms[k].append(pst["kernel_ms"][k])
             total_ms.append(pst["total_ms"])
     lm.lm_destroy(pctx)
+    med = {k: statistics.median(v) for k, v in kms.items()}
     peak, peak_kind = _peaks()
     bytes_sweep = sweep_model_bytes(pst)
-    sw_ms = statistics.median(sweep_ms)
+    bytes_cand = cand_model_bytes(pst)
+    sw_ms, cd_ms = med[lm.LM_K_SWEEP], med[lm.LM_K_CAND]
     achieved = bytes_sweep / (sw_ms * 1e-3) / 1e9 if sw_ms > 0 else 0.0
+    cand_achieved = bytes_cand / (cd_ms * 1e-3) / 1e9 if cd_ms > 0 else 0.0
+    names = {lm.LM_K_INIT: "k_init", lm.LM_K_SWEEP: "k_sweep", lm.LM_K_VERTEX: "k_vertex",
+             lm.LM_K_CAND: "k_round0", lm.LM_K_OTHER: "other (k_round0_cut, k_loop_check)"}
+    kernels = {names[k]: {"ms_per_match": med[k], "launches_per_match": pst["kernel_launches"][k]}
+               for k in range(lm.LM_K_COUNT)}
 
     # end to end through the C ABI with host buffers: graph upload + build, match, result download
     e2e = None
@@ -237,14 +256,176 @@ def run_lm(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "bytes_per_match": bytes_sweep, "sweep_ms_per_match": sw_ms,
-                     "sweep_launches_per_match": statistics.median(sweep_n),
-                     "vertex_ms_per_match": statistics.median(vert_ms),
+                     "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
+                     "bytes_per_match": bytes_sweep, "ms_per_match": sw_ms,
+                     "launches_per_match": pst["kernel_launches"][lm.LM_K_SWEEP],
                      "profiled_total_ms": statistics.median(total_ms)},
+        "roofline_k_round0": {"bound": "hbm", "achieved": cand_achieved, "peak": peak, "unit": "GB/s",
+                              "frac": cand_achieved / peak, "bytes_per_launch": bytes_cand, "ms": cd_ms},
+        "kernels": kernels,
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
     }
     return out, g
+
+
+def _pctl(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    return xs[min(len(xs) - 1, int(math.ceil(q * len(xs))) - 1)]
+
+
+def run_batch(args, ws, rank, local):
+    """4096 mixed graphs (n log-uniform in [64, 65536], degree U[4,16], ER / grid /
+    R-MAT): one lm_batch_match per step against the same graphs matched back to
+    back with lm_match.  Latency of a graph = time from the call's start until its
+    mate is complete (the whole call for the batch; the running sum for plain)."""
+    import torch
+    import paper_1302_4587_gb300 as lm
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    gs = synth.batch(4096, seed=4)
+    seeds = [1000 + i for i in range(len(gs))]
+    ctx = lm.lm_create(local, stream)
+    hs = [lm.lm_graph_create(ctx, g.n, g.eu, g.ev, g.w) for g in gs]
+    mates = [torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n] for g in gs]
+    m_tot = sum(g.m for g in gs)
+    for _ in range(max(args.warmup, 3)):
+        lm.lm_batch_match(ctx, hs, seeds, mates)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            lm.lm_batch_match(ctx, hs, seeds, mates)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    batched = [m.clone() for m in mates]
+    # plain: the same graphs back to back
+    pm = [torch.empty_like(m) for m in mates]
+    for i, h in enumerate(hs):
+        lm.lm_match(ctx, h, seeds[i], pm[i])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = []
+    for i, h in enumerate(hs):
+        lm.lm_match(ctx, h, seeds[i], pm[i])
+        done.append(time.perf_counter() - t0)
+    plain_s = done[-1]
+    same = all(torch.equal(a, b) for a, b in zip(batched, pm))
+    for h in hs:
+        lm.lm_graph_destroy(h)
+    lm.lm_destroy(ctx)
+    gps = len(gs) / (ms * 1e-3)
+    return {
+        "metric": "graphs/s (batched, 4096 mixed graphs)", "value": ws * gps, "unit": "graphs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
+        "config": {"workload": "batch", "graphs": len(gs), "sum_m": m_tot, "sum_n": sum(g.n for g in gs),
+                   "desc": "n log-uniform [64,65536], degree U[4,16], ER/grid/R-MAT mixed, w~U[0,1), gen seed 4",
+                   "l2": "inputs larger than L2 (sum of graphs about 2.3 GB)"},
+        "edges_per_s": ws * m_tot / (ms * 1e-3), "p50_ms": ms, "p99_ms": ms,
+        "plain_back_to_back": {"graphs_per_s": len(gs) / plain_s, "edges_per_s": m_tot / plain_s,
+                               "p50_ms": _pctl(done, 0.5) * 1e3, "p99_ms": _pctl(done, 0.99) * 1e3},
+        "bit_identical_to_plain": bool(same), "clocks": clk.summary(),
+    }
+
+
+def run_serve(args, ws, rank, local):
+    """Poisson stream of requests (edge counts log-uniform in [1e3, 4e6], n = m / U[2,8],
+    ER / grid / R-MAT mixed; a pool of 48 generated graphs, each request with its own
+    seed) served by lm_submit / lm_poll, against one thread running lm_match on the
+    same arrivals in order.  Offered load swept as fractions of the served capacity."""
+    import torch
+    import paper_1302_4587_gb300 as lm
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = synth.request_sizes(48, seed=5)
+    pool = [synth.request_graph(*sz, name=f"r{i}") for i, sz in enumerate(sizes)]
+    ctx = lm.lm_create(local, None, hbm_budget_bytes=40 << 30)
+    hs = [lm.lm_graph_create(ctx, g.n, g.eu, g.ev, g.w) for g in pool]
+    nreq = max(200, args.steps * 100)
+
+    def serve(arr):
+        """Submit at the arrival times; returns latencies (s) and the makespan."""
+        t0 = time.perf_counter()
+        out = {}
+        pending = {}
+        lat = []
+        i = 0
+        while i < len(arr) or pending:
+            now = time.perf_counter() - t0
+            while i < len(arr) and arr[i] <= now:
+                g = pool[i % len(pool)]
+                mate = torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n]
+                try:
+                    tk = lm.lm_submit(ctx, hs[i % len(pool)], 2000 + i, mate)
+                except lm.LmError as e:
+                    if e.code == lm.LM_EAGAIN:
+                        break
+                    raise
+                pending[tk] = (arr[i], mate, i)
+                i += 1
+            for tk in list(pending):
+                dn, _ = lm.lm_poll(ctx, tk)
+                if dn:
+                    a, mate, idx = pending.pop(tk)
+                    lat.append(time.perf_counter() - t0 - a)
+                    out[idx] = mate
+            time.sleep(0.0001)
+        return lat, time.perf_counter() - t0, out
+
+    def plain(arr):
+        t0 = time.perf_counter()
+        lat = []
+        for i, a in enumerate(arr):
+            while time.perf_counter() - t0 < a:
+                time.sleep(0.00005)
+            g = pool[i % len(pool)]
+            mate = torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n]
+            lm.lm_match(ctx, hs[i % len(pool)], 2000 + i, mate)
+            lat.append(time.perf_counter() - t0 - a)
+        return lat, time.perf_counter() - t0
+
+    # warm-up and capacity: everything offered at t = 0
+    serve(np.zeros(len(pool)))
+    lat0, span0, outs = serve(np.zeros(nreq))
+    cap = nreq / span0
+    # a check that the mix changes no result: served mates equal lm_match alone
+    same = True
+    for idx in list(outs)[:16]:
+        g = pool[idx % len(pool)]
+        ref = torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n]
+        lm.lm_match(ctx, hs[idx % len(pool)], 2000 + idx, ref)
+        same &= bool(torch.equal(ref, outs[idx]))
+    points = []
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+        arr = synth.arrivals(nreq, frac * cap, seed=5)
+        sl, sspan, _ = serve(arr)
+        pl, pspan = plain(arr)
+        w = nreq // 10  # first 10% are warm-up
+        points.append({"offered_per_s": frac * cap,
+                       "served": {"graphs_per_s": nreq / sspan, "p50_ms": _pctl(sl[w:], 0.5) * 1e3,
+                                  "p99_ms": _pctl(sl[w:], 0.99) * 1e3},
+                       "plain": {"graphs_per_s": nreq / pspan, "p50_ms": _pctl(pl[w:], 0.5) * 1e3,
+                                 "p99_ms": _pctl(pl[w:], 0.99) * 1e3}})
+    for h in hs:
+        lm.lm_graph_destroy(h)
+    lm.lm_destroy(ctx)
+    return {
+        "metric": "graphs/s (served, saturation)", "value": ws * cap, "unit": "graphs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": 1, "ms_per_step": span0 * 1e3 / nreq, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
+        "config": {"workload": "serve", "requests_per_point": nreq, "pool_graphs": len(pool),
+                   "mean_m": sum(g.m for g in pool) / len(pool), "hbm_budget_gb": 40,
+                   "desc": "m log-uniform [1e3,4e6], n = m/U[2,8], ER/grid/R-MAT, w~U[0,1), gen seed 5"},
+        "capacity_p50_ms": _pctl(lat0, 0.5) * 1e3, "capacity_p99_ms": _pctl(lat0, 0.99) * 1e3,
+        "load_sweep": points, "served_equals_alone": bool(same),
+    }
 
 
 def cpu_baseline(budget_s: float = 20.0):
@@ -294,7 +475,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
-    ap.add_argument("--workload", default="rmat23", choices=["rmat23", "rmat21", "grid", "er"])
+    ap.add_argument("--workload", default="rmat23", choices=["rmat23", "rmat21", "grid", "er", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = _dist()
@@ -307,6 +488,14 @@ def main():
         out = run_reference(args, ws, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload in ("batch", "serve"):
+        out = (run_batch if args.workload == "batch" else run_serve)(args, ws, rank, local)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     out, g = run_lm(args, ws, rank, local)
     if rank == 0:

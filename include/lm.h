@@ -74,10 +74,10 @@ typedef struct {
 #define LM_STATS_ROUNDS 64
 /* kernel kinds (index into the per-kind arrays of lm_stats) */
 #define LM_K_INIT    0   /* reset of mate / candidate / deletion state */
-#define LM_K_SWEEP   1   /* candidate (segmented max) + deletion + compaction over live entries */
-#define LM_K_VERTEX  2   /* mutual-choice match over live vertices + tile index */
-#define LM_K_TAIL    3   /* single-CTA finish of the last rounds */
-#define LM_K_OTHER   4   /* result conversion, batch set-up */
+#define LM_K_SWEEP   1   /* k_sweep: deletion + compaction + next candidates over live rows */
+#define LM_K_VERTEX  2   /* k_vertex: mutual-choice match over live rows + task lists */
+#define LM_K_CAND    3   /* k_round0: round-0 candidates over the input arrays in tiles */
+#define LM_K_OTHER   4   /* cut rows of round 0, loop checks, result conversion, batch set-up */
 #define LM_K_COUNT   5
 
 typedef struct {
@@ -89,7 +89,6 @@ typedef struct {
     /* filled only with LM_F_PROFILE: */
     double   kernel_ms[LM_K_COUNT];         /* summed device time per kernel kind */
     uint32_t kernel_launches[LM_K_COUNT];   /* launches per kernel kind */
-    uint64_t kernel_bytes[LM_K_COUNT];      /* modelled algorithmic HBM bytes per kernel kind */
     double   total_ms;                      /* device time from first to last kernel of the call */
 } lm_stats;
 

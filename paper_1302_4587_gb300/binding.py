@@ -20,7 +20,7 @@ LM_NIL = 0xFFFFFFFF
 LM_HOST, LM_DEVICE = 0, 1
 LM_F_PROFILE = 1
 LM_STATS_ROUNDS = 64
-LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_TAIL, LM_K_OTHER, LM_K_COUNT = range(6)
+LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_COUNT = range(6)
 
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
@@ -38,7 +38,7 @@ class LmStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("matched", ctypes.c_uint64),
                 ("round_m", ctypes.c_uint64 * LM_STATS_ROUNDS), ("round_n", ctypes.c_uint64 * LM_STATS_ROUNDS),
                 ("kernel_ms", ctypes.c_double * LM_K_COUNT), ("kernel_launches", ctypes.c_uint32 * LM_K_COUNT),
-                ("kernel_bytes", ctypes.c_uint64 * LM_K_COUNT), ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double)]
 
     def to_dict(self) -> dict:
         r = int(self.rounds)

@@ -365,7 +365,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         prof.begin(LM_K_INIT);
         LM_CK(ctx, launch_init(s, &D->init));
         prof.end();
-        prof.begin(LM_K_SWEEP);
+        prof.begin(LM_K_CAND);
         LM_CK(ctx, launch_round0(s, &D->r0));
         prof.end();
         prof.begin(LM_K_OTHER);
@@ -405,8 +405,9 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         // 2 sweeps), then per pair of rounds 2 vertex passes + 2 sweeps + 1 check; round 1
         // leaves DevState::round at 2 and every later vertex pass advances it
         const uint32_t pairs = (e.st_host->round >= 2) ? (e.st_host->round - 2) / 2 : 0;
+        prof.launches[LM_K_CAND] += 1;
         prof.launches[LM_K_VERTEX] += 2 + 2 * pairs;
-        prof.launches[LM_K_SWEEP] += 3 + 2 * pairs;
+        prof.launches[LM_K_SWEEP] += 2 + 2 * pairs;
         prof.launches[LM_K_OTHER] += 1 + pairs;
     }
     return check_err(ctx, e);
