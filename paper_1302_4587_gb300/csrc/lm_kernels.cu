@@ -96,6 +96,12 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
     }
     return x;
 }
+// device-scope fetch-and-add with acquire-release ordering
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ void set_err(DevState* st, uint32_t bit, uint32_t info) {
     if ((atomicOr(&st->err, bit) & bit) == 0) st->err_info = info;
 }
@@ -364,15 +370,19 @@ __device__ __forceinline__ uint32_t recover_nbr(const SweepArgs& a, uint32_t v, 
     return recover_nbr_seg(a.segs[g], a.st, v, K);
 }
 
-// key of entry q of a row: the live buffer's key, or ord(w) << 32 | perm_seed(edge id) from the input word
+// the stored word of entry q (input: ord(w) << 32 | edge id; live: the key) and its key
 template <bool INPUT>
-__device__ __forceinline__ uint64_t entry_key(const SweepArgs& a, uint32_t g, uint32_t q) {
+__device__ __forceinline__ uint64_t entry_word(const SweepArgs& a, uint32_t g, uint32_t q) {
+    if (INPUT) return __ldcs(a.segs[g].pk + q);
+    return __ldcs(a.in_key + q);
+}
+template <bool INPUT>
+__device__ __forceinline__ uint64_t word_key(const SweepArgs& a, uint32_t g, uint64_t w) {
     if (INPUT) {
         const SegIn& sg = a.segs[g];
-        const uint64_t w = __ldcs(sg.pk + q);
         return (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, sg.k0, sg.k1);
     }
-    return __ldcs(a.in_key + q);
+    return w;
 }
 template <bool INPUT>
 __device__ __forceinline__ uint32_t entry_nbr(const SweepArgs& a, uint32_t g, uint32_t q) {
@@ -430,12 +440,12 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 q[i] = W.roff[rr] + (f - W.pre[rr]);
             }
         }
-        // neighbours (deletion test) or, without deletion, the keys directly
+        // neighbours and entry words together (one round trip), then the deletion test
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             if (r[i] == 32) continue;
             if (COMPACT) u[i] = entry_nbr<INPUT>(a, W.rseg[r[i]], q[i]);
-            else key[i] = entry_key<INPUT>(a, W.rseg[r[i]], q[i]);
+            key[i] = entry_word<INPUT>(a, W.rseg[r[i]], q[i]);
         }
         if (COMPACT) {
             bool keep[SG];
@@ -448,8 +458,11 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 }
             }
 #pragma unroll
+            for (int i = 0; i < SG; i++) key[i] = keep[i] ? word_key<INPUT>(a, W.rseg[r[i]], key[i]) : 0ull;
+        } else {
+#pragma unroll
             for (int i = 0; i < SG; i++)
-                if (keep[i]) key[i] = entry_key<INPUT>(a, W.rseg[r[i]], q[i]);
+                if (r[i] != 32) key[i] = word_key<INPUT>(a, W.rseg[r[i]], key[i]);
         }
         // per row: compaction slots and maximum, aggregated over the lanes of a row
 #pragma unroll
@@ -509,7 +522,7 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
             key[i] = 0;
             if (jj < je) {
                 if (COMPACT) u[i] = entry_nbr<INPUT>(a, g, off + jj);
-                else key[i] = entry_key<INPUT>(a, g, off + jj);
+                key[i] = entry_word<INPUT>(a, g, off + jj);
             }
         }
         if (COMPACT) {
@@ -523,8 +536,11 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
                 }
             }
 #pragma unroll
+            for (int i = 0; i < SG; i++) key[i] = keep[i] ? word_key<INPUT>(a, g, key[i]) : 0ull;
+        } else {
+#pragma unroll
             for (int i = 0; i < SG; i++)
-                if (keep[i]) key[i] = entry_key<INPUT>(a, g, off + j + i * 32 + lane);
+                if (j + i * 32 + lane < je) key[i] = word_key<INPUT>(a, g, key[i]);
         }
         uint32_t ball[SG], sub = 0;
 #pragma unroll
@@ -555,11 +571,11 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
     if (lane == 0) {
         const uint64_t K = ((uint64_t)hi << 32) | lo;
         if (K) atomicMax(&va.bkey[v], (unsigned long long)K);
-        __threadfence();
         const uint32_t nch = (L + CHUNK - 1) / CHUNK;
-        const uint32_t old = atomicAdd(&va.bcnt[v], 1u);
+        // release: this chunk's maximum is visible before its count; acquire: the last
+        // chunk sees every other chunk's maximum
+        const uint32_t old = atom_add_acq_rel(&va.bcnt[v], 1u);
         if (old == nch - 1) {
-            __threadfence();
             const uint64_t R = *reinterpret_cast<volatile unsigned long long*>(&va.bkey[v]);
             va.bkey[v] = 0;
             va.bcnt[v] = 0;
@@ -584,11 +600,13 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
     }
     const uint32_t total = nC + (nR + 31) / 32;
     (void)gw; (void)nw;
+    // the next task's index is fetched while the current one runs
+    uint32_t t_next = 0;
+    if (lane == 0) t_next = atomicAdd(a.task_ctr, 1u);
     for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(a.task_ctr, 1u);
-        t = __shfl_sync(FULL, t, 0);
+        const uint32_t t = __shfl_sync(FULL, t_next, 0);
         if (t >= total) break;
+        if (lane == 0) t_next = atomicAdd(a.task_ctr, 1u);
         if (t < nC) do_chunk<INPUT, COMPACT>(a, t, lane);
         else do_rows<INPUT, COMPACT>(a, W, t - nC, nR, lane);
     }
