@@ -30,9 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "input edges/s to maximal matching"
 
-# dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match,
-# from one ncu capture of the same workload (None until taken for the current kernels)
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
+# an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
+# capture with several metrics); None for workloads without a capture of the current kernels
+TRAFFIC = {"rmat23": 7874387140}
 
 
 def _peaks():
@@ -58,7 +59,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -107,13 +108,21 @@ def _dist():
 
 
 def _barrier_max(value: float, ws: int) -> float:
+    """Max of a per-rank value over all ranks (the slowest rank's time)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(units_per_rank: int, ws: int, ms_max: float) -> float:
+    """Replicas: every rank processes the same units; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max * 1e-3)
 
 
 def _barrier(ws: int):
@@ -176,6 +185,7 @@ def run_lm(args, ws, rank, local):
     ev = torch.from_numpy(g.ev.view(np.int32)).to(dev)
     w = torch.from_numpy(g.w).to(dev)
     h = lm.lm_graph_create(ctx, g.n, eu, ev, w)
+    graph_bytes = lm.lm_graph_info(h)[2]
     del eu, ev, w
     mate = torch.empty(g.n, dtype=torch.int32, device=dev)
     launches = 0
@@ -248,11 +258,12 @@ def run_lm(args, ws, rank, local):
     lm.lm_graph_destroy(h)
     lm.lm_destroy(ctx)
     out = {
-        "metric": METRIC, "value": ws * g.m / (ms_max * 1e-3), "unit": "edges/s", "n_gpus": ws,
+        "metric": METRIC, "value": whole_job_value(g.m, ws, ms_max), "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "seed": seed,
-                   "rounds": pst["rounds"], "l2": "inputs larger than L2 (graph arrays 3.1 GB)",
+                   "rounds": pst["rounds"], "graph_bytes": graph_bytes,
+                   "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -290,6 +301,7 @@ def run_batch(args, ws, rank, local):
     seeds = [1000 + i for i in range(len(gs))]
     ctx = lm.lm_create(local, stream)
     hs = [lm.lm_graph_create(ctx, g.n, g.eu, g.ev, g.w) for g in gs]
+    graph_bytes = sum(lm.lm_graph_info(h)[2] for h in hs)
     mates = [torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n] for g in gs]
     m_tot = sum(g.m for g in gs)
     for _ in range(max(args.warmup, 3)):
@@ -326,7 +338,8 @@ def run_batch(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
         "config": {"workload": "batch", "graphs": len(gs), "sum_m": m_tot, "sum_n": sum(g.n for g in gs),
                    "desc": "n log-uniform [64,65536], degree U[4,16], ER/grid/R-MAT mixed, w~U[0,1), gen seed 4",
-                   "l2": "inputs larger than L2 (sum of graphs about 2.3 GB)"},
+                   "graph_bytes": graph_bytes,
+                   "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)"},
         "edges_per_s": ws * m_tot / (ms * 1e-3), "p50_ms": ms, "p99_ms": ms,
         "plain_back_to_back": {"graphs_per_s": len(gs) / plain_s, "edges_per_s": m_tot / plain_s,
                                "p50_ms": _pctl(done, 0.5) * 1e3, "p99_ms": _pctl(done, 0.99) * 1e3},

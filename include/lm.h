@@ -15,7 +15,7 @@
  * of the edge in the caller's edge list).  This total order stands in for the
  * paper's "ties broken by random perturbation" (Sec. 1); it is fixed for the
  * whole call.  With a strict order fixed for the run, local max selects
- * exactly the greedy matching of Sec. 4 under the same order, so the result
+ * exactly the greedy matching of Sec. 3 under the same order, so the result
  * is unique for a given (graph, seed).
  *     perm_seed(e) = fmix32(fmix32(e ^ k0) ^ k1),
  *     (k0, k1) = low and high 32 bits of SplitMix64(seed) (its first output),
@@ -102,7 +102,7 @@ int  lm_create(const lm_config* cfg, lm_ctx** out);
  * destroyed first.  NULL is ignored. */
 void lm_destroy(lm_ctx* ctx);
 
-/* Build a device graph from an undirected edge list (Sec. 2, "graph
+/* Build a device graph from an undirected edge list (Sec. 2.1, "graph
  * representation": offsets V over the vertices, the adjacency array A of
  * (vertex, edge) entries, and per-edge records).  Edge i joins eu[i] and ev[i]
  * with weight w[i]; its index i is the edge id used by perm_seed.  Parallel

@@ -9,7 +9,7 @@ use into ``oracle/_build/``); this module only marshals numpy arrays.
 Passages followed (see the header of ``oracle.c`` for each function):
   * the edge order -- Sec. 1 (local max, random-perturbation tie breaking),
     read as (float32 weight, seeded bijective permutation of the edge index);
-  * ``greedy``        -- Sec. 4, the greedy algorithm (the oracle for mate[]);
+  * ``greedy``        -- Sec. 3, the greedy algorithm (the oracle for mate[]);
   * ``seq_local_max`` -- Sec. 2, sequential model, three passes per iteration;
   * ``brute_mwm``     -- exact maximum weight matching for small n, used for
     the 1/2-approximation property (Sec. 1).
@@ -124,7 +124,7 @@ def keys(w, seed: int) -> np.ndarray:
 
 
 def greedy(n: int, eu, ev, w, seed: int) -> np.ndarray:
-    """mate[] of the greedy matching under the order K(e) (Sec. 4)."""
+    """mate[] of the greedy matching under the order K(e) (Sec. 3)."""
     eu, up = _u32(eu)
     ev, vp = _u32(ev)
     w, wp = _f32(w)

@@ -15,7 +15,7 @@
  *       local max algorithm; Sec. 2, sequential model).  Reading: weight
  *       first, then a seeded bijective permutation of the edge index; the
  *       perturbation is drawn once per call and never renewed.
- *   lmo_greedy  -- the greedy algorithm of Sec. 4 (sort by decreasing
+ *   lmo_greedy  -- the greedy algorithm of Sec. 3 (sort by decreasing
  *       weight, scan, take an edge when both ends are free).  For a strict
  *       total order fixed for the whole run, local max selects exactly this
  *       matching; this is the oracle for the GPU's mate[].
@@ -112,7 +112,7 @@ void lmo_keys(uint64_t m, const float* w, uint64_t seed, uint64_t* out) {
     for (uint64_t e = 0; e < m; e++) out[e] = lmo_key(w[e], seed, (uint32_t)e);
 }
 
-/* ---- greedy (Sec. 4) ------------------------------------------------ */
+/* ---- greedy (Sec. 3) ------------------------------------------------ */
 
 typedef struct { uint64_t key; uint32_t e; } kv;
 

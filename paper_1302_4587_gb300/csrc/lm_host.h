@@ -82,7 +82,7 @@ struct lm_ctx {
     lm::ServeState* serve = nullptr;
 };
 
-// A device graph (Sec. 2 representation): per-vertex offsets V into the
+// A device graph (Sec. 2.1 representation): per-vertex offsets V into the
 // adjacency array A, whose entries carry the neighbour and a word with the
 // order-preserving image of the edge weight and the edge index, plus the
 // edge records E (both endpoints of every edge).

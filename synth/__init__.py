@@ -6,7 +6,7 @@ This module only draws graphs (edge lists ``eu, ev`` of uint32 and weights
 heavy lifting is plain C (``gen.c``), compiled on first use into
 ``synth/_build/``.
 
-Workload families (shapes of the paper's inputs, Sec. 4; the paper's own data
+Workload families (shapes of the paper's inputs, Sec. 3; the paper's own data
 sets are not available, so these stand in for them):
 
 * ``er``    -- random graph G(n, m) with weights uniform in [0, 1)

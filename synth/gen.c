@@ -12,7 +12,7 @@
  * function of (seed, index) and the large generators can run on several
  * threads while producing identical bytes.
  *
- * Workload shapes follow the paper's input families (Sec. 4): random graphs
+ * Workload shapes follow the paper's input families (Sec. 3): random graphs
  * with uniform [0,1) weights, a locality-heavy grid family standing in for the
  * geometric and sparse-matrix inputs, and a skewed R-MAT family (Chakrabarti,
  * Zhan, Faloutsos 2004) standing in for the large irregular graphs.

@@ -15,12 +15,24 @@ from helpers import dominated, is_matching, is_maximal, load_hand_cases
 
 pytestmark = pytest.mark.gpu
 
-TILE = 2048  # entries per sweep tile in the library
+TILE = 1024   # entries per round-0 tile (TILE0)
+CHUNK = 512   # entries per chunk task of a long row
+RMAX = 64     # longest row handled as part of a 32-row batch
 
 
 @pytest.fixture(scope="module")
 def lmctx():
+    # profiled context: kernels launched one by one on the stream, per-kernel events
     c = Lm(profile=True)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def lmgraph():
+    # default context: the whole job as one CUDA graph with a device-driven round loop
+    # (the launch configuration the benchmark times)
+    c = Lm(profile=False)
     yield c
     c.close()
 
@@ -217,12 +229,56 @@ def test_served_results_equal_alone(lmctx):
         srv.close()
 
 
+def _stars(sizes, seed):
+    # disjoint stars with the given leaf counts plus a path through their centres
+    eu, ev, base, centres = [], [], 0, []
+    for k in sizes:
+        centres.append(base)
+        eu.append(np.full(k, base, np.uint32))
+        ev.append(np.arange(base + 1, base + k + 1, dtype=np.uint32))
+        base += k + 1
+    c = np.array(centres, np.uint32)
+    eu.append(c[:-1])
+    ev.append(c[1:])
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    return synth.Graph(base, eu, ev, synth.weights(eu.shape[0], seed), f"stars{seed}")
+
+
+def test_row_length_boundaries(lmctx):
+    # rows right at the short-row limit, the chunk size and the tile size
+    sizes = [RMAX - 2, RMAX - 1, RMAX, RMAX + 1, CHUNK - 1, CHUNK, CHUNK + 1, 2 * CHUNK + 1,
+             TILE - 1, TILE, TILE + 1, 3 * TILE]
+    for seed in (1, 2):
+        _check(lmctx, _stars(sizes, seed), seed)
+
+
+def test_rows_starting_on_tile_boundaries(lmctx):
+    # a first row of exactly one tile, so the next rows start on tile boundaries
+    g = _stars([TILE - 1, TILE, 2 * TILE - 1, 1, 1, TILE], 5)
+    _check(lmctx, g, 9)
+
+
+@pytest.mark.parametrize("which", ["er", "grid", "hubs", "small"])
+def test_graph_launch_path(lmgraph, which):
+    """The CUDA-graph path (device-driven loop) against the oracle."""
+    if which == "er":
+        g, seed = synth.er(10_000, 50_000, seed=1), 101
+    elif which == "grid":
+        g, seed = synth.grid(256, 256, 0.05, seed=2), 102
+    elif which == "hubs":
+        g, seed = _stars([3 * TILE + 7, RMAX + 1, CHUNK + 3, 5], 6), 6
+    else:
+        g, seed = synth.pairs(40, 300, 11, "few"), 11
+    _check(lmgraph, g, seed)
+
+
 @pytest.mark.slow
-def test_rmat_scale23_full_parity(lmctx):
+def test_rmat_scale23_full_parity(lmgraph):
     """The headline workload at full size, in the benchmark's launch
-    configuration, checked against the oracle element by element."""
+    configuration (one CUDA graph per match), checked against the oracle
+    element by element."""
     g = synth.rmat(scale=23, edge_factor=16, seed=3)
-    mate, st = lmctx.match(g, 103)
+    mate, st = lmgraph.match(g, 103)
     want = oracle.greedy(g.n, g.eu, g.ev, g.w, 103)
     bad = np.nonzero(mate != want)[0]
     assert bad.size == 0, f"{bad.size} vertices differ"
