@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -163,7 +164,7 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     c.add(&nw.len[0], V);
     c.add(&nw.len[1], V);
     c.add(&nw.cnbr, V);
-    c.add(&nw.dead, V);
+    c.add(&nw.dead, V / 32 + 2);
     c.add(&nw.mate, V);
     c.add(&nw.bcnt, V);
     c.add(&nw.bkey, V);
@@ -294,6 +295,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     memset(&A, 0, sizeof A);
     A.init.mate = job.va.mate;
     A.init.dead = job.va.dead;
+    A.init.dbase = 0;
     A.init.bcnt = job.va.bcnt;
     A.init.bkey = job.va.bkey;
     A.init.n = job.va.nvert;
@@ -383,6 +385,8 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         prof.begin(LM_K_SWEEP);
         LM_CK(ctx, launch_sweep_live(s, &D->s[1]));
         prof.end();
+        // the same limits as the device-driven loop: the round cap and LOOP_LIMIT_NS
+        const auto t_start = std::chrono::steady_clock::now();
         for (uint32_t pair = 0;; pair++) {
             for (int k = 2; k < 4; k++) {
                 prof.begin(LM_K_VERTEX);
@@ -396,6 +400,9 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
             if (e.st_host->round > job.nedges + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            const auto waited = std::chrono::steady_clock::now() - t_start;
+            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)LOOP_LIMIT_NS)
+                return fail(ctx, LM_ETIMEOUT, "round loop exceeded its time limit");
         }
     }
     LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));

@@ -25,7 +25,7 @@ struct Workspace {
     uint32_t* gid = nullptr;         // [cap_v] graph of each vertex (batches)
     uint32_t* len[2] = {nullptr, nullptr};   // [cap_v] live row lengths by round parity
     uint32_t* cnbr = nullptr;        // [cap_v] chosen neighbour
-    uint8_t* dead = nullptr;         // [cap_v] matched flag
+    uint32_t* dead = nullptr;        // [cap_v / 32 + 2] matched bit per vertex
     uint32_t* mate = nullptr;        // [cap_v] union result / staging
     uint32_t* bcnt = nullptr;        // [cap_v] finished chunks of long rows
     unsigned long long* bkey = nullptr;  // [cap_v] heaviest surviving key of long rows

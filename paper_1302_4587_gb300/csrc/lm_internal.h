@@ -106,7 +106,7 @@ struct VertexArrays {
     const uint32_t* start;    // [N] union entry index of each vertex's row
     uint32_t* len[2];         // [N] live length of each row, by round parity
     uint32_t* cnbr;           // [N] neighbour over the heaviest live edge (valid for live rows)
-    uint8_t* dead;            // [N] 1 once matched
+    uint32_t* dead;           // [N / 32 + 1] bit v set once v is matched (read through the read-only cache)
     uint32_t* mate;           // [N] result (union ids)
     uint32_t* bcnt;           // [N] chunks of a long row finished in the running sweep
     unsigned long long* bkey; // [N] heaviest surviving key of a long row (0 between sweeps)
@@ -169,7 +169,8 @@ struct Round0Args {
 // v[2]/s[2], v[3]/s[3] run rounds of parity 0 and 1.
 struct InitArgs {
     uint32_t* mate;
-    uint8_t* dead;
+    uint32_t* dead;           // the whole bitmap; bits [dbase, dbase + n) are cleared
+    uint32_t dbase;
     uint32_t* bcnt;
     unsigned long long* bkey;
     uint32_t n;

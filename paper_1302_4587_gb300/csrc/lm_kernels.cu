@@ -96,6 +96,11 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
     }
     return x;
 }
+// matched bit of vertex u; the bitmap is read-only during a sweep, so it may go
+// through the non-coherent (read-only) cache
+__device__ __forceinline__ bool is_dead(const VertexArrays& va, uint32_t u) {
+    return (__ldg(&va.dead[u >> 5]) >> (u & 31)) & 1u;
+}
 // device-scope fetch-and-add with acquire-release ordering
 __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
     uint32_t old;
@@ -125,7 +130,7 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 __global__ void k_init(const InitArgs* __restrict__ pa) {
     const InitArgs& A = *pa;
     uint32_t* mate = A.mate;
-    uint8_t* dead = A.dead;
+    uint32_t* dead = A.dead;
     uint32_t* bcnt = A.bcnt;
     unsigned long long* bkey = A.bkey;
     const uint32_t n = A.n;
@@ -133,9 +138,24 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         if (mate) mate[v] = NIL;
-        dead[v] = 0;
         bcnt[v] = 0;
         bkey[v] = 0;
+    }
+    // matched bits [dbase, dbase + n): whole words are stored, the partial words at
+    // either end are cleared with atomicAnd (their other bits belong to other jobs)
+    if (n) {
+        const uint32_t b0 = A.dbase, b1 = A.dbase + n;
+        const uint32_t w0 = b0 >> 5, w1 = (b1 - 1) >> 5;
+        for (uint32_t w = w0 + blockIdx.x * blockDim.x + threadIdx.x; w <= w1; w += stride) {
+            const uint32_t lo = max(b0, w * 32u), hi = min(b1, w * 32u + 32u);
+            if (lo == w * 32u && hi == w * 32u + 32u) {
+                dead[w] = 0;
+            } else {
+                const uint32_t width = hi - lo;
+                const uint32_t mask = (width == 32u ? FULL : ((1u << width) - 1u)) << (lo & 31u);
+                atomicAnd(&dead[w], ~mask);
+            }
+        }
     }
     if (st && blockIdx.x == 0) {
         for (int i = threadIdx.x; i < 64; i += blockDim.x) { st->ring_m[i] = 0; st->ring_n[i] = 0; }
@@ -248,7 +268,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                 const bool matched = a.match && back == v;
                 if (matched) {
                     va.mate[v] = uu[i];
-                    va.dead[v] = 1;
+                    atomicOr(&va.dead[v >> 5], 1u << (v & 31));
                     my_match++;
                 } else {
                     open_row = true;
@@ -454,7 +474,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 keep[i] = r[i] != 32;
                 if (keep[i]) {
                     if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-                    else keep[i] = va.dead[u[i]] == 0;
+                    else keep[i] = !is_dead(va, u[i]);
                 }
             }
 #pragma unroll
@@ -532,7 +552,7 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
                 keep[i] = u[i] != NIL;
                 if (keep[i]) {
                     if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-                    else keep[i] = va.dead[u[i]] == 0;
+                    else keep[i] = !is_dead(va, u[i]);
                 }
             }
 #pragma unroll

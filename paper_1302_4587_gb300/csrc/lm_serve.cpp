@@ -140,7 +140,8 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         LM_CK(ctx, launch_req_setup(s, r->g->off, r->g->n, r->vbase, r->ebase, r->slot, w.start, w.gid));
         InitArgs& ia = A.init[k];
         ia.mate = w.mate + r->vbase;
-        ia.dead = w.dead + r->vbase;
+        ia.dead = w.dead;
+        ia.dbase = r->vbase;
         ia.bcnt = w.bcnt + r->vbase;
         ia.bkey = w.bkey + r->vbase;
         ia.n = r->g->n;
