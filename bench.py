@@ -240,20 +240,25 @@ def run_lm(args, ws, rank, local):
         pw = torch.from_numpy(g.w).pin_memory()
         hmate = torch.empty(g.n, dtype=torch.int32).pin_memory()
         reps = max(1, min(args.steps, 5))
+        e2e_times, parts = [], []
         for i in range(reps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hh = lm.lm_graph_create(ctx, g.n, peu, pev, pw)
-            lm.lm_match(ctx, hh, seed, hmate)
-            lm.lm_graph_destroy(hh)
             t1 = time.perf_counter()
-            if i == 0:
-                e2e_times = []
-            else:
-                e2e_times.append(t1 - t0)
+            lm.lm_match(ctx, hh, seed, hmate)
+            t2 = time.perf_counter()
+            lm.lm_graph_destroy(hh)
+            t3 = time.perf_counter()
+            if i > 0:
+                e2e_times.append(t3 - t0)
+                parts.append((t1 - t0, t2 - t1, t3 - t2))
         e2e_s = statistics.median(e2e_times)
         e2e = {"value": g.m / e2e_s, "unit": "edges/s", "h2d_bytes_per_step": 12 * g.m,
                "d2h_bytes_per_step": 4 * g.n, "ms_per_step": e2e_s * 1e3,
+               "graph_create_ms": statistics.median(p[0] for p in parts) * 1e3,
+               "match_to_host_ms": statistics.median(p[1] for p in parts) * 1e3,
+               "graph_destroy_ms": statistics.median(p[2] for p in parts) * 1e3,
                "includes": "lm_graph_create from pinned host arrays + lm_match to a pinned host mate + lm_graph_destroy"}
     lm.lm_graph_destroy(h)
     lm.lm_destroy(ctx)

@@ -959,36 +959,66 @@ __global__ void k_round0_cut(const Round0Args* __restrict__ pa) {
 }
 
 // ---------------------------------------------------------------- graph construction
+// Edge-list passes of the graph build.  Lanes of a warp that hit the same
+// vertex (R-MAT hubs) combine into one atomic: the lowest of them adds the
+// group's count and hands each its own slot.
+__device__ __forceinline__ uint32_t warp_add(uint32_t* ctr, uint32_t key, bool active, uint32_t lane) {
+    const uint32_t act = __ballot_sync(FULL, active);
+    const uint32_t peers = __match_any_sync(FULL, key) & act;
+    uint32_t base = 0;
+    if (active) {
+        const uint32_t leader = __ffs(peers) - 1;
+        if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader) + __popc(peers & ((1u << lane) - 1u));
+    }
+    return base;
+}
+
 __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n, uint32_t m,
                                 uint32_t* deg, uint32_t* err) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const uint32_t u = eu[e], v = ev[e];
-        const uint32_t wb = __float_as_uint(w[e]);
-        const bool nan = ((wb & 0x7F800000u) == 0x7F800000u) && (wb & 0x007FFFFFu);
-        if (u >= n || v >= n || u == v || nan) {
-            atomicOr(err, 1u);
-            continue;
+    const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
+    const uint32_t mr = (m + 31) & ~31u;  // whole warps iterate together
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < mr; e += stride) {
+        bool ok = e < m;
+        uint32_t u = 0, v = 0;
+        if (ok) {
+            u = eu[e];
+            v = ev[e];
+            const uint32_t wb = __float_as_uint(w[e]);
+            const bool nan = ((wb & 0x7F800000u) == 0x7F800000u) && (wb & 0x007FFFFFu);
+            if (u >= n || v >= n || u == v || nan) {
+                atomicOr(err, 1u);
+                ok = false;
+            }
         }
-        atomicAdd(&deg[u], 1u);
-        atomicAdd(&deg[v], 1u);
+        warp_add(&deg[ok ? u : 0], u, ok, lane);
+        warp_add(&deg[ok ? v : 0], v, ok, lane);
     }
 }
-
 __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
                              uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const uint32_t u = eu[e], v = ev[e];
-        const uint64_t word = ((uint64_t)ord_of_bits(__float_as_uint(w[e])) << 32) | e;
-        edges[e] = (uint64_t)u | ((uint64_t)v << 32);
-        const uint32_t pu = atomicAdd(&cursor[u], 1u);
-        nbr[pu] = v; pk[pu] = word;
-        const uint32_t pv = atomicAdd(&cursor[v], 1u);
-        nbr[pv] = u; pk[pv] = word;
+    const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
+    const uint32_t mr = (m + 31) & ~31u;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < mr; e += stride) {
+        const bool ok = e < m;
+        uint32_t u = 0, v = 0;
+        uint64_t word = 0;
+        if (ok) {
+            u = eu[e];
+            v = ev[e];
+            word = ((uint64_t)ord_of_bits(__float_as_uint(w[e])) << 32) | e;
+            edges[e] = (uint64_t)u | ((uint64_t)v << 32);
+        }
+        const uint32_t pu = warp_add(&cursor[u], u, ok, lane);
+        const uint32_t pv = warp_add(&cursor[v], v, ok, lane);
+        if (ok) {
+            nbr[pu] = v;
+            pk[pu] = word;
+            nbr[pv] = u;
+            pk[pv] = word;
+        }
     }
 }
-
 __global__ void k_nonzero_flags(const uint32_t* deg, uint32_t n, uint32_t* flags) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) flags[v] = deg[v] ? 1u : 0u;
