@@ -31,11 +31,14 @@ namespace lm {
 
 constexpr uint32_t NIL = 0xFFFFFFFFu;
 
+// Task sizes of the sweep (measured on R-MAT scale 23: batching rows of up to
+// 2048 live entries 32 to a warp beats splitting them into chunk tasks, whose
+// slots need a global atomic per step)
 #ifndef LM_CHUNK
-#define LM_CHUNK 512
+#define LM_CHUNK 4096
 #endif
 #ifndef LM_RMAX
-#define LM_RMAX 64
+#define LM_RMAX 2048
 #endif
 constexpr uint32_t CHUNK = LM_CHUNK;        // long rows are split into chunks of this size
 #ifndef LM_TILE0

@@ -16,8 +16,8 @@ from helpers import dominated, is_matching, is_maximal, load_hand_cases
 pytestmark = pytest.mark.gpu
 
 TILE = 1024   # entries per round-0 tile (TILE0)
-CHUNK = 512   # entries per chunk task of a long row
-RMAX = 64     # longest row handled as part of a 32-row batch
+CHUNK = 4096  # entries per chunk task of a long row
+RMAX = 2048   # longest row handled as part of a 32-row batch
 
 
 @pytest.fixture(scope="module")
