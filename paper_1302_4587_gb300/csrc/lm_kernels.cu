@@ -488,6 +488,29 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             const bool surv = key[i] != 0;
+            if (__shfl_sync(FULL, r[i], 0) == __shfl_sync(FULL, r[i], 31)) {
+                // the whole group lies in one row: full-warp vote and reductions
+                const uint32_t ball = __ballot_sync(FULL, surv);
+                if (ball) {
+                    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i] >> 32));
+                    const uint32_t lo =
+                        __reduce_max_sync(FULL, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
+                    uint32_t base = 0;
+                    if (lane == 0) {
+                        if (COMPACT) base = atomicAdd(&W.rcnt[r[i]], (uint32_t)__popc(ball));
+                        atomicMax(&W.rkey[r[i]], ((unsigned long long)hi << 32) | lo);
+                    }
+                    if (COMPACT) {
+                        base = __shfl_sync(FULL, base, 0);
+                        if (surv) {
+                            const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & lt);
+                            a.out_key[pos] = key[i];
+                            a.out_nbr[pos] = u[i];
+                        }
+                    }
+                }
+                continue;
+            }
             const uint32_t grp = __match_any_sync(FULL, surv ? r[i] : 64u + lane);
             if (surv) {
                 const int leader = __ffs(grp) - 1;
@@ -654,7 +677,7 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
 #define LM_R0C 256
 #endif
 #ifndef LM_R0MINB
-#define LM_R0MINB 3
+#define LM_R0MINB 4   // CTAs per SM (56 registers a thread, about 45 KB of shared memory a CTA)
 #endif
 constexpr int R0S = LM_R0S;                         // pipeline stages
 constexpr int R0C = LM_R0C;                         // consumer threads
