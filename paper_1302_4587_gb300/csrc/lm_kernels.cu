@@ -215,6 +215,11 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
         nC = ld_volatile_u32(&a.in.cnt[1]);
         total = nC + nR;
     }
+    // only CTAs with rows take part (CTA 0 closes an empty pass): idle CTAs leave
+    // before touching the exit counter
+    const uint32_t working = (uint32_t)min((uint64_t)gridDim.x, ((uint64_t)total + VT * VI - 1) / (VT * VI));
+    const uint32_t closers = working ? working : 1u;
+    if (blockIdx.x >= closers) return;
     unsigned long long my_rows = 0, my_ent = 0, my_match = 0;
 
     for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
         // the last CTA closes the pass: consumed lists are emptied, round statistics recorded
         __threadfence();
         const uint32_t done = atomicAdd(&st->exit_v, 1u);
-        if (done == gridDim.x - 1) {
+        if (done == closers - 1) {
             __threadfence();
             if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; }
             st->task[0] = 0; st->task[1] = 0; st->task[2] = 0; st->task[3] = 0;
@@ -642,14 +647,14 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
         return;
     }
     const uint32_t total = nC + (nR + 31) / 32;
-    (void)gw; (void)nw;
-    // the next task's index is fetched while the current one runs
+    // a warp's first task is its own index (idle warps leave without an atomic), later
+    // ones come from the counter; the next index is fetched while the current task runs
+    uint32_t t = gw;
+    if (t >= total) return;
     uint32_t t_next = 0;
-    if (lane == 0) t_next = atomicAdd(a.task_ctr, 1u);
-    for (;;) {
-        const uint32_t t = __shfl_sync(FULL, t_next, 0);
+    for (;; t = __shfl_sync(FULL, t_next, 0)) {
         if (t >= total) break;
-        if (lane == 0) t_next = atomicAdd(a.task_ctr, 1u);
+        if (lane == 0) t_next = nw + atomicAdd(a.task_ctr, 1u);
         if (t < nC) do_chunk<INPUT, COMPACT>(a, t, lane);
         else do_rows<INPUT, COMPACT>(a, W, t - nC, nR, lane);
     }
