@@ -369,14 +369,13 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
 #ifndef LM_SWEEP_MINB
 #define LM_SWEEP_MINB 4
 #endif
+
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
 constexpr int SG = LM_SG;      // groups of 32 entries a warp keeps in flight
 
 struct WarpRows {              // one warp's batch of rows
     unsigned long long rkey[32];   // heaviest surviving key per row
     uint32_t rcnt[32];             // survivors per row
-    uint32_t pre[33];              // exclusive prefix of the rows' lengths
-    uint32_t roff[32];             // source index of the row's entry 0
     uint32_t rstart[32];           // union entry index of the row (output base)
     uint32_t rseg[32];             // graph of the row
 };
@@ -439,39 +438,51 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
     W.rcnt[lane] = 0;
     W.rstart[lane] = s0;
     W.rseg[lane] = g;
-    W.roff[lane] = INPUT ? s0 - a.segs[g].ebase : s0;
+    const uint32_t ro = INPUT ? s0 - a.segs[g].ebase : s0;  // source index of the row's entry 0
     const uint32_t incl = warp_incl_scan(L, lane);
-    W.pre[lane + 1] = incl;
-    if (lane == 0) W.pre[0] = 0;
+    const uint32_t ex = incl - L;                             // the row's first flattened entry
     const uint32_t F = __shfl_sync(FULL, incl, 31);
     __syncwarp();
     const uint32_t lt = lanemask_lt();
-    for (uint32_t f0 = 0; f0 < F; f0 += 32 * SG) {
-        uint32_t r[SG], q[SG], u[SG];
-        uint64_t key[SG];
+    // the entries f0 .. f0 + 32 SG - 1 of the flattened batch: row, source index,
+    // neighbour and stored word.  The row of entry g0 + j is the number of rows
+    // starting at or before g0 (a ballot) plus the rows starting inside the group
+    // at positions 1..j (bits of an OR-reduction), minus one; uni[i] says that no
+    // row starts inside group i.
+    auto fetch = [&](uint32_t f0, uint32_t (&r)[SG], uint32_t (&q)[SG], uint32_t (&u)[SG], uint64_t (&key)[SG],
+                     bool (&uni)[SG]) {
 #pragma unroll
         for (int i = 0; i < SG; i++) {
-            const uint32_t f = f0 + i * 32 + lane;
+            const uint32_t g0 = f0 + i * 32, f = g0 + lane;
             r[i] = 32;
             q[i] = 0;
             u[i] = NIL;
             key[i] = 0;
+            uni[i] = true;
+            if (g0 >= F) continue;  // warp-uniform
+            const uint32_t below = __ballot_sync(FULL, ex <= g0);
+            const uint32_t starts = __reduce_or_sync(FULL, (ex > g0 && ex - g0 < 32u) ? 1u << (ex - g0) : 0u);
+            const uint32_t lim = F - g0;
+            uni[i] = (starts & (lim >= 32u ? FULL : (1u << lim) - 1u)) == 0;
+            const uint32_t rr = __popc(below) - 1 + __popc(starts & (FULL >> (31 - lane)));
+            const uint32_t exr = __shfl_sync(FULL, ex, rr & 31u), ror = __shfl_sync(FULL, ro, rr & 31u);
             if (f < F) {
-                uint32_t rr = 0;
-#pragma unroll
-                for (uint32_t step = 16; step > 0; step >>= 1)
-                    if (W.pre[rr + step] <= f) rr += step;
                 r[i] = rr;
-                q[i] = W.roff[rr] + (f - W.pre[rr]);
+                q[i] = ror + (f - exr);
             }
         }
-        // neighbours and entry words together (one round trip), then the deletion test
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             if (r[i] == 32) continue;
             if (COMPACT) u[i] = entry_nbr<INPUT>(a, W.rseg[r[i]], q[i]);
             key[i] = entry_word<INPUT>(a, W.rseg[r[i]], q[i]);
         }
+    };
+    uint32_t r[SG], q[SG], u[SG];
+    uint64_t key[SG];
+    bool uni[SG];
+    fetch(0, r, q, u, key, uni);
+    for (uint32_t f0 = 0; f0 < F; f0 += 32 * SG) {
         if (COMPACT) {
             bool keep[SG];
 #pragma unroll
@@ -493,7 +504,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             const bool surv = key[i] != 0;
-            if (__shfl_sync(FULL, r[i], 0) == __shfl_sync(FULL, r[i], 31)) {
+            if (uni[i]) {
                 // the whole group lies in one row: full-warp vote and reductions
                 const uint32_t ball = __ballot_sync(FULL, surv);
                 if (ball) {
@@ -534,6 +545,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 }
             }
         }
+        if (f0 + 32 * SG < F) fetch(f0 + 32 * SG, r, q, u, key, uni);
     }
     __syncwarp();
     if (v != NIL) {
