@@ -188,6 +188,8 @@ def run_lm(args, ws, rank, local):
     graph_bytes = lm.lm_graph_info(h)[2]
     del eu, ev, w
     mate = torch.empty(g.n, dtype=torch.int32, device=dev)
+    # launch parameters picked by the library's autotuner on this graph (untimed)
+    tuning = lm.lm_autotune(ctx, [h], [seed], [mate])
     launches = 0
     for _ in range(max(args.warmup, 3)):
         _, st = lm.lm_match(ctx, h, seed, mate, stats=True)
@@ -211,6 +213,8 @@ def run_lm(args, ws, rank, local):
 
     # per-kernel device times (CUDA events recorded by the library on its stream)
     pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE)
+    lm.lm_set_tuning(pctx, tuning["rmax"], tuning["chunk"], tuning["sweep_ctas_per_sm"],
+                     tuning["vertex_ctas_per_sm"])
     kms = {k: [] for k in range(lm.LM_K_COUNT)}
     total_ms = []
     for i in range(max(args.warmup, 3) + args.steps):
@@ -269,6 +273,7 @@ def run_lm(args, ws, rank, local):
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "seed": seed,
                    "rounds": pst["rounds"], "graph_bytes": graph_bytes,
                    "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)",
+                   "tuning": tuning,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -310,6 +315,7 @@ def run_batch(args, ws, rank, local):
     mates = [torch.empty(max(g.n, 1), dtype=torch.int32, device=dev)[:g.n] for g in gs]
     m_tot = sum(g.m for g in gs)
     job = lm.BatchArgs(hs, seeds, mates)  # marshalled once, reused by every step
+    tuning = lm.lm_autotune(ctx, job)     # launch parameters picked on this batch (untimed)
     for _ in range(max(args.warmup, 3)):
         lm.lm_batch_match(ctx, job)
     torch.cuda.synchronize()
@@ -344,7 +350,7 @@ def run_batch(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
         "config": {"workload": "batch", "graphs": len(gs), "sum_m": m_tot, "sum_n": sum(g.n for g in gs),
                    "desc": "n log-uniform [64,65536], degree U[4,16], ER/grid/R-MAT mixed, w~U[0,1), gen seed 4",
-                   "graph_bytes": graph_bytes,
+                   "graph_bytes": graph_bytes, "tuning": tuning,
                    "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)"},
         "edges_per_s": ws * m_tot / (ms * 1e-3), "p50_ms": ms, "p99_ms": ms,
         "plain_back_to_back": {"graphs_per_s": len(gs) / plain_s, "edges_per_s": m_tot / plain_s,

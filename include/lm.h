@@ -161,6 +161,38 @@ int  lm_poll(lm_ctx* ctx, uint64_t ticket, int* done, lm_stats* stats);
  * ticket stays valid).  Does not release the ticket: call lm_poll after. */
 int  lm_wait(lm_ctx* ctx, uint64_t ticket, uint32_t timeout_ms);
 
+/* Launch parameters of a context's matching path (the paper has no
+ * counterpart; they only affect speed, never the result):
+ *   rmax               rows with at most this many live entries are swept 32 to a
+ *                      warp; longer rows are split into chunks (1 .. 2^20)
+ *   chunk              entries per chunk of a long row (a power of two, 2^8 .. 2^20)
+ *   sweep_ctas_per_sm  CTAs per SM of the sweep kernel (0 = as many as fit, at most 16)
+ *   vertex_ctas_per_sm CTAs per SM of the vertex pass (0 = 4, at most 4)
+ *   ms                 lm_autotune only: median time of one call with these parameters
+ * Defaults: rmax 2048, chunk 4096, sweep 0, vertex 4.  The serving thread takes
+ * the context's parameters when it starts (first lm_submit). */
+typedef struct lm_tuning {
+    uint32_t rmax;
+    uint32_t chunk;
+    uint32_t sweep_ctas_per_sm;
+    uint32_t vertex_ctas_per_sm;
+    double   ms;
+} lm_tuning;
+
+/* Current launch parameters of the context (ms = 0). */
+int  lm_get_tuning(const lm_ctx* ctx, lm_tuning* out);
+
+/* Set the launch parameters (ms is ignored).  Errors: LM_EINVAL (out of range). */
+int  lm_set_tuning(lm_ctx* ctx, const lm_tuning* t);
+
+/* Autotuner: times a fixed set of candidate launch parameters on the caller's
+ * own workload -- lm_match of g[0] when count == 1, lm_batch_match of the
+ * `count` graphs otherwise (one warm-up call and three timed calls each) --
+ * keeps the fastest in the context and returns it in *best (best may be NULL).
+ * mates receive the results as in lm_batch_match.  Errors: as lm_batch_match. */
+int  lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uint64_t* seeds,
+                 uint32_t* const* mates, lm_tuning* best);
+
 /* Small graphs without allocation.  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory while they run,
  * for example a host loop that keeps a fixed device footprint or hands all

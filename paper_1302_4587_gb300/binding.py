@@ -25,7 +25,7 @@ LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_COUNT = range(6)
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
            "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error",
-           "lm_match_small_noalloc")
+           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune")
 LM_NOALLOC_MAX_N, LM_NOALLOC_MAX_M = 65536, 262144
 
 
@@ -47,6 +47,15 @@ class LmStats(ctypes.Structure):
                 "round_m": [int(x) for x in self.round_m[:k]], "round_n": [int(x) for x in self.round_n[:k]],
                 "kernel_ms": [float(x) for x in self.kernel_ms],
                 "kernel_launches": [int(x) for x in self.kernel_launches], "total_ms": float(self.total_ms)}
+
+
+class LmTuning(ctypes.Structure):
+    _fields_ = [("rmax", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("sweep_ctas_per_sm", ctypes.c_uint32),
+                ("vertex_ctas_per_sm", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+    def to_dict(self) -> dict:
+        return {"rmax": int(self.rmax), "chunk": int(self.chunk), "sweep_ctas_per_sm": int(self.sweep_ctas_per_sm),
+                "vertex_ctas_per_sm": int(self.vertex_ctas_per_sm), "ms": float(self.ms)}
 
 
 class LmError(RuntimeError):
@@ -89,6 +98,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.lm_last_error.argtypes = [vp]
         lib.lm_last_error.restype = ctypes.c_char_p
         lib.lm_match_small_noalloc.argtypes = [u32, u32, vp, vp, vp, u64, vp, vp, vp]
+        lib.lm_get_tuning.argtypes = [vp, ctypes.POINTER(LmTuning)]
+        lib.lm_set_tuning.argtypes = [vp, ctypes.POINTER(LmTuning)]
+        lib.lm_autotune.argtypes = [vp, ctypes.POINTER(vp), u32, ctypes.POINTER(u64), ctypes.POINTER(vp),
+                                    ctypes.POINTER(LmTuning)]
         _LIB = lib
         return lib
 
@@ -281,3 +294,23 @@ def lm_match_small_noalloc(n: int, eu, ev, w, seed: int, mate, status, stream=No
         s = stream.cuda_stream
     _check(lib.lm_match_small_noalloc(n, m, eu.data_ptr(), ev.data_ptr(), w.data_ptr(), seed & (2**64 - 1),
                                       mate.data_ptr(), status.data_ptr(), s))
+
+
+def lm_get_tuning(ctx) -> dict:
+    t = LmTuning()
+    _check(load().lm_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t.to_dict()
+
+
+def lm_set_tuning(ctx, rmax: int, chunk: int, sweep_ctas_per_sm: int = 0, vertex_ctas_per_sm: int = 4) -> None:
+    t = LmTuning(rmax, chunk, sweep_ctas_per_sm, vertex_ctas_per_sm, 0.0)
+    _check(load().lm_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def lm_autotune(ctx, graphs, seeds=None, mates=None) -> dict:
+    """Time the candidate launch parameters on these graphs (a list of handles with
+    seeds and mates, or a BatchArgs), keep the fastest in the context, return it."""
+    b = graphs if isinstance(graphs, BatchArgs) else BatchArgs(graphs, seeds, mates)
+    t = LmTuning()
+    _check(load().lm_autotune(ctx, b.graphs, b.count, b.seeds, b.mates, ctypes.byref(t)), ctx)
+    return t.to_dict()

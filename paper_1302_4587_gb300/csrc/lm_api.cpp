@@ -149,7 +149,7 @@ void engine_free(Engine& e) {
 
 int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     Workspace& w = e.ws;
-    const uint32_t nc = chunks_cap(ne);
+    const uint32_t nc = chunks_cap(ne, e.cfg);
     if (w.block && nv <= w.cap_v && ne <= w.cap_e && nc <= w.cap_c && ng <= w.cap_g) return LM_OK;
     LM_CK(ctx, cudaStreamSynchronize(e.stream));
     Workspace nw;
@@ -311,6 +311,8 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         v.par = par;
         v.match = match;
         v.grounds = match ? job.grounds : nullptr;
+        v.rmax = e.cfg.rmax;
+        v.chunk_shift = e.cfg.chunk_shift;
         v.st = e.st;
     };
     auto sargs = [&](SweepArgs& c, int in_set, uint32_t par, bool input) {
@@ -325,6 +327,8 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         c.out_key = w.key[par ^ 1u];
         c.out_nbr = w.nbr[par ^ 1u];
         c.ecap = job.ecap;
+        c.rmax = e.cfg.rmax;
+        c.chunk_shift = e.cfg.chunk_shift;
         c.st = e.st;
     };
     // round 0: candidates over the graphs' own arrays in tiles; match, open rows
@@ -359,7 +363,14 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         LM_CK(ctx, launch_init(s, &D->init));
         prof.end();
     } else if (!prof.on) {
-        if (!e.graph) LM_CK(ctx, build_job_graph(D, e.st, &e.graph));
+        if (e.graph && e.graph_cfg != e.cfg) {
+            destroy_job_graph(e.graph);
+            e.graph = nullptr;
+        }
+        if (!e.graph) {
+            LM_CK(ctx, build_job_graph(D, e.st, e.cfg, &e.graph));
+            e.graph_cfg = e.cfg;
+        }
         LM_CK(ctx, launch_job_graph(e.graph, s));
         // launches of one job: init, 4 for round 0, then 5 per pair of rounds
         prof.launches[LM_K_INIT] += 1;
@@ -374,26 +385,26 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         LM_CK(ctx, launch_round0_cut(s, &D->r0));
         prof.end();
         prof.begin(LM_K_VERTEX);
-        LM_CK(ctx, launch_vertex(s, &D->v[0]));
+        LM_CK(ctx, launch_vertex(s, &D->v[0], e.cfg));
         prof.end();
         prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_input(s, &D->s[0]));
+        LM_CK(ctx, launch_sweep_input(s, &D->s[0], e.cfg));
         prof.end();
         prof.begin(LM_K_VERTEX);
-        LM_CK(ctx, launch_vertex(s, &D->v[1]));
+        LM_CK(ctx, launch_vertex(s, &D->v[1], e.cfg));
         prof.end();
         prof.begin(LM_K_SWEEP);
-        LM_CK(ctx, launch_sweep_live(s, &D->s[1]));
+        LM_CK(ctx, launch_sweep_live(s, &D->s[1], e.cfg));
         prof.end();
         // the same limits as the device-driven loop: the round cap and LOOP_LIMIT_NS
         const auto t_start = std::chrono::steady_clock::now();
         for (uint32_t pair = 0;; pair++) {
             for (int k = 2; k < 4; k++) {
                 prof.begin(LM_K_VERTEX);
-                LM_CK(ctx, launch_vertex(s, &D->v[k]));
+                LM_CK(ctx, launch_vertex(s, &D->v[k], e.cfg));
                 prof.end();
                 prof.begin(LM_K_SWEEP);
-                LM_CK(ctx, launch_sweep_live(s, &D->s[k]));
+                LM_CK(ctx, launch_sweep_live(s, &D->s[k], e.cfg));
                 prof.end();
             }
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -774,6 +785,80 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
             stats[i].round_n[0] = gs[i]->nrows;
         }
     }
+    return LM_OK;
+}
+
+namespace {
+bool cfg_from(const lm_tuning* t, LaunchCfg* c) {
+    if (!t || t->rmax < 1 || t->rmax > (1u << 20)) return false;
+    if (t->chunk < 256 || t->chunk > (1u << 20) || (t->chunk & (t->chunk - 1))) return false;
+    if (t->sweep_ctas_per_sm > 16 || t->vertex_ctas_per_sm > 4) return false;
+    c->rmax = t->rmax;
+    c->chunk_shift = 0;
+    while ((1u << c->chunk_shift) < t->chunk) c->chunk_shift++;
+    c->sweep_ctas_per_sm = t->sweep_ctas_per_sm;
+    c->vertex_ctas_per_sm = t->vertex_ctas_per_sm;
+    return true;
+}
+void tuning_of(const LaunchCfg& c, lm_tuning* t) {
+    t->rmax = c.rmax;
+    t->chunk = 1u << c.chunk_shift;
+    t->sweep_ctas_per_sm = c.sweep_ctas_per_sm;
+    t->vertex_ctas_per_sm = c.vertex_ctas_per_sm;
+    t->ms = 0.0;
+}
+}  // namespace
+
+int lm_get_tuning(const lm_ctx* ctx, lm_tuning* out) {
+    if (!ctx || !out) return LM_EINVAL;
+    tuning_of(ctx->eng.cfg, out);
+    return LM_OK;
+}
+
+int lm_set_tuning(lm_ctx* ctx, const lm_tuning* t) {
+    if (!ctx) return LM_EINVAL;
+    LaunchCfg c;
+    if (!cfg_from(t, &c)) return fail(ctx, LM_EINVAL, "tuning out of range");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    ctx->eng.cfg = c;
+    return LM_OK;
+}
+
+int lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uint64_t* seeds,
+                uint32_t* const* mates, lm_tuning* best) {
+    if (!ctx) return LM_EINVAL;
+    if (count == 0 || !g || !seeds || !mates) return fail(ctx, LM_EINVAL, "nothing to tune on");
+    // candidates: task sizes from many short tasks to few long ones, sweep at full or
+    // three-quarter occupancy
+    static const uint32_t sizes[][2] = {{64, 1024}, {256, 2048}, {2048, 4096}, {8192, 16384}};
+    static const uint32_t sweeps[] = {0, 3};
+    lm_tuning keep;
+    lm_get_tuning(ctx, &keep);
+    lm_tuning top = keep;
+    top.ms = -1.0;
+    for (const auto& sz : sizes) {
+        for (uint32_t sw : sweeps) {
+            lm_tuning t = {sz[0], sz[1], sw, keep.vertex_ctas_per_sm, 0.0};
+            int rc = lm_set_tuning(ctx, &t);
+            if (rc) return rc;
+            std::vector<double> ms;
+            for (int it = 0; it < 4; it++) {
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = count == 1 ? lm_match(ctx, g[0], seeds[0], mates[0], nullptr)
+                                : lm_batch_match(ctx, g, count, seeds, mates, nullptr);
+                if (rc) {
+                    lm_set_tuning(ctx, &keep);
+                    return rc;
+                }
+                if (it > 0) ms.push_back(std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+            }
+            std::sort(ms.begin(), ms.end());
+            t.ms = ms[ms.size() / 2];
+            if (top.ms < 0 || t.ms < top.ms) top = t;
+        }
+    }
+    lm_set_tuning(ctx, &top);
+    if (best) *best = top;
     return LM_OK;
 }
 

@@ -58,6 +58,8 @@ struct Engine {
     char* dargs = nullptr;           // [ARG_AREA] kernel arguments (device)
     char* hargs = nullptr;           // [ARG_AREA] their pinned staging
     void* graph = nullptr;           // executable job graph (device-driven round loop)
+    LaunchCfg cfg;                   // launch parameters of the next jobs
+    LaunchCfg graph_cfg;             // the ones `graph` was built with
     Workspace ws;
     int sweep_grid = 0, vertex_grid = 0;
 };
@@ -112,7 +114,9 @@ uint64_t splitmix64_first(uint64_t seed);
 SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase, uint32_t tile_begin);
 // chunk-list capacity for a union entry space of `ne` entries: every row longer
 // than RMAX adds at most one partial chunk to its ne / CHUNK full ones
-inline uint32_t chunks_cap(uint64_t ne) { return (uint32_t)(ne / CHUNK + ne / (RMAX + 1) + 64); }
+inline uint32_t chunks_cap(uint64_t ne, const LaunchCfg& c) {
+    return (uint32_t)(ne / (1u << c.chunk_shift) + ne / (c.rmax + 1) + 64);
+}
 
 int engine_init(lm_ctx* ctx, Engine& e, cudaStream_t stream);
 void engine_free(Engine& e);

@@ -104,6 +104,24 @@ struct SegIn {
     uint32_t k0, k1;          // perm_seed keys of the graph's seed
 };
 
+// Launch parameters a context may tune (lm_set_tuning / lm_autotune): the
+// sweep's task sizes and the CTAs per SM of the vertex pass and the sweep
+// (0 = as many as fit).
+struct LaunchCfg {
+    uint32_t rmax = RMAX;
+    uint32_t chunk_shift = 0;
+    uint32_t sweep_ctas_per_sm = 0;
+    uint32_t vertex_ctas_per_sm = 4;
+    LaunchCfg() {
+        while ((1u << chunk_shift) < CHUNK) chunk_shift++;
+    }
+    bool operator==(const LaunchCfg& o) const {
+        return rmax == o.rmax && chunk_shift == o.chunk_shift && sweep_ctas_per_sm == o.sweep_ctas_per_sm &&
+               vertex_ctas_per_sm == o.vertex_ctas_per_sm;
+    }
+    bool operator!=(const LaunchCfg& o) const { return !(*this == o); }
+};
+
 // Per-vertex arrays of a job (union ids).
 struct VertexArrays {
     const uint32_t* start;    // [N] union entry index of each vertex's row
@@ -135,6 +153,8 @@ struct VertexArgs {
     uint32_t round_from_state; // 1: the round index is DevState::round (advanced by this pass)
     uint32_t* grounds;        // per-graph rounds: max(round + 1) over graphs with a live row, NULL = none
     uint32_t* glive;          // live unmatched rows per graph seen by this pass, NULL = none
+    uint32_t rmax;            // rows of at most this many live entries go to R, longer ones to C
+    uint32_t chunk_shift;     // chunks of a long row hold 1 << chunk_shift entries
     DevState* st;
 };
 
@@ -155,6 +175,7 @@ struct SweepArgs {
     uint64_t* out_key;
     uint32_t* out_nbr;
     uint32_t ecap;            // entries in the union entry space
+    uint32_t rmax, chunk_shift;  // as in VertexArgs
     DevState* st;
 };
 
@@ -193,10 +214,10 @@ constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
 // cudaError_t value as int.
 // kernel arguments are passed as pointers to device memory
 int launch_init(void* stream, const InitArgs* dargs);
-int launch_vertex(void* stream, const VertexArgs* dargs);
-int launch_sweep_cand(void* stream, const SweepArgs* dargs);   // round 0, all entries live, candidates only
-int launch_sweep_input(void* stream, const SweepArgs* dargs);  // round 0 compaction from the input arrays
-int launch_sweep_live(void* stream, const SweepArgs* dargs);   // rounds >= 1
+int launch_vertex(void* stream, const VertexArgs* dargs, const struct LaunchCfg& cfg);
+int launch_sweep_cand(void* stream, const SweepArgs* dargs, const struct LaunchCfg& cfg);   // round 0, candidates only
+int launch_sweep_input(void* stream, const SweepArgs* dargs, const struct LaunchCfg& cfg);  // round-0 compaction
+int launch_sweep_live(void* stream, const SweepArgs* dargs, const struct LaunchCfg& cfg);   // rounds >= 1
 int launch_round0(void* stream, const Round0Args* dargs);      // round-0 candidates in TMA-fed tiles
 int launch_round0_cut(void* stream, const Round0Args* dargs);  // candidates of rows cut by tile boundaries
 int device_sm_count(int device);
@@ -204,7 +225,7 @@ uint64_t splitmix64_first(uint64_t seed);  // lm_api.cpp
 // executable graph that runs a whole job from its arguments in device memory
 // (init, round 0, then a conditional loop of rounds until the device's done
 // flag is set); returns a cudaError_t value
-int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out);
+int build_job_graph(const JobArgs* dargs, DevState* st, const struct LaunchCfg& cfg, void** exec_out);
 int launch_job_graph(void* exec, void* stream);
 void destroy_job_graph(void* exec);
 

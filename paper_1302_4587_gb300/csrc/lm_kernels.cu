@@ -277,10 +277,10 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                     my_match++;
                 } else {
                     open_row = true;
-                    if (L <= RMAX) { cls[i] = 1; cR++; }
+                    if (L <= a.rmax) { cls[i] = 1; cR++; }
                     else {
                         cls[i] = 2;
-                        cC += (L + CHUNK - 1) / CHUNK;
+                        cC += ((L - 1) >> a.chunk_shift) + 1;
                         if (a.match) va.len[par ^ 1][v] = 0;  // long rows gather their survivors atomically
                     }
                 }
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                 if (pR < a.out.capR) a.out.R[pR] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pR);
                 pR++;
             } else if (cls[i] == 2) {
-                const uint32_t nch = (LL[i] + CHUNK - 1) / CHUNK;
+                const uint32_t nch = ((LL[i] - 1) >> a.chunk_shift) + 1;
                 for (uint32_t c = 0; c < nch; c++, pC++) {
                     if (pC < a.out.capC) a.out.C[pC] = make_uint2(vv[i], c); else set_err(st, ERR_BOUNDS, pC);
                 }
@@ -427,7 +427,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
         const uint2 rv = a.in.R[idx];
         v = rv.x;
         L = rv.y;
-        if (v >= va.nvert || L > RMAX) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
+        if (v >= va.nvert || L > a.rmax) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
         else {
             s0 = va.start[v];
             g = va.gid ? va.gid[v] : 0u;
@@ -564,7 +564,7 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
     const uint32_t v = c.x;
     if (v >= va.nvert) { if (lane == 0) set_err(a.st, ERR_BOUNDS, v); return; }
     const uint32_t L = va.len[a.par][v];
-    const uint32_t jb = c.y * CHUNK, je = min(L, jb + CHUNK);
+    const uint32_t jb = c.y << a.chunk_shift, je = min(L, jb + (1u << a.chunk_shift));
     const uint32_t s0 = va.start[v];
     const uint32_t g = va.gid ? va.gid[v] : 0u;
     if (jb >= L || (uint64_t)s0 + L > a.ecap || g >= a.nsegs) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); return; }
@@ -631,7 +631,7 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
     if (lane == 0) {
         const uint64_t K = ((uint64_t)hi << 32) | lo;
         if (K) atomicMax(&va.bkey[v], (unsigned long long)K);
-        const uint32_t nch = (L + CHUNK - 1) / CHUNK;
+        const uint32_t nch = ((L - 1) >> a.chunk_shift) + 1;
         // release: this chunk's maximum is visible before its count; acquire: the last
         // chunk sees every other chunk's maximum
         const uint32_t old = atom_add_acq_rel(&va.bcnt[v], 1u);
@@ -1301,28 +1301,34 @@ int launch_init(void* stream, const InitArgs* dargs) {
     return (int)cudaGetLastError();
 }
 
-static uint32_t vertex_grid() { return (uint32_t)current_sms() * 4; }
+// the vertex pass fits 4 CTAs per SM (launch bounds); 0 or more takes that
+static uint32_t vertex_grid(const LaunchCfg& c) {
+    const uint32_t per = (c.vertex_ctas_per_sm == 0 || c.vertex_ctas_per_sm > 4) ? 4u : c.vertex_ctas_per_sm;
+    return (uint32_t)current_sms() * per;
+}
 
-int launch_vertex(void* stream, const VertexArgs* dargs) {
+int launch_vertex(void* stream, const VertexArgs* dargs, const LaunchCfg& cfg) {
     // a fixed grid: the pass iterates its rows block-strided (row counts live on the device)
-    k_vertex<<<vertex_grid(), VT, 0, (cudaStream_t)stream>>>(dargs);
+    k_vertex<<<vertex_grid(cfg), VT, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
 
 template <bool I, bool C>
-static uint32_t sweep_grid() {
+static uint32_t sweep_grid(const LaunchCfg& cfg) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<I, C>, ST, 0);
         blocks_per_sm = per > 0 ? per : 1;
     }
-    return (uint32_t)(current_sms() * blocks_per_sm);
+    int per = blocks_per_sm;
+    if (cfg.sweep_ctas_per_sm && (int)cfg.sweep_ctas_per_sm < per) per = (int)cfg.sweep_ctas_per_sm;
+    return (uint32_t)(current_sms() * per);
 }
 
 template <bool I, bool C>
-static int launch_sweep_t(void* stream, const SweepArgs* dargs) {
-    k_sweep<I, C><<<sweep_grid<I, C>(), ST, 0, (cudaStream_t)stream>>>(dargs);
+static int launch_sweep_t(void* stream, const SweepArgs* dargs, const LaunchCfg& cfg) {
+    k_sweep<I, C><<<sweep_grid<I, C>(cfg), ST, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
 static int round0_blocks_per_sm() {
@@ -1356,9 +1362,9 @@ int launch_round0_cut(void* stream, const Round0Args* d) {
     k_round0_cut<<<round0_cut_grid(), 256, 0, (cudaStream_t)stream>>>(d);
     return (int)cudaGetLastError();
 }
-int launch_sweep_cand(void* stream, const SweepArgs* d) { return launch_sweep_t<true, false>(stream, d); }
-int launch_sweep_input(void* stream, const SweepArgs* d) { return launch_sweep_t<true, true>(stream, d); }
-int launch_sweep_live(void* stream, const SweepArgs* d) { return launch_sweep_t<false, true>(stream, d); }
+int launch_sweep_cand(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<true, false>(stream, d, c); }
+int launch_sweep_input(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<true, true>(stream, d, c); }
+int launch_sweep_live(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<false, true>(stream, d, c); }
 
 int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n,
                          uint32_t m, uint32_t* deg, uint32_t* err) {
@@ -1445,7 +1451,7 @@ static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNod
 
 // init -> round-0 candidate tiles (+ cut rows) -> round-0 match -> round-0
 // compaction from the input arrays -> round 1 -> while (live) { two rounds }
-int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out) {
+int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, void** exec_out) {
     *exec_out = nullptr;
     uint32_t rgrid = 0;
     if (int pe = round0_grid(&rgrid)) return pe;
@@ -1465,8 +1471,8 @@ int build_job_graph(const JobArgs* dargs, DevState* st, void** exec_out) {
         vparams[k][0] = &pv[k];
         sparams[k][0] = &ps[k];
     }
-    const dim3 vgrid(vertex_grid()), vblock(VT), sblock(ST), rblock(R0T), cgrid(round0_cut_grid());
-    const dim3 lgrid(sweep_grid<false, true>()), igrid(sweep_grid<true, true>());
+    const dim3 vgrid(vertex_grid(cfg)), vblock(VT), sblock(ST), rblock(R0T), cgrid(round0_cut_grid());
+    const dim3 lgrid(sweep_grid<false, true>(cfg)), igrid(sweep_grid<true, true>(cfg));
     do {
         if ((e = add_kernel(g, &node, prev, (void*)k_init, dim3(current_sms() * 16), dim3(256), init_params))) break;
         prev = node;

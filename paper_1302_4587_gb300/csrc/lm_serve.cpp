@@ -158,6 +158,8 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         pre.out = lists_of(e, 2);
         pre.out_set = 2;
         pre.par = par;
+        pre.rmax = e.cfg.rmax;
+        pre.chunk_shift = e.cfg.chunk_shift;
         pre.st = e.st;
     }
     auto vpass = [&](VertexArgs& v, int in_set, int out_set) {
@@ -171,6 +173,8 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         v.match = 1;
         v.glive = w.glive;
         v.grounds = w.grounds;
+        v.rmax = e.cfg.rmax;
+        v.chunk_shift = e.cfg.chunk_shift;
         v.st = e.st;
     };
     vpass(A.v_live, par, par ^ 1u);
@@ -187,6 +191,8 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         c.out_key = w.key[par ^ 1u];
         c.out_nbr = w.nbr[par ^ 1u];
         c.ecap = S->cap_e;
+        c.rmax = e.cfg.rmax;
+        c.chunk_shift = e.cfg.chunk_shift;
         c.st = e.st;
     };
     sargs(A.cand, 2, true);
@@ -206,16 +212,16 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         if (fresh[k]->g->n) LM_CK(ctx, launch_init(s, &D->init[k]));
         if (fresh[k]->g->nent == 0) continue;
         any_fresh_edges = true;
-        LM_CK(ctx, launch_vertex(s, &D->pre[k]));
+        LM_CK(ctx, launch_vertex(s, &D->pre[k], e.cfg));
     }
-    if (any_fresh_edges) LM_CK(ctx, launch_sweep_cand(s, &D->cand));
+    if (any_fresh_edges) LM_CK(ctx, launch_sweep_cand(s, &D->cand, e.cfg));
     // mutual choice: in-flight rows (sets par and 3), then the fresh rows (set 2 -> set 3)
-    LM_CK(ctx, launch_vertex(s, &D->v_live));
-    LM_CK(ctx, launch_vertex(s, &D->v_prev_fresh));
-    if (any_fresh_edges) LM_CK(ctx, launch_vertex(s, &D->v_fresh));
+    LM_CK(ctx, launch_vertex(s, &D->v_live, e.cfg));
+    LM_CK(ctx, launch_vertex(s, &D->v_prev_fresh, e.cfg));
+    if (any_fresh_edges) LM_CK(ctx, launch_vertex(s, &D->v_fresh, e.cfg));
     // sweeps: in-flight rows from the live buffers, fresh rows from their own arrays
-    LM_CK(ctx, launch_sweep_live(s, &D->s_live));
-    if (any_fresh_edges) LM_CK(ctx, launch_sweep_input(s, &D->s_fresh));
+    LM_CK(ctx, launch_sweep_live(s, &D->s_live, e.cfg));
+    if (any_fresh_edges) LM_CK(ctx, launch_sweep_input(s, &D->s_fresh, e.cfg));
     // which requests still have live rows
     std::vector<uint32_t> glive(ctx->max_slots), gr(ctx->max_slots);
     LM_CK(ctx, cudaMemcpyAsync(glive.data(), w.glive, (size_t)ctx->max_slots * sizeof(uint32_t),
@@ -315,6 +321,7 @@ int serve_start(lm_ctx* ctx) {
         cudaStreamDestroy(st);
         return rc;
     }
+    S->eng.cfg = ctx->eng.cfg;  // the context's launch parameters when serving starts
     // capacities from the budget: per entry 24 B (two 12-byte buffers) + list and
     // partial space; per vertex 9 words of vertex state and task lists
     const double B = (double)ctx->budget;
