@@ -431,6 +431,38 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     return check_err(ctx, e);
 }
 
+// One graph on engine e, results to mate (device memory when dev_out, else host
+// memory staged through the workspace); the engine's DevState holds its statistics.
+int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof) {
+    cudaStream_t s = e.stream;
+    int rc = ensure_ws(ctx, e, g->n, g->nent, 1);
+    if (rc) return rc;
+    rc = ensure_pinned(ctx, e, sizeof(SegIn));
+    if (rc) return rc;
+    Job job;
+    uint32_t* mate_d = dev_out ? mate : e.ws.mate;
+    job.va = vertex_arrays(e, g->n, g->off, false, mate_d);
+    job.nedges = g->m;
+    job.ecap = g->nent;
+    job.vlist = g->vid;
+    job.rdeg = g->rdeg;
+    job.nvlist = g->nrows;
+    job.nseg = g->nent > 0 ? 1 : 0;
+    job.ntiles = g->ntiles;
+    if (job.nseg) {
+        const SegIn sg = seg_of(g, seed, 0, 0, 0);
+        memcpy(e.pinned, &sg, sizeof sg);
+        LM_CK(ctx, cudaMemcpyAsync(e.ws.segs, e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
+    }
+    rc = run_job(ctx, e, job, prof);
+    if (rc) return rc;
+    if (!dev_out && g->n > 0) {
+        LM_CK(ctx, cudaMemcpyAsync(mate, mate_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+        LM_CK(ctx, cudaStreamSynchronize(s));
+    }
+    return LM_OK;
+}
+
 }  // namespace lm
 
 namespace {
@@ -640,38 +672,12 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DevGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
-    Engine& e = ctx->eng;
-    cudaStream_t s = e.stream;
     if (stats) memset(stats, 0, sizeof *stats);
-    const bool dev_out = is_device_ptr(mate);
-    int rc = ensure_ws(ctx, e, g->n, g->nent, 1);
+    Prof prof(ctx, ctx->eng.stream);
+    const int rc = match_one(ctx, ctx->eng, g, seed, mate, is_device_ptr(mate), prof);
     if (rc) return rc;
-    rc = ensure_pinned(ctx, e, sizeof(SegIn));
-    if (rc) return rc;
-    Job job;
-    uint32_t* mate_d = dev_out ? mate : e.ws.mate;
-    job.va = vertex_arrays(e, g->n, g->off, false, mate_d);
-    job.nedges = g->m;
-    job.ecap = g->nent;
-    job.vlist = g->vid;
-    job.rdeg = g->rdeg;
-    job.nvlist = g->nrows;
-    job.nseg = g->nent > 0 ? 1 : 0;
-    job.ntiles = g->ntiles;
-    if (job.nseg) {
-        const SegIn sg = seg_of(g, seed, 0, 0, 0);
-        memcpy(e.pinned, &sg, sizeof sg);
-        LM_CK(ctx, cudaMemcpyAsync(e.ws.segs, e.pinned, sizeof sg, cudaMemcpyHostToDevice, s));
-    }
-    Prof prof(ctx, s);
-    rc = run_job(ctx, e, job, prof);
-    if (rc) return rc;
-    if (!dev_out && g->n > 0) {
-        LM_CK(ctx, cudaMemcpyAsync(mate, mate_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
-        LM_CK(ctx, cudaStreamSynchronize(s));
-    }
     if (stats) {
-        fill_round_stats(*e.st_host, stats);
+        fill_round_stats(*ctx->eng.st_host, stats);
         prof.fill(stats);
     }
     return LM_OK;

@@ -154,6 +154,7 @@ struct Prof {
     void fill(lm_stats* st);
 };
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof);
+int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof);
 
 }  // namespace lm
 

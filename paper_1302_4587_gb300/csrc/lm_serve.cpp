@@ -106,16 +106,21 @@ namespace {
 constexpr size_t MAX_QUEUE = 1u << 20;
 
 constexpr uint32_t MAX_FRESH = 64;  // admissions per step (kernel arguments of one step fit the argument area)
+constexpr uint32_t MAX_ROUNDS_PER_STEP = 8;  // a step without admissions runs up to this many rounds
 
 struct StepArgs {
     InitArgs init[MAX_FRESH];
     VertexArgs pre[MAX_FRESH];
     VertexArgs v_live, v_prev_fresh, v_fresh;
     SweepArgs cand, s_live, s_fresh;
+    VertexArgs v_more[MAX_ROUNDS_PER_STEP];  // rounds 1.. of a step without admissions
+    SweepArgs s_more[MAX_ROUNDS_PER_STEP];
 };
 
-// One scheduler step (see the file comment).  Returns LM_OK or an error code.
-int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*>& finished) {
+// One scheduler step (see the file comment).  A step that admits nothing and has
+// nobody waiting runs `rounds` rounds before it returns to the host (fewer host
+// round trips while the load is light).  Returns LM_OK or an error code.
+int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*>& finished, uint32_t rounds) {
     lm_ctx* ctx = S->ctx;
     Engine& e = S->eng;
     Workspace& w = e.ws;
@@ -162,14 +167,14 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         pre.chunk_shift = e.cfg.chunk_shift;
         pre.st = e.st;
     }
-    auto vpass = [&](VertexArgs& v, int in_set, int out_set) {
+    auto vpass = [&](VertexArgs& v, int in_set, int out_set, uint32_t p = 2, uint32_t rnd = 0) {
         v.va = va;
         v.in = lists_of(e, in_set);
         v.in_set = in_set;
         v.out = lists_of(e, out_set);
         v.out_set = out_set;
-        v.par = par;
-        v.round = S->step;
+        v.par = p < 2 ? p : par;
+        v.round = rnd;  // round index within the step (per-request round counts)
         v.match = 1;
         v.glive = w.glive;
         v.grounds = w.grounds;
@@ -180,16 +185,17 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     vpass(A.v_live, par, par ^ 1u);
     vpass(A.v_prev_fresh, 3, par ^ 1u);
     vpass(A.v_fresh, 2, 3);
-    auto sargs = [&](SweepArgs& c, int in_set, bool input) {
+    auto sargs = [&](SweepArgs& c, int in_set, bool input, uint32_t p = 2) {
+        const uint32_t pp = p < 2 ? p : par;
         c.va = va;
         c.in = lists_of(e, in_set);
         c.in_set = in_set;
-        c.par = par;
+        c.par = pp;
         c.segs = w.segs;
         c.nsegs = ctx->max_slots;
-        if (!input) { c.in_key = w.key[par]; c.in_nbr = w.nbr[par]; }
-        c.out_key = w.key[par ^ 1u];
-        c.out_nbr = w.nbr[par ^ 1u];
+        if (!input) { c.in_key = w.key[pp]; c.in_nbr = w.nbr[pp]; }
+        c.out_key = w.key[pp ^ 1u];
+        c.out_nbr = w.nbr[pp ^ 1u];
         c.ecap = S->cap_e;
         c.rmax = e.cfg.rmax;
         c.chunk_shift = e.cfg.chunk_shift;
@@ -202,6 +208,14 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     A.cand.task_ctr = &e.st->task[0];
     A.s_live.task_ctr = &e.st->task[1];
     A.s_fresh.task_ctr = &e.st->task[2];
+    if (!fresh.empty()) rounds = 1;
+    rounds = std::max(1u, std::min(rounds, MAX_ROUNDS_PER_STEP));
+    for (uint32_t r = 1; r < rounds; r++) {
+        const uint32_t pr = (S->step + r) & 1u;
+        vpass(A.v_more[r], (int)pr, (int)(pr ^ 1u), pr, r);
+        sargs(A.s_more[r], (int)(pr ^ 1u), false, pr);
+        A.s_more[r].task_ctr = &e.st->task[1];
+    }
     LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
     LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
     LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
@@ -222,6 +236,13 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     // sweeps: in-flight rows from the live buffers, fresh rows from their own arrays
     LM_CK(ctx, launch_sweep_live(s, &D->s_live, e.cfg));
     if (any_fresh_edges) LM_CK(ctx, launch_sweep_input(s, &D->s_fresh, e.cfg));
+    // further rounds of a step without admissions; the live-row counts that decide
+    // completion are those of the last round
+    for (uint32_t r = 1; r < rounds; r++) {
+        if (r == rounds - 1) LM_CK(ctx, cudaMemsetAsync(w.glive, 0, (size_t)ctx->max_slots * sizeof(uint32_t), s));
+        LM_CK(ctx, launch_vertex(s, &D->v_more[r], e.cfg));
+        LM_CK(ctx, launch_sweep_live(s, &D->s_more[r], e.cfg));
+    }
     // which requests still have live rows
     std::vector<uint32_t> glive(ctx->max_slots), gr(ctx->max_slots);
     LM_CK(ctx, cudaMemcpyAsync(glive.data(), w.glive, (size_t)ctx->max_slots * sizeof(uint32_t),
@@ -233,11 +254,11 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
     if (e.st_host->err & ERR_BOUNDS) return fail(ctx, LM_ECUDA, "device index check failed (serving)");
     if (e.st_host->err & ERR_TIMEOUT) return fail(ctx, LM_ETIMEOUT, "a bounded device wait gave up (serving)");
     (void)na;
-    // a round counts for a request when it had live rows in this step's vertex passes;
-    // it is complete once no live row is left unmatched
+    // grounds[slot] = 1 + the last round of the step in which the request had live
+    // rows (its rounds are consecutive); it is complete once no live row is left unmatched
     std::vector<Request*> done;
     for (Request* r : S->active) {
-        if (gr[r->slot]) r->rounds++;
+        r->rounds += gr[r->slot];
         if (glive[r->slot] == 0) done.push_back(r);
     }
     if (!done.empty()) {
@@ -256,7 +277,7 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         LM_CK(ctx, cudaStreamSynchronize(s));
         for (size_t k = 0; k < done.size(); k++) done[k]->matched = gm[k] / 2;
     }
-    S->step++;
+    S->step += rounds;
     finished = done;
     return LM_OK;
 }
@@ -265,11 +286,19 @@ void scheduler(ServeState* S) {
     cudaSetDevice(S->ctx->device);
     for (;;) {
         std::vector<Request*> fresh;
+        Request* lone = nullptr;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
             if (S->stop) return;
-            while (!S->queue.empty() && !S->free_slots.empty() && fresh.size() < MAX_FRESH) {
+            // a request with nothing else in flight or queued runs alone, as one job
+            // graph (the plain path): round-by-round stepping only pays off in a mix
+            if (S->active.empty() && S->queue.size() == 1 && !S->fatal) {
+                lone = S->queue.front();
+                S->queue.pop_front();
+                lone->state = 1;
+            }
+            while (!lone && !S->queue.empty() && !S->free_slots.empty() && fresh.size() < MAX_FRESH) {
                 Request* r = S->queue.front();
                 uint32_t vb = 0, eb = 0;
                 if (!S->vspace.alloc(r->g->n, &vb)) break;
@@ -287,8 +316,28 @@ void scheduler(ServeState* S) {
                 fresh.push_back(r);
             }
         }
+        if (lone) {
+            Prof off(nullptr, S->eng.stream);
+            const int rc = match_one(S->ctx, S->eng, lone->g, lone->seed, lone->mate, !lone->host_dst, off);
+            std::lock_guard<std::mutex> lk(S->mu);
+            lone->rc = rc;
+            if (rc == LM_OK) {
+                lone->rounds = S->eng.st_host->rounds;
+                lone->matched = S->eng.st_host->matched2 / 2;
+            } else if (rc == LM_ECUDA) {
+                S->fatal = rc;
+            }
+            lone->state = 2;
+            S->cv_done.notify_all();
+            continue;
+        }
         std::vector<Request*> finished;
-        const int rc = S->fatal ? S->fatal : step(S, fresh, finished);
+        bool waiting;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            waiting = !S->queue.empty();
+        }
+        const int rc = S->fatal ? S->fatal : step(S, fresh, finished, waiting ? 1u : MAX_ROUNDS_PER_STEP);
         std::lock_guard<std::mutex> lk(S->mu);
         if (rc) {
             // the shared live state is lost: fail every request in flight
