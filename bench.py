@@ -173,6 +173,18 @@ def cand_model_bytes(st: dict) -> int:
     return 12 * 2 * st["round_m"][0] + 8 * st["round_n"][0]
 
 
+def edge_model_bytes(st: dict, m: int) -> int:
+    """Algorithmic HBM bytes of the edge-centric path of one match: per live edge
+    and round, the offer reads its id, record and weight word (16 B) and updates
+    two 8-byte maxima, the match reads the same 16 B and both maxima, the
+    compaction reads 16 B, clears both maxima and stamps (24 B) and appends the
+    id (4 B); round 0 reads no ids."""
+    b = 0
+    for r, e in enumerate(st["round_m"]):
+        b += e * (3 * 16 + 16 + 16 + 24 + 4) - (3 * 4 * e if r == 0 else 0)
+    return b
+
+
 def run_lm(args, ws, rank, local):
     import torch
     import paper_1302_4587_gb300 as lm
@@ -180,7 +192,8 @@ def run_lm(args, ws, rank, local):
     g, seed, desc = make_workload(args.workload)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = lm.lm_create(local, stream)
+    edge = args.algo == "edge"
+    ctx = lm.lm_create(local, stream, flags=lm.LM_F_EDGE_CENTRIC if edge else 0)
     eu = torch.from_numpy(g.eu.view(np.int32)).to(dev)
     ev = torch.from_numpy(g.ev.view(np.int32)).to(dev)
     w = torch.from_numpy(g.w).to(dev)
@@ -188,8 +201,9 @@ def run_lm(args, ws, rank, local):
     graph_bytes = lm.lm_graph_info(h)[2]
     del eu, ev, w
     mate = torch.empty(g.n, dtype=torch.int32, device=dev)
-    # launch parameters picked by the library's autotuner on this graph (untimed)
-    tuning = lm.lm_autotune(ctx, [h], [seed], [mate])
+    # launch parameters picked by the library's autotuner on this graph (untimed; the
+    # edge-centric path has none)
+    tuning = None if edge else lm.lm_autotune(ctx, [h], [seed], [mate])
     launches = 0
     for _ in range(max(args.warmup, 3)):
         _, st = lm.lm_match(ctx, h, seed, mate, stats=True)
@@ -212,9 +226,10 @@ def run_lm(args, ws, rank, local):
     clocks = clk.summary()
 
     # per-kernel device times (CUDA events recorded by the library on its stream)
-    pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE)
-    lm.lm_set_tuning(pctx, tuning["rmax"], tuning["chunk"], tuning["sweep_ctas_per_sm"],
-                     tuning["vertex_ctas_per_sm"])
+    pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE | (lm.LM_F_EDGE_CENTRIC if edge else 0))
+    if tuning:
+        lm.lm_set_tuning(pctx, tuning["rmax"], tuning["chunk"], tuning["sweep_ctas_per_sm"],
+                         tuning["vertex_ctas_per_sm"])
     kms = {k: [] for k in range(lm.LM_K_COUNT)}
     total_ms = []
     for i in range(max(args.warmup, 3) + args.steps):
@@ -233,8 +248,14 @@ def run_lm(args, ws, rank, local):
     cand_achieved = bytes_cand / (cd_ms * 1e-3) / 1e9 if cd_ms > 0 else 0.0
     names = {lm.LM_K_INIT: "k_init", lm.LM_K_SWEEP: "k_sweep", lm.LM_K_VERTEX: "k_vertex",
              lm.LM_K_CAND: "k_round0", lm.LM_K_OTHER: "other (k_round0_cut, k_loop_check)"}
+    if edge:
+        names = {lm.LM_K_INIT: "k_init", lm.LM_K_SWEEP: "k_ec_compact", lm.LM_K_VERTEX: "k_ec_match",
+                 lm.LM_K_CAND: "k_ec_offer", lm.LM_K_OTHER: "k_ec_close"}
     kernels = {names[k]: {"ms_per_match": med[k], "launches_per_match": pst["kernel_launches"][k]}
                for k in range(lm.LM_K_COUNT)}
+    bytes_ec = edge_model_bytes(pst, g.m) if edge else 0
+    ec_ms = med[lm.LM_K_CAND] + med[lm.LM_K_VERTEX] + med[lm.LM_K_SWEEP]
+    ec_achieved = bytes_ec / (ec_ms * 1e-3) / 1e9 if edge and ec_ms > 0 else 0.0
 
     # end to end through the C ABI with host buffers: graph upload + build, match, result download
     e2e = None
@@ -273,16 +294,21 @@ def run_lm(args, ws, rank, local):
         "config": {"workload": args.workload, "desc": desc, "n": g.n, "m": g.m, "seed": seed,
                    "rounds": pst["rounds"], "graph_bytes": graph_bytes,
                    "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)",
-                   "tuning": tuning,
+                   "tuning": tuning, "algorithm": "edge-centric" if edge else "segmented",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
-                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
-                     "bytes_per_match": bytes_sweep, "ms_per_match": sw_ms,
-                     "launches_per_match": pst["kernel_launches"][lm.LM_K_SWEEP],
-                     "profiled_total_ms": statistics.median(total_ms)},
-        "roofline_k_round0": {"bound": "hbm", "achieved": cand_achieved, "peak": peak, "unit": "GB/s",
-                              "frac": cand_achieved / peak, "bytes_per_launch": bytes_cand, "ms": cd_ms},
+        "roofline": ({"bound": "hbm", "kernel": "k_ec_offer + k_ec_match + k_ec_compact (all launches)",
+                      "achieved": ec_achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                      "frac": ec_achieved / peak, "traffic": None, "bytes_per_match": bytes_ec, "ms_per_match": ec_ms}
+                     if edge else
+                     {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
+                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                      "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
+                      "bytes_per_match": bytes_sweep, "ms_per_match": sw_ms,
+                      "launches_per_match": pst["kernel_launches"][lm.LM_K_SWEEP],
+                      "profiled_total_ms": statistics.median(total_ms)}),
+        "roofline_k_round0": None if edge else {"bound": "hbm", "achieved": cand_achieved, "peak": peak,
+                                                "unit": "GB/s", "frac": cand_achieved / peak,
+                                                "bytes_per_launch": bytes_cand, "ms": cd_ms},
         "kernels": kernels,
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
     }
@@ -509,6 +535,8 @@ def main():
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
     ap.add_argument("--workload", default="rmat23", choices=["rmat23", "rmat21", "grid", "er", "batch", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--algo", default="segmented", choices=["segmented", "edge"],
+                    help="edge: the edge-centric (Combining CRCW) path, for comparison")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if ws > 1:

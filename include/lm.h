@@ -59,6 +59,9 @@ extern "C" {
 
 /* lm_config.flags */
 #define LM_F_PROFILE   1u   /* record CUDA events around every kernel (fills lm_stats timings) */
+#define LM_F_EDGE_CENTRIC 2u /* lm_match takes the edge-centric path: every live edge offers its key
+                                to both ends with an atomic maximum (the Combining CRCW formulation
+                                of Sec. 2) instead of the row-wise segmented maximum; same result */
 
 typedef struct lm_ctx lm_ctx;
 typedef struct lm_graph lm_graph;

@@ -143,6 +143,7 @@ void engine_free(Engine& e) {
     if (e.dargs) cudaFree(e.dargs);
     if (e.hargs) cudaFreeHost(e.hargs);
     destroy_job_graph(e.graph);
+    destroy_job_graph(e.egraph);
     cudaGetLastError();
     e = Engine();
 }
@@ -431,6 +432,97 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     return check_err(ctx, e);
 }
 
+// The edge-centric path of one graph (LM_F_EDGE_CENTRIC).  Its arguments sit
+// in the second half of the argument area; the live edge lists reuse the
+// workspace's neighbour buffers, the offers its long-row maxima, the stamps its
+// long-row counters (all of which it leaves at zero).
+constexpr size_t EDGE_ARGS_OFF = ARG_AREA / 2;
+struct EdgeJobArgs {
+    InitArgs init;
+    EdgeArgs ea;
+};
+int match_edges(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof) {
+    cudaStream_t s = e.stream;
+    int rc = ensure_ws(ctx, e, g->n, g->nent, 1);
+    if (rc) return rc;
+    Workspace& w = e.ws;
+    uint32_t* mate_d = dev_out ? mate : w.mate;
+    static_assert(EDGE_ARGS_OFF + sizeof(EdgeJobArgs) <= ARG_AREA, "argument area too small");
+    EdgeJobArgs& A = *reinterpret_cast<EdgeJobArgs*>(e.hargs + EDGE_ARGS_OFF);
+    EdgeJobArgs* D = reinterpret_cast<EdgeJobArgs*>(e.dargs + EDGE_ARGS_OFF);
+    memset(&A, 0, sizeof A);
+    A.init.mate = mate_d;
+    A.init.dead = w.dead;
+    A.init.dbase = 0;
+    A.init.bcnt = w.bcnt;
+    A.init.bkey = w.bkey;
+    A.init.n = g->n;
+    A.init.max_rounds = g->m + 2;
+    A.init.st = e.st;
+    const uint64_t z = splitmix64_first(seed);
+    EdgeArgs& a = A.ea;
+    a.edges = g->edges;
+    a.eword = g->eword;
+    a.m = g->m;
+    a.k0 = (uint32_t)z;
+    a.k1 = (uint32_t)(z >> 32);
+    a.nvert = g->n;
+    a.live[0] = w.nbr[0];
+    a.live[1] = w.nbr[1];
+    a.cap = w.cap_e;
+    a.best = w.bkey;
+    a.stamp = w.bcnt;
+    a.dead = w.dead;
+    a.mate = mate_d;
+    a.st = e.st;
+    LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
+    if (g->m == 0) {
+        prof.begin(LM_K_INIT);
+        LM_CK(ctx, launch_init(s, &D->init));
+        prof.end();
+    } else if (!prof.on) {
+        if (!e.egraph) LM_CK(ctx, build_edge_graph(&D->init, &D->ea, e.st, &e.egraph));
+        LM_CK(ctx, launch_job_graph(e.egraph, s));
+        prof.launches[LM_K_INIT] += 1;
+    } else {
+        prof.begin(LM_K_INIT);
+        LM_CK(ctx, launch_init(s, &D->init));
+        prof.end();
+        static const int kinds[4] = {LM_K_CAND, LM_K_VERTEX, LM_K_SWEEP, LM_K_OTHER};
+        const auto t_start = std::chrono::steady_clock::now();
+        for (;;) {
+            for (int ph = 0; ph < 4; ph++) {
+                prof.begin(kinds[ph]);
+                LM_CK(ctx, launch_edge_round(s, &D->ea, ph));
+                prof.end();
+            }
+            LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+            LM_CK(ctx, cudaStreamSynchronize(s));
+            if (e.st_host->err || e.st_host->done) break;
+            if (e.st_host->round > g->m + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            const auto waited = std::chrono::steady_clock::now() - t_start;
+            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)LOOP_LIMIT_NS)
+                return fail(ctx, LM_ETIMEOUT, "round loop exceeded its time limit");
+        }
+    }
+    LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LM_CK(ctx, cudaStreamSynchronize(s));
+    if (g->m && !prof.on) {
+        const uint32_t rounds = e.st_host->round >= 1 ? e.st_host->round - 1 : 0;  // rounds the loop ran
+        prof.launches[LM_K_CAND] += rounds;
+        prof.launches[LM_K_VERTEX] += rounds;
+        prof.launches[LM_K_SWEEP] += rounds;
+        prof.launches[LM_K_OTHER] += rounds;
+    }
+    rc = check_err(ctx, e);
+    if (rc) return rc;
+    if (!dev_out && g->n > 0) {
+        LM_CK(ctx, cudaMemcpyAsync(mate, mate_d, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+        LM_CK(ctx, cudaStreamSynchronize(s));
+    }
+    return LM_OK;
+}
+
 // One graph on engine e, results to mate (device memory when dev_out, else host
 // memory staged through the workspace); the engine's DevState holds its statistics.
 int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof) {
@@ -627,6 +719,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     gc.add(&g->nbr, (size_t)g->nent + 4);
     gc.add(&g->pk, (size_t)g->nent + 4);
     gc.add(&g->edges, (size_t)g->m + 2);
+    gc.add(&g->eword, (size_t)g->m + 4);
     ce = cudaMalloc(&g->block, gc.total);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
     gc.assign(g->block);
@@ -634,7 +727,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
     if (m > 0) {
         LM_CK(ctx, cudaMemcpyAsync(cursor, g->off, nn * 4, cudaMemcpyDeviceToDevice, s));
-        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges));
+        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges, g->eword));
     }
     LM_CK(ctx, launch_build_rows(s, deg, rowidx, g->off, n, g->nrows, g->nent, g->vid, g->rdeg, g->roff));
     if (g->nrows) {
@@ -674,7 +767,9 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
     if (stats) memset(stats, 0, sizeof *stats);
     Prof prof(ctx, ctx->eng.stream);
-    const int rc = match_one(ctx, ctx->eng, g, seed, mate, is_device_ptr(mate), prof);
+    const bool dev_out = is_device_ptr(mate);
+    const int rc = (ctx->flags & LM_F_EDGE_CENTRIC) ? match_edges(ctx, ctx->eng, g, seed, mate, dev_out, prof)
+                                                    : match_one(ctx, ctx->eng, g, seed, mate, dev_out, prof);
     if (rc) return rc;
     if (stats) {
         fill_round_stats(*ctx->eng.st_host, stats);

@@ -58,6 +58,7 @@ struct Engine {
     char* dargs = nullptr;           // [ARG_AREA] kernel arguments (device)
     char* hargs = nullptr;           // [ARG_AREA] their pinned staging
     void* graph = nullptr;           // executable job graph (device-driven round loop)
+    void* egraph = nullptr;          // the same for the edge-centric path
     LaunchCfg cfg;                   // launch parameters of the next jobs
     LaunchCfg graph_cfg;             // the ones `graph` was built with
     Workspace ws;
@@ -103,6 +104,7 @@ struct lm_graph {
     uint32_t* nbr = nullptr;         // [2m] neighbour of each entry
     uint64_t* pk = nullptr;          // [2m] ord(weight) << 32 | edge index, per entry
     uint64_t* edges = nullptr;       // [m] edge records eu | ev << 32
+    uint32_t* eword = nullptr;       // [m] ord(weight) of each edge (edge-centric path)
 };
 
 namespace lm {

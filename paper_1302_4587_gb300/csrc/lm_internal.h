@@ -207,6 +207,23 @@ struct JobArgs {
     VertexArgs v[4];          // round 0, round 1, loop rounds of parity 0 and 1
     SweepArgs s[4];           // round-0 compaction, round 1, loop rounds of parity 0 and 1
 };
+// The edge-centric path (LM_F_EDGE_CENTRIC) of one graph: per round every live
+// edge offers its key to both ends (atomic maximum), an edge that is the best
+// offer at both ends is matched, and the others with no matched end are
+// compacted into the next round's edge list.  Round r = DevState::round - 1.
+struct EdgeArgs {
+    const uint64_t* edges;       // [m] eu | ev << 32
+    const uint32_t* eword;       // [m] ord(weight)
+    uint32_t m, k0, k1, nvert;
+    uint32_t* live[2];           // live edge ids by round parity (round 0: every edge, implicitly)
+    uint32_t cap;                // capacity of each live list
+    unsigned long long* best;    // [n] heaviest offer of the running round (zero between rounds)
+    uint32_t* stamp;             // [n] round + 1 of the last offer (zero between rounds)
+    uint32_t* dead;              // matched bits
+    uint32_t* mate;
+    DevState* st;
+};
+
 constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
 
 // ---------------------------------------------------------------------------
@@ -227,6 +244,10 @@ uint64_t splitmix64_first(uint64_t seed);  // lm_api.cpp
 // flag is set); returns a cudaError_t value
 int build_job_graph(const JobArgs* dargs, DevState* st, const struct LaunchCfg& cfg, void** exec_out);
 int launch_job_graph(void* exec, void* stream);
+// edge-centric path: the job graph (init, then a conditional loop of rounds) and the
+// per-round launches of the profiled path
+int build_edge_graph(const InitArgs* init, const EdgeArgs* dargs, DevState* st, void** exec_out);
+int launch_edge_round(void* stream, const EdgeArgs* dargs, int phase);  // phase 0 offer, 1 match, 2 compact, 3 close
 void destroy_job_graph(void* exec);
 
 // graph construction
@@ -236,7 +257,7 @@ int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint3
                           size_t tmp_words);
 size_t exclusive_scan_tmp_words(uint32_t count);
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges);
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword);
 int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, const uint32_t* off,
                       uint32_t n, uint32_t nrows, uint32_t nent, uint32_t* vid0, uint32_t* rdeg0, uint32_t* roff);
 int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uint32_t nent, uint32_t* tmap,

@@ -998,6 +998,155 @@ __global__ void k_round0_cut(const Round0Args* __restrict__ pa) {
     }
 }
 
+// ---------------------------------------------------------------- edge-centric path
+// The Combining CRCW formulation of Sec. 2 (LM_F_EDGE_CENTRIC): per round,
+// (offer) every live edge raises best[] of both ends to its key with an atomic
+// maximum, lanes of a warp on the same vertex combining first; (match) an edge
+// that is the best offer at both ends joins M; (compact) edges with no matched
+// end go to the next round's list; (close) one thread records the round.
+
+constexpr int EC_T = 256;
+
+__device__ __forceinline__ uint32_t ec_round(const EdgeArgs& a) { return ld_volatile_u32(&a.st->round) - 1u; }
+
+// warp-combined atomic maximum: lanes with the same vertex reduce first
+__device__ __forceinline__ void warp_max_at(unsigned long long* best, uint32_t x, unsigned long long K, bool act) {
+    const uint32_t ball = __ballot_sync(FULL, act);
+    const uint32_t peers = __match_any_sync(FULL, act ? x : NIL) & ball;
+    if (!act) return;
+    const uint32_t hi = __reduce_max_sync(peers, (uint32_t)(K >> 32));
+    const uint32_t lo = __reduce_max_sync(peers, ((uint32_t)(K >> 32) == hi) ? (uint32_t)K : 0u);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&best[x], ((unsigned long long)hi << 32) | lo);
+}
+
+__global__ void __launch_bounds__(EC_T) k_ec_offer(const EdgeArgs* __restrict__ pa) {
+    const EdgeArgs& a = *pa;
+    const uint32_t r = ec_round(a);
+    const uint32_t cnt = r == 0 ? a.m : ld_volatile_u32(&a.st->lcnt[0][r & 1u]);
+    const uint32_t* L = a.live[r & 1u];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->lcnt[0][(r + 1) & 1u] = 0;
+    const uint32_t stride = gridDim.x * blockDim.x, cr = (cnt + 31) & ~31u;
+    uint32_t fresh = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cr; i += stride) {
+        bool act = i < cnt;
+        uint32_t u = 0, v = 0;
+        unsigned long long K = 0;
+        if (act) {
+            const uint32_t e = r == 0 ? i : L[i];
+            if (e >= a.m) set_err(a.st, ERR_BOUNDS, e);
+            act = e < a.m;  // (the whole warp stays in the loop for the collectives below)
+        }
+        if (act) {
+            const uint32_t e = r == 0 ? i : L[i];
+            const uint64_t rec = a.edges[e];
+            u = (uint32_t)rec;
+            v = (uint32_t)(rec >> 32);
+            K = ((unsigned long long)a.eword[e] << 32) | perm_seed(e, a.k0, a.k1);
+        }
+        warp_max_at(a.best, u, K, act);
+        warp_max_at(a.best, v, K, act);
+        if (act) {  // live vertices of the round: the first offer stamps them
+            fresh += atomicExch(&a.stamp[u], r + 1u) != r + 1u;
+            fresh += atomicExch(&a.stamp[v], r + 1u) != r + 1u;
+        }
+    }
+    fresh = __reduce_add_sync(FULL, fresh);
+    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(&a.st->live_rows, fresh);
+}
+
+__global__ void __launch_bounds__(EC_T) k_ec_match(const EdgeArgs* __restrict__ pa) {
+    const EdgeArgs& a = *pa;
+    const uint32_t r = ec_round(a);
+    const uint32_t cnt = r == 0 ? a.m : ld_volatile_u32(&a.st->lcnt[0][r & 1u]);
+    const uint32_t* L = a.live[r & 1u];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned long long matched = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+        const uint32_t e = r == 0 ? i : L[i];
+        if (e >= a.m) continue;
+        const uint64_t rec = a.edges[e];
+        const uint32_t u = (uint32_t)rec, v = (uint32_t)(rec >> 32);
+        const unsigned long long K = ((unsigned long long)a.eword[e] << 32) | perm_seed(e, a.k0, a.k1);
+        if (a.best[u] == K && a.best[v] == K) {
+            a.mate[u] = v;
+            a.mate[v] = u;
+            atomicOr(&a.dead[u >> 5], 1u << (u & 31));
+            atomicOr(&a.dead[v >> 5], 1u << (v & 31));
+            matched += 2;
+        }
+    }
+    if (matched) atomicAdd(&a.st->matched2, matched);
+}
+
+__global__ void __launch_bounds__(EC_T) k_ec_compact(const EdgeArgs* __restrict__ pa) {
+    const EdgeArgs& a = *pa;
+    const uint32_t r = ec_round(a);
+    const uint32_t cnt = r == 0 ? a.m : ld_volatile_u32(&a.st->lcnt[0][r & 1u]);
+    const uint32_t* L = a.live[r & 1u];
+    uint32_t* N = a.live[(r + 1) & 1u];
+    uint32_t* ncnt = &a.st->lcnt[0][(r + 1) & 1u];
+    const uint32_t stride = gridDim.x * blockDim.x, cr = (cnt + 31) & ~31u, lane = threadIdx.x & 31;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cr; i += stride) {
+        bool keep = false;
+        uint32_t e = 0;
+        if (i < cnt) {
+            e = r == 0 ? i : L[i];
+            if (e < a.m) {
+                const uint64_t rec = a.edges[e];
+                const uint32_t u = (uint32_t)rec, v = (uint32_t)(rec >> 32);
+                a.best[u] = 0;  // offers and stamps go back to zero for the next round
+                a.best[v] = 0;
+                a.stamp[u] = 0;
+                a.stamp[v] = 0;
+                keep = !(((__ldg(&a.dead[u >> 5]) >> (u & 31)) | (__ldg(&a.dead[v >> 5]) >> (v & 31))) & 1u);
+            }
+        }
+        const uint32_t ball = __ballot_sync(FULL, keep);
+        uint32_t base = 0;
+        if (lane == 0 && ball) base = atomicAdd(ncnt, (uint32_t)__popc(ball));
+        base = __shfl_sync(FULL, base, 0) + __popc(ball & lanemask_lt());
+        if (keep) {
+            if (base < a.cap) N[base] = e;
+            else set_err(a.st, ERR_BOUNDS, base);
+        }
+    }
+}
+
+// one thread: the round's statistics, completion, the next round's index
+__device__ void ec_close(const EdgeArgs& a) {
+    DevState* st = a.st;
+    const uint32_t r = ec_round(a);
+    const uint32_t cnt = r == 0 ? a.m : ld_volatile_u32(&st->lcnt[0][r & 1u]);
+    const uint32_t next = ld_volatile_u32(&st->lcnt[0][(r + 1) & 1u]);
+    if (r < 64) {
+        st->ring_m[r] = cnt;
+        st->ring_n[r] = ld_volatile_u32(&st->live_rows);
+    }
+    st->live_rows = 0;
+    if (next == 0 && !st->done) {
+        st->done = 1;
+        st->rounds = r + 1;
+    }
+    st->round = r + 2;
+}
+__global__ void k_ec_close(const EdgeArgs* __restrict__ pa) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ec_close(*pa);
+}
+__global__ void k_ec_check(const EdgeArgs* __restrict__ pa, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const EdgeArgs& a = *pa;
+    ec_close(a);
+    DevState* st = a.st;
+    unsigned int go = 1;
+    if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) go = 0;
+    else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
+             globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+        set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
 // ---------------------------------------------------------------- graph construction
 // Edge-list passes of the graph build.  Lanes of a warp that hit the same
 // vertex (R-MAT hubs) combine into one atomic: the lowest of them adds the
@@ -1036,7 +1185,7 @@ __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const fl
     }
 }
 __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges) {
+                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword) {
     const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
     const uint32_t mr = (m + 31) & ~31u;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < mr; e += stride) {
@@ -1046,8 +1195,10 @@ __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float
         if (ok) {
             u = eu[e];
             v = ev[e];
-            word = ((uint64_t)ord_of_bits(__float_as_uint(w[e])) << 32) | e;
+            const uint32_t ow = ord_of_bits(__float_as_uint(w[e]));
+            word = ((uint64_t)ow << 32) | e;
             edges[e] = (uint64_t)u | ((uint64_t)v << 32);
+            eword[e] = ow;
         }
         const uint32_t pu = warp_add(&cursor[u], u, ok, lane);
         const uint32_t pv = warp_add(&cursor[v], v, ok, lane);
@@ -1372,8 +1523,9 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
     return (int)cudaGetLastError();
 }
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges) {
-    k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, pk, edges);
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword) {
+    k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, pk, edges,
+                                                                     eword);
     return (int)cudaGetLastError();
 }
 int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t* flags) {
@@ -1509,6 +1661,62 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, vo
         if (e) break;
         void* cparams[2] = {&st, &h};
         if ((e = add_kernel(body, &bn, bp, (void*)k_loop_check, dim3(1), dim3(32), cparams))) break;
+        cudaGraphExec_t ex = nullptr;
+        if ((e = cudaGraphInstantiate(&ex, g, 0))) break;
+        *exec_out = ex;
+    } while (0);
+    cudaGraphDestroy(g);
+    return (int)e;
+}
+
+static uint32_t ec_grid() { return (uint32_t)current_sms() * 8; }
+
+int launch_edge_round(void* stream, const EdgeArgs* d, int phase) {
+    const cudaStream_t s = (cudaStream_t)stream;
+    switch (phase) {
+        case 0: k_ec_offer<<<ec_grid(), EC_T, 0, s>>>(d); break;
+        case 1: k_ec_match<<<ec_grid(), EC_T, 0, s>>>(d); break;
+        case 2: k_ec_compact<<<ec_grid(), EC_T, 0, s>>>(d); break;
+        default: k_ec_close<<<1, 32, 0, s>>>(d); break;
+    }
+    return (int)cudaGetLastError();
+}
+
+// init -> while (live) { offer, match, compact, check }
+int build_edge_graph(const InitArgs* init, const EdgeArgs* dargs, DevState* st, void** exec_out) {
+    *exec_out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return (int)e;
+    const InitArgs* p_init = init;
+    const EdgeArgs* p_a = dargs;
+    void* init_params[1] = {&p_init};
+    void* params[1] = {&p_a};
+    cudaGraphNode_t node = nullptr;
+    do {
+        if ((e = add_kernel(g, &node, nullptr, (void*)k_init, dim3(current_sms() * 16), dim3(256), init_params))) break;
+        cudaGraphNode_t prev = node;
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault))) break;
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        memset(cp_raw, 0, sizeof cp_raw);
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&node, g, &prev, nullptr, 1, &cp))) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t bn = nullptr, bp = nullptr;
+        const dim3 grid(ec_grid()), block(EC_T);
+        if ((e = add_kernel(body, &bn, bp, (void*)k_ec_offer, grid, block, params))) break;
+        bp = bn;
+        if ((e = add_kernel(body, &bn, bp, (void*)k_ec_match, grid, block, params))) break;
+        bp = bn;
+        if ((e = add_kernel(body, &bn, bp, (void*)k_ec_compact, grid, block, params))) break;
+        bp = bn;
+        void* cparams[2] = {&p_a, &h};
+        if ((e = add_kernel(body, &bn, bp, (void*)k_ec_check, dim3(1), dim3(32), cparams))) break;
         cudaGraphExec_t ex = nullptr;
         if ((e = cudaGraphInstantiate(&ex, g, 0))) break;
         *exec_out = ex;
