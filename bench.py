@@ -479,6 +479,66 @@ def run_serve(args, ws, rank, local):
     }
 
 
+def run_paper_sweep(args, ws, rank, local):
+    """The shape of the paper's GPU comparison (Sec. 3.3, rgg and random-graph
+    figures): for random geometric graphs and random graphs with alpha n edges
+    (alpha = 4, 16, 64), the time of lm_match on a device-resident graph
+    against the literal sequential local max (the oracle's C code, one core of
+    this host) on the same graph, over a range of sizes."""
+    import torch
+    import oracle
+    import paper_1302_4587_gb300 as lm
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = lm.lm_create(local, None)
+    rows = []
+    fams = [("rgg", None, [15, 17, 19, 21]), ("random", 4, [15, 17, 19, 21]),
+            ("random", 16, [15, 17, 19, 21]), ("random", 64, [15, 17, 19])]
+    for fam, alpha, logs in fams:
+        for lg in logs:
+            n = 1 << lg
+            g = synth.rgg(n, 20 + lg) if fam == "rgg" else synth.er(n, alpha * n, seed=30 + lg)
+            seed = 7
+            eu = torch.from_numpy(g.eu.view(np.int32)).to(dev)
+            ev = torch.from_numpy(g.ev.view(np.int32)).to(dev)
+            w = torch.from_numpy(g.w).to(dev)
+            h = lm.lm_graph_create(ctx, g.n, eu, ev, w)
+            del eu, ev, w
+            mate = torch.empty(g.n, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                lm.lm_match(ctx, h, seed, mate)
+            t = []
+            for _ in range(max(5, args.steps // 2)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                lm.lm_match(ctx, h, seed, mate)
+                e1.record()
+                torch.cuda.synchronize()
+                t.append(e0.elapsed_time(e1))
+            gpu_ms = statistics.median(t)
+            got = mate.cpu().numpy().view(np.uint32)
+            t0 = time.perf_counter()
+            want, rounds, _, _ = oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed)
+            seq_ms = (time.perf_counter() - t0) * 1e3
+            lm.lm_graph_destroy(h)
+            rows.append({"family": fam, "alpha": alpha, "n": n, "m": g.m, "rounds": int(rounds),
+                         "gpu_ms": gpu_ms, "sequential_local_max_ms": seq_ms,
+                         "speedup": seq_ms / gpu_ms, "gpu_edges_per_s": g.m / (gpu_ms * 1e-3),
+                         "identical": bool(np.array_equal(got, want[:g.n]))})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    lm.lm_destroy(ctx)
+    best = max(r["speedup"] for r in rows)
+    return {"metric": "speedup of lm_match over the sequential local max (max over the sweep)", "value": best,
+            "unit": "x", "n_gpus": ws, "steps": args.steps, "warmup": 3, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)",
+            "data": "synthetic", "config": {"workload": "paper_sweep",
+                                            "desc": "rgg (0.55 sqrt(ln n / n)) and random graphs alpha n edges, "
+                                                    "alpha 4/16/64, n = 2^15..2^21, w~U[0,1); sequential local max "
+                                                    "on one host core"},
+            "table": rows}
+
+
 def cpu_baseline(budget_s: float = 20.0):
     """The oracle (greedy, one thread) on a bounded sample of the workload: an
     R-MAT graph of the same family at scale 20.  Beside it, the literal
@@ -533,7 +593,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
-    ap.add_argument("--workload", default="rmat23", choices=["rmat23", "rmat21", "grid", "er", "batch", "serve"])
+    ap.add_argument("--workload", default="rmat23",
+                    choices=["rmat23", "rmat21", "grid", "er", "batch", "serve", "paper_sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--algo", default="segmented", choices=["segmented", "edge"],
                     help="edge: the edge-centric (Combining CRCW) path, for comparison")
@@ -549,8 +610,8 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    if args.workload in ("batch", "serve"):
-        out = (run_batch if args.workload == "batch" else run_serve)(args, ws, rank, local)
+    if args.workload in ("batch", "serve", "paper_sweep"):
+        out = {"batch": run_batch, "serve": run_serve, "paper_sweep": run_paper_sweep}[args.workload](args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         if ws > 1:

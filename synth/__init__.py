@@ -60,6 +60,8 @@ def _lib():
             lib.sx_derive.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.gen_er.restype = ctypes.c_int64
             lib.gen_er.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, u32p, u32p]
+            lib.gen_rgg.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64, u32p, u32p, ctypes.c_uint64]
+            lib.gen_rgg.restype = ctypes.c_int64
             lib.gen_grid.restype = ctypes.c_int64
             lib.gen_grid.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_uint64, u32p, u32p, ctypes.c_uint64]
@@ -125,6 +127,20 @@ def er(n: int = 10_000, m: int = 50_000, seed: int = 1, unit: bool = False) -> G
         raise ValueError("gen_er failed")
     return Graph(n, eu[:got].copy(), ev[:got].copy(), weights(got, derive(seed, 3), unit),
                  f"er_n{n}_m{m}_s{seed}{'_unit' if unit else ''}")
+
+
+def rgg(n: int, seed: int = 6) -> Graph:
+    """Random geometric graph of Sec. 3: n points uniform in the unit square, an
+    edge between points closer than 0.55 sqrt(ln n / n); weights U[0,1) (the
+    paper states no weights for this family)."""
+    r = 0.55 * math.sqrt(math.log(n) / n) if n > 1 else 0.0
+    cap = int(n * math.pi * r * r * n * 0.75) + 4 * n + 1024
+    eu = np.empty(max(cap, 1), dtype=np.uint32)
+    ev = np.empty(max(cap, 1), dtype=np.uint32)
+    got = _lib().gen_rgg(n, r, derive(seed, 13), _p(eu, ctypes.c_uint32), _p(ev, ctypes.c_uint32), cap)
+    if got < 0:
+        raise ValueError("gen_rgg failed")
+    return Graph(n, eu[:got].copy(), ev[:got].copy(), weights(got, derive(seed, 3)), f"rgg_n{n}_s{seed}")
 
 
 def grid(rows: int = 1024, cols: int = 1024, frac_long: float = 0.05, seed: int = 2,

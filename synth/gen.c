@@ -135,6 +135,72 @@ int64_t gen_grid(uint32_t rows, uint32_t cols, uint32_t n_vertices, uint64_t n_l
 }
 
 /* ------------------------------------------------------------------ */
+/* Random geometric graph (Sec. 3's rgg family): n points uniform in the unit
+ * square (point i from draws 2i and 2i+1), an edge between every two points
+ * closer than `radius`.  Points are bucketed in k x k cells of side 1/k >=
+ * radius; each pair is listed once, from its lower id, in id order and, for one
+ * id, in cell-scan order.  Returns the edge count, or -1 when cap is too small
+ * or on allocation failure. */
+int64_t gen_rgg(uint32_t n, double radius, uint64_t seed, uint32_t* eu, uint32_t* ev, uint64_t cap) {
+    if (n == 0) return 0;
+    if (!(radius > 0.0)) return 0;
+    uint32_t k = (uint32_t)(1.0 / radius);
+    if (k < 1) k = 1;
+    if (k > 65536) k = 65536;
+    double* x = (double*)malloc((size_t)n * sizeof(double));
+    double* y = (double*)malloc((size_t)n * sizeof(double));
+    uint32_t* cell = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t* start = (uint32_t*)calloc((size_t)k * k + 1, sizeof(uint32_t));
+    uint32_t* order = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
+    if (!x || !y || !cell || !start || !order) {
+        free(x); free(y); free(cell); free(start); free(order);
+        return -1;
+    }
+    for (uint32_t i = 0; i < n; i++) {
+        x[i] = u01(sx_at(seed, 2ull * i));
+        y[i] = u01(sx_at(seed, 2ull * i + 1));
+        uint32_t cx = (uint32_t)(x[i] * k), cy = (uint32_t)(y[i] * k);
+        if (cx >= k) cx = k - 1;
+        if (cy >= k) cy = k - 1;
+        cell[i] = cy * k + cx;
+        start[cell[i] + 1]++;
+    }
+    for (uint64_t c = 0; c < (uint64_t)k * k; c++) start[c + 1] += start[c];
+    {
+        uint32_t* fill = (uint32_t*)malloc(((size_t)k * k + 1) * sizeof(uint32_t));
+        if (!fill) { free(x); free(y); free(cell); free(start); free(order); return -1; }
+        memcpy(fill, start, ((size_t)k * k + 1) * sizeof(uint32_t));
+        for (uint32_t i = 0; i < n; i++) order[fill[cell[i]]++] = i;  /* ids ascending within a cell */
+        free(fill);
+    }
+    const double r2 = radius * radius;
+    uint64_t m = 0;
+    int fail = 0;
+    for (uint32_t i = 0; i < n && !fail; i++) {
+        const int32_t cx = (int32_t)(cell[i] % k), cy = (int32_t)(cell[i] / k);
+        for (int32_t dy = -1; dy <= 1 && !fail; dy++) {
+            for (int32_t dx = -1; dx <= 1 && !fail; dx++) {
+                const int32_t nx = cx + dx, ny = cy + dy;
+                if (nx < 0 || ny < 0 || nx >= (int32_t)k || ny >= (int32_t)k) continue;
+                const uint32_t c = (uint32_t)ny * k + (uint32_t)nx;
+                for (uint32_t t = start[c]; t < start[c + 1]; t++) {
+                    const uint32_t j = order[t];
+                    if (j <= i) continue;
+                    const double ddx = x[i] - x[j], ddy = y[i] - y[j];
+                    if (ddx * ddx + ddy * ddy >= r2) continue;
+                    if (m >= cap) { fail = 1; break; }
+                    eu[m] = i;
+                    ev[m] = j;
+                    m++;
+                }
+            }
+        }
+    }
+    free(x); free(y); free(cell); free(start); free(order);
+    return fail ? -1 : (int64_t)m;
+}
+
+/* ------------------------------------------------------------------ */
 /* R-MAT: one edge = `scale` quadrant choices with probabilities (a,b,c,d).
  * Draw j of edge e uses counter e*scale + j of the stream `seed`. */
 static inline void rmat_edge(int scale, double a, double ab, double abc, uint64_t seed,
