@@ -363,11 +363,13 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
 // ---------------------------------------------------------------- sweep
 // Tasks: [0, nC) chunks of long rows, then batches of 32 rows of R.
 // Warps take tasks round-robin and never synchronise with each other.
+// two 32-entry groups in flight per warp at six CTAs (48 warps) per SM measured
+// faster than four groups at four CTAs: the sweep is latency-bound
 #ifndef LM_SG
-#define LM_SG 4
+#define LM_SG 2
 #endif
 #ifndef LM_SWEEP_MINB
-#define LM_SWEEP_MINB 4
+#define LM_SWEEP_MINB 6
 #endif
 
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
