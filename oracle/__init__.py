@@ -71,6 +71,8 @@ def _lib():
             lib.lmo_seq_local_max.restype = ctypes.c_int64
             lib.lmo_seq_local_max.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, f32p,
                                               ctypes.c_uint64, u32p, u64p, u64p, ctypes.c_uint64]
+            lib.lmo_seq_local_max_renew.restype = ctypes.c_int64
+            lib.lmo_seq_local_max_renew.argtypes = lib.lmo_seq_local_max.argtypes
             lib.lmo_brute_mwm.restype = ctypes.c_double
             lib.lmo_brute_mwm.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, f32p]
             _LIB = lib
@@ -136,15 +138,17 @@ def greedy(n: int, eu, ev, w, seed: int) -> np.ndarray:
     return mate[:n]
 
 
-def seq_local_max(n: int, eu, ev, w, seed: int, max_rounds: int = 1 << 16):
-    """(mate[], rounds, round_m[], round_n[]) of the sequential local max (Sec. 2)."""
+def seq_local_max(n: int, eu, ev, w, seed: int, max_rounds: int = 1 << 16, renew: bool = False):
+    """(mate[], rounds, round_m[], round_n[]) of the sequential local max (Sec. 2); with
+    renew=True the perturbation is renewed in every iteration (the footnote to Lemma 1)."""
     eu, up = _u32(eu)
     ev, vp = _u32(ev)
     w, wp = _f32(w)
     mate = np.empty(max(n, 1), dtype=np.uint32)
     rm = np.zeros(max_rounds, dtype=np.uint64)
     rn = np.zeros(max_rounds, dtype=np.uint64)
-    r = _lib().lmo_seq_local_max(n, eu.shape[0], up, vp, wp, _seed(seed),
+    fn = _lib().lmo_seq_local_max_renew if renew else _lib().lmo_seq_local_max
+    r = fn(n, eu.shape[0], up, vp, wp, _seed(seed),
                                  mate.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                  rm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                  rn.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), max_rounds)

@@ -21,7 +21,9 @@
  *       matching; this is the oracle for the GPU's mate[].
  *   lmo_seq_local_max -- the three-pass sequential local max of Sec. 2
  *       ("Sequential Model"), iteration by iteration, recording the live edge
- *       and live vertex counts at the start of every iteration.
+ *       and live vertex counts at the start of every iteration;
+ *       lmo_seq_local_max_renew the same with the perturbation renewed in
+ *       every iteration (Sec. 2, the footnote to Lemma 1).
  *   lmo_brute_mwm -- maximum weight matching by exhaustive dynamic
  *       programming over vertex subsets (small n only), for the
  *       1/2-approximation property cited in Sec. 1.
@@ -150,9 +152,29 @@ int64_t lmo_greedy(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* e
  * vertex count (unmatched vertices with a remaining edge) at the start of
  * iteration r, for r < max_rounds.  Returns the number of iterations, or -1
  * on allocation failure. */
+static int64_t seq_local_max(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev,
+                             const float* w, uint64_t seed, int renew, uint32_t* mate,
+                             uint64_t* round_m, uint64_t* round_n, uint64_t max_rounds);
+
 int64_t lmo_seq_local_max(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev,
                           const float* w, uint64_t seed, uint32_t* mate,
                           uint64_t* round_m, uint64_t* round_n, uint64_t max_rounds) {
+    return seq_local_max(n, m, eu, ev, w, seed, 0, mate, round_m, round_n, max_rounds);
+}
+
+/* The same algorithm with the random perturbation renewed in every iteration,
+ * as the proof of Lemma 1 assumes (Sec. 2, its footnote): iteration r orders
+ * the edges by (weight, perm of the r-th SplitMix64 output of the seed), i.e.
+ * lmo_key(w, seed + r * golden_gamma, e); iteration 0 is the unrenewed order. */
+int64_t lmo_seq_local_max_renew(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev,
+                                const float* w, uint64_t seed, uint32_t* mate,
+                                uint64_t* round_m, uint64_t* round_n, uint64_t max_rounds) {
+    return seq_local_max(n, m, eu, ev, w, seed, 1, mate, round_m, round_n, max_rounds);
+}
+
+static int64_t seq_local_max(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev,
+                             const float* w, uint64_t seed, int renew, uint32_t* mate,
+                             uint64_t* round_m, uint64_t* round_n, uint64_t max_rounds) {
     uint64_t* key = (uint64_t*)malloc((m ? m : 1) * sizeof(uint64_t));
     uint32_t* live = (uint32_t*)malloc((m ? m : 1) * sizeof(uint32_t));
     uint64_t* cand = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));   /* key of C[v] */
@@ -176,6 +198,10 @@ int64_t lmo_seq_local_max(uint32_t n, uint64_t m, const uint32_t* eu, const uint
             round_m[rounds] = nlive;
             round_n[rounds] = nv;
         }
+        /* renewed perturbation: this iteration's keys */
+        if (renew && rounds > 0)
+            for (uint64_t i = 0; i < nlive; i++)
+                key[live[i]] = lmo_key(w[live[i]], seed + rounds * 0x9E3779B97F4A7C15ull, live[i]);
         /* pass 1 */
         for (uint64_t i = 0; i < nlive; i++) {
             uint32_t e = live[i];

@@ -248,3 +248,36 @@ def test_checks_reject_planted_mistakes():
     gu = synth.er(300, 1500, 11, unit=True)
     a = oracle.greedy(gu.n, gu.eu, gu.ev, gu.w, 1)
     assert not dominated(gu.eu, gu.ev, oracle.keys(gu.w, 2), a)
+
+
+# ---- the renewed perturbation (Sec. 2, the footnote to Lemma 1) -------------
+
+def test_renewed_order_changes_nothing_when_weights_are_distinct():
+    # ties never reach the permutation, so renewing it cannot change the result:
+    # renewed local max = unrenewed local max = greedy (two independent algorithms)
+    for seed in (1, 2, 3):
+        g0 = synth.er(3000, 12000, seed=40 + seed)
+        w = (np.random.default_rng(seed).permutation(g0.m) + 1).astype(np.float32)  # distinct weights
+        g = synth.Graph(g0.n, g0.eu, g0.ev, w, "distinct")
+        assert len(np.unique(g.w)) == g.m
+        a, ra, ma, na = oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed, renew=True)
+        b, rb, mb, nb = oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed)
+        assert np.array_equal(a, b) and np.array_equal(a, oracle.greedy(g.n, g.eu, g.ev, g.w, seed))
+        assert ra == rb and np.array_equal(ma, mb) and np.array_equal(na, nb)
+
+
+def test_renewed_order_on_unit_weights():
+    diff = 0
+    for seed in range(6):
+        g = synth.er(2000, 8000, seed=50 + seed, unit=True)
+        a, ra, ma, _ = oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed, renew=True)
+        b, _, mb, _ = oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed)
+        assert is_matching(g.n, g.eu, g.ev, a) and is_maximal(g.eu, g.ev, a)
+        # iteration 0 uses the unrenewed order: the first two live counts agree
+        assert ma[0] == mb[0] and ma[1] == mb[1]
+        diff += int(not np.array_equal(a, b))
+        # Lemma 1 (renewed noise): at least half of the edges leave per iteration in
+        # expectation; with this many edges every early iteration does so
+        for r in range(min(3, ra - 1)):
+            assert ma[r + 1] <= ma[r] / 2 + 3 * np.sqrt(ma[r])
+    assert diff > 0  # renewal does change unit-weight results
