@@ -145,6 +145,9 @@ def make_workload(name: str):
         return synth.grid(1024, 1024, 0.05, seed=2), 102, "2D grid 1024x1024 4-neighbour + 5% long-range, w~U[0,1)"
     if name == "er":
         return synth.er(10_000, 50_000, seed=1), 101, "Erdos-Renyi n=10000 m=50000, w~U[0,1)"
+    if name == "rmat23_unit":
+        g = synth.rmat(scale=23, edge_factor=16, seed=3, unit=True)
+        return g, 103, "R-MAT scale 23, edge factor 16, unit weights (every order decided by the perturbation)"
     raise ValueError(name)
 
 
@@ -193,7 +196,8 @@ def run_lm(args, ws, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     edge = args.algo == "edge"
-    ctx = lm.lm_create(local, stream, flags=lm.LM_F_EDGE_CENTRIC if edge else 0)
+    order = lm.LM_F_RENEW if args.order == "renewed" else 0
+    ctx = lm.lm_create(local, stream, flags=(lm.LM_F_EDGE_CENTRIC if edge else 0) | order)
     eu = torch.from_numpy(g.eu.view(np.int32)).to(dev)
     ev = torch.from_numpy(g.ev.view(np.int32)).to(dev)
     w = torch.from_numpy(g.w).to(dev)
@@ -226,7 +230,7 @@ def run_lm(args, ws, rank, local):
     clocks = clk.summary()
 
     # per-kernel device times (CUDA events recorded by the library on its stream)
-    pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE | (lm.LM_F_EDGE_CENTRIC if edge else 0))
+    pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE | (lm.LM_F_EDGE_CENTRIC if edge else 0) | order)
     if tuning:
         lm.lm_set_tuning(pctx, tuning["rmax"], tuning["chunk"], tuning["sweep_ctas_per_sm"],
                          tuning["vertex_ctas_per_sm"])
@@ -295,6 +299,7 @@ def run_lm(args, ws, rank, local):
                    "rounds": pst["rounds"], "graph_bytes": graph_bytes,
                    "l2": f"inputs larger than L2 (graph arrays {graph_bytes / 1e9:.1f} GB, L2 0.13 GB)",
                    "tuning": tuning, "algorithm": "edge-centric" if edge else "segmented",
+                   "order": args.order,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": ({"bound": "hbm", "kernel": "k_ec_offer + k_ec_match + k_ec_compact (all launches)",
                       "achieved": ec_achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -302,7 +307,7 @@ def run_lm(args, ws, rank, local):
                      if edge else
                      {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
                       "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                      "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload),
+                      "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload) if not order else None,
                       "bytes_per_match": bytes_sweep, "ms_per_match": sw_ms,
                       "launches_per_match": pst["kernel_launches"][lm.LM_K_SWEEP],
                       "profiled_total_ms": statistics.median(total_ms)}),
@@ -594,11 +599,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
     ap.add_argument("--workload", default="rmat23",
-                    choices=["rmat23", "rmat21", "grid", "er", "batch", "serve", "paper_sweep"])
+                    choices=["rmat23", "rmat21", "grid", "er", "rmat23_unit", "batch", "serve", "paper_sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--algo", default="segmented", choices=["segmented", "edge"],
                     help="edge: the edge-centric (Combining CRCW) path, for comparison")
+    ap.add_argument("--order", default="fixed", choices=["fixed", "renewed"],
+                    help="renewed: the perturbation is renewed every round (LM_F_RENEW)")
     args = ap.parse_args()
+    if args.algo == "edge" and args.order == "renewed":
+        ap.error("the edge-centric path keeps the fixed order")
     ws, rank, local = _dist()
     if ws > 1:
         import torch

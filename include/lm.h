@@ -62,6 +62,12 @@ extern "C" {
 #define LM_F_EDGE_CENTRIC 2u /* lm_match takes the edge-centric path: every live edge offers its key
                                 to both ends with an atomic maximum (the Combining CRCW formulation
                                 of Sec. 2) instead of the row-wise segmented maximum; same result */
+#define LM_F_RENEW     4u   /* lm_match / lm_batch_match renew the perturbation every round, as the
+                                proof of Lemma 1 assumes (Sec. 2, its footnote): round r orders edges
+                                by (weight, perm_seed with the halves of the r-th SplitMix64 output of
+                                the seed); round 0 is the default order.  The result can differ from
+                                the default's when weights tie.  Not with LM_F_EDGE_CENTRIC, and
+                                lm_submit refuses it (LM_EINVAL) */
 
 typedef struct lm_ctx lm_ctx;
 typedef struct lm_graph lm_graph;

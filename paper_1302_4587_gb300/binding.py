@@ -20,6 +20,7 @@ LM_NIL = 0xFFFFFFFF
 LM_HOST, LM_DEVICE = 0, 1
 LM_F_PROFILE = 1
 LM_F_EDGE_CENTRIC = 2
+LM_F_RENEW = 4
 LM_STATS_ROUNDS = 64
 LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_COUNT = range(6)
 

@@ -116,6 +116,7 @@ SegIn seg_of(const lm_graph* g, uint64_t seed, uint32_t vbase, uint32_t ebase, u
     d.vbase = vbase;
     d.k0 = (uint32_t)z;
     d.k1 = (uint32_t)(z >> 32);
+    d.seed = seed;
     return d;
 }
 
@@ -598,11 +599,13 @@ int lm_create(const lm_config* cfg, lm_ctx** out) {
     }
     DevGuard g(cfg->device);
     if (!g.ok) return LM_ECUDA;
+    if ((cfg->flags & LM_F_EDGE_CENTRIC) && (cfg->flags & LM_F_RENEW)) return LM_EINVAL;
     std::unique_ptr<lm_ctx> ctx(new lm_ctx());
     ctx->device = cfg->device;
     ctx->budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (40ull << 30);
     ctx->max_slots = cfg->max_slots ? cfg->max_slots : 4096;
     ctx->flags = cfg->flags;
+    ctx->eng.cfg.renew = (cfg->flags & LM_F_RENEW) != 0;
     int rc = engine_init(ctx.get(), ctx->eng, (cudaStream_t)cfg->stream);
     if (rc) {
         engine_free(ctx->eng);
@@ -921,6 +924,7 @@ int lm_set_tuning(lm_ctx* ctx, const lm_tuning* t) {
     LaunchCfg c;
     if (!cfg_from(t, &c)) return fail(ctx, LM_EINVAL, "tuning out of range");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
+    c.renew = ctx->eng.cfg.renew;  // the order is the context's, not a tuning knob
     ctx->eng.cfg = c;
     return LM_OK;
 }

@@ -101,7 +101,8 @@ struct SegIn {
     uint32_t ntiles, tile_begin;  // round-0 tiles of the graph and the job-wide index of the first
     uint32_t ebase;           // union entry index of the graph's entry 0
     uint32_t vbase;           // union id of the graph's vertex 0
-    uint32_t k0, k1;          // perm_seed keys of the graph's seed
+    uint32_t k0, k1;          // perm_seed keys of the graph's seed (round 0)
+    uint64_t seed;            // the seed itself (renewed keys of later rounds)
 };
 
 // Launch parameters a context may tune (lm_set_tuning / lm_autotune): the
@@ -112,12 +113,13 @@ struct LaunchCfg {
     uint32_t chunk_shift = 0;
     uint32_t sweep_ctas_per_sm = 0;
     uint32_t vertex_ctas_per_sm = 4;
+    bool renew = false;  // sweeps renew the order every round (LM_F_RENEW)
     LaunchCfg() {
         while ((1u << chunk_shift) < CHUNK) chunk_shift++;
     }
     bool operator==(const LaunchCfg& o) const {
         return rmax == o.rmax && chunk_shift == o.chunk_shift && sweep_ctas_per_sm == o.sweep_ctas_per_sm &&
-               vertex_ctas_per_sm == o.vertex_ctas_per_sm;
+               vertex_ctas_per_sm == o.vertex_ctas_per_sm && renew == o.renew;
     }
     bool operator!=(const LaunchCfg& o) const { return !(*this == o); }
 };

@@ -375,39 +375,75 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
 constexpr int SG = LM_SG;      // groups of 32 entries a warp keeps in flight
 
+template <bool RENEW>
 struct WarpRows {              // one warp's batch of rows
     unsigned long long rkey[32];   // heaviest surviving key per row
     uint32_t rcnt[32];             // survivors per row
     uint32_t rstart[32];           // union entry index of the row (output base)
     uint32_t rseg[32];             // graph of the row
+    uint32_t rk0[RENEW ? 32 : 1], rk1[RENEW ? 32 : 1];  // renewed order: the row's keys this round
 };
+
+// SplitMix64 (Steele, Lea, Flood 2014): the r-th output (r >= 0) for state `seed`
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint32_t r) {
+    uint64_t z = seed + (uint64_t)(r + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// keys ordering the entries of graph g in the round being prepared (nr): the graph's
+// own keys, or with a renewed order those of the nr-th SplitMix64 output
+template <bool RENEW>
+__device__ __forceinline__ void round_keys(const SweepArgs& a, uint32_t g, uint32_t nr, uint32_t& k0, uint32_t& k1) {
+    const SegIn& sg = a.segs[g];
+    if (RENEW) {
+        const uint64_t z = splitmix64_at(sg.seed, nr);
+        k0 = (uint32_t)z;
+        k1 = (uint32_t)(z >> 32);
+    } else {
+        k0 = sg.k0;
+        k1 = sg.k1;
+    }
+}
 
 // neighbour of v over the edge with key K (the edge is incident to v): the key's
 // low half is perm_seed(e); its inverse gives e, whose record holds both ends
-__device__ __forceinline__ uint32_t recover_nbr_seg(const SegIn& sg, DevState* st, uint32_t v, uint64_t K) {
-    const uint32_t e = perm_seed_inv((uint32_t)K, sg.k0, sg.k1);
+__device__ __forceinline__ uint32_t recover_nbr_keys(const SegIn& sg, DevState* st, uint32_t v, uint64_t K,
+                                                     uint32_t k0, uint32_t k1) {
+    const uint32_t e = perm_seed_inv((uint32_t)K, k0, k1);
     if (e >= sg.m) { set_err(st, ERR_BOUNDS, e); return NIL; }
     const uint64_t rec = sg.edges[e];
     const uint32_t x = (uint32_t)rec, y = (uint32_t)(rec >> 32), vl = v - sg.vbase;
     if (x != vl && y != vl) { set_err(st, ERR_BOUNDS, e); return NIL; }
     return (x == vl ? y : x) + sg.vbase;
 }
-__device__ __forceinline__ uint32_t recover_nbr(const SweepArgs& a, uint32_t v, uint32_t g, uint64_t K) {
-    return recover_nbr_seg(a.segs[g], a.st, v, K);
+__device__ __forceinline__ uint32_t recover_nbr_seg(const SegIn& sg, DevState* st, uint32_t v, uint64_t K) {
+    return recover_nbr_keys(sg, st, v, K, sg.k0, sg.k1);
 }
 
-// the stored word of entry q (input: ord(w) << 32 | edge id; live: the key) and its key
+// the stored word of entry q (input, or live with a renewed order: ord(w) << 32 |
+// edge id; live otherwise: the key) and its key under (k0, k1)
 template <bool INPUT>
 __device__ __forceinline__ uint64_t entry_word(const SweepArgs& a, uint32_t g, uint32_t q) {
     if (INPUT) return __ldcs(a.segs[g].pk + q);
     return __ldcs(a.in_key + q);
 }
-template <bool INPUT>
-__device__ __forceinline__ uint64_t word_key(const SweepArgs& a, uint32_t g, uint64_t w) {
-    if (INPUT) {
-        const SegIn& sg = a.segs[g];
-        return (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, sg.k0, sg.k1);
-    }
+template <bool INPUT, bool RENEW>
+__device__ __forceinline__ uint64_t word_key(uint32_t k0, uint32_t k1, uint64_t w) {
+    if (INPUT || RENEW) return (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, k0, k1);
+    return w;
+}
+// what a survivor stores: its key, or with a renewed order its edge id (keys change per round)
+template <bool RENEW>
+__device__ __forceinline__ uint64_t stored_word(uint32_t k0, uint32_t k1, uint64_t key) {
+    if (RENEW) return (key & 0xFFFFFFFF00000000ull) | perm_seed_inv((uint32_t)key, k0, k1);
+    return key;
+}
+// the key of stored word w of row r of a warp's batch
+template <bool INPUT, bool RENEW>
+__device__ __forceinline__ uint64_t row_word_key(const SweepArgs& a, const WarpRows<RENEW>& W, uint32_t r, uint64_t w) {
+    if (RENEW) return word_key<INPUT, true>(W.rk0[r], W.rk1[r], w);
+    if (INPUT) { const SegIn& sg = a.segs[W.rseg[r]]; return word_key<true, false>(sg.k0, sg.k1, w); }
     return w;
 }
 template <bool INPUT>
@@ -420,8 +456,8 @@ __device__ __forceinline__ uint32_t entry_nbr(const SweepArgs& a, uint32_t g, ui
 }
 
 // One row batch: 32 rows of R walked as one flattened sequence.
-template <bool INPUT, bool COMPACT>
-__device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR, int lane) {
+template <bool INPUT, bool COMPACT, bool RENEW>
+__device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint32_t nR, uint32_t nr, int lane) {
     const VertexArrays& va = a.va;
     const uint32_t idx = b * 32 + lane;
     uint32_t v = NIL, L = 0, s0 = 0, g = 0;
@@ -440,6 +476,12 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
     W.rcnt[lane] = 0;
     W.rstart[lane] = s0;
     W.rseg[lane] = g;
+    uint32_t rk0 = 0, rk1 = 0;
+    if (RENEW) {
+        round_keys<true>(a, g, nr, rk0, rk1);
+        W.rk0[lane] = rk0;
+        W.rk1[lane] = rk1;
+    }
     const uint32_t ro = INPUT ? s0 - a.segs[g].ebase : s0;  // source index of the row's entry 0
     const uint32_t incl = warp_incl_scan(L, lane);
     const uint32_t ex = incl - L;                             // the row's first flattened entry
@@ -496,11 +538,11 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 }
             }
 #pragma unroll
-            for (int i = 0; i < SG; i++) key[i] = keep[i] ? word_key<INPUT>(a, W.rseg[r[i]], key[i]) : 0ull;
+            for (int i = 0; i < SG; i++) key[i] = keep[i] ? row_word_key<INPUT, RENEW>(a, W, r[i], key[i]) : 0ull;
         } else {
 #pragma unroll
             for (int i = 0; i < SG; i++)
-                if (r[i] != 32) key[i] = word_key<INPUT>(a, W.rseg[r[i]], key[i]);
+                if (r[i] != 32) key[i] = row_word_key<INPUT, RENEW>(a, W, r[i], key[i]);
         }
         // per row: compaction slots and maximum, aggregated over the lanes of a row
 #pragma unroll
@@ -522,7 +564,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                         base = __shfl_sync(FULL, base, 0);
                         if (surv) {
                             const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & lt);
-                            a.out_key[pos] = key[i];
+                            a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
                             a.out_nbr[pos] = u[i];
                         }
                     }
@@ -542,7 +584,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
                 if (COMPACT) {
                     base = __shfl_sync(grp, base, leader);
                     const uint32_t pos = W.rstart[r[i]] + base + __popc(grp & lt);
-                    a.out_key[pos] = key[i];
+                    a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
                     a.out_nbr[pos] = u[i];
                 }
             }
@@ -553,14 +595,14 @@ __device__ void do_rows(const SweepArgs& a, WarpRows& W, uint32_t b, uint32_t nR
     if (v != NIL) {
         if (COMPACT) va.len[a.par ^ 1u][v] = W.rcnt[lane];
         const uint64_t K = W.rkey[lane];
-        if (K) va.cnbr[v] = recover_nbr(a, v, g, K);
+        if (K) va.cnbr[v] = RENEW ? recover_nbr_keys(a.segs[g], a.st, v, K, rk0, rk1) : recover_nbr_seg(a.segs[g], a.st, v, K);
     }
     __syncwarp();
 }
 
 // One chunk of a long row (all lanes on the same row).
-template <bool INPUT, bool COMPACT>
-__device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
+template <bool INPUT, bool COMPACT, bool RENEW>
+__device__ void do_chunk(const SweepArgs& a, uint32_t t, uint32_t nr, int lane) {
     const VertexArrays& va = a.va;
     const uint2 c = a.in.C[t];
     const uint32_t v = c.x;
@@ -571,6 +613,15 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
     const uint32_t g = va.gid ? va.gid[v] : 0u;
     if (jb >= L || (uint64_t)s0 + L > a.ecap || g >= a.nsegs) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); return; }
     const uint32_t off = INPUT ? s0 - a.segs[g].ebase : s0;
+    // renewed order: this round's keys, held for the chunk; default order: the graph's
+    // keys, read where they are needed (two registers fewer across the loop)
+    uint32_t ck0 = 0, ck1 = 0;
+    if (RENEW) round_keys<true>(a, g, nr, ck0, ck1);
+    auto chunk_key = [&](uint64_t w) -> uint64_t {
+        if (RENEW) return word_key<INPUT, true>(ck0, ck1, w);
+        if (INPUT) { const SegIn& sg = a.segs[g]; return word_key<true, false>(sg.k0, sg.k1, w); }
+        return w;
+    };
     uint32_t* len_next = va.len[a.par ^ 1u];
     uint64_t bk = 0;
     const uint32_t lt = lanemask_lt();
@@ -598,11 +649,11 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
                 }
             }
 #pragma unroll
-            for (int i = 0; i < SG; i++) key[i] = keep[i] ? word_key<INPUT>(a, g, key[i]) : 0ull;
+            for (int i = 0; i < SG; i++) key[i] = keep[i] ? chunk_key(key[i]) : 0ull;
         } else {
 #pragma unroll
             for (int i = 0; i < SG; i++)
-                if (j + i * 32 + lane < je) key[i] = word_key<INPUT>(a, g, key[i]);
+                if (j + i * 32 + lane < je) key[i] = chunk_key(key[i]);
         }
         uint32_t ball[SG], sub = 0;
 #pragma unroll
@@ -619,7 +670,7 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
             for (int i = 0; i < SG; i++) {
                 if (key[i] != 0) {
                     const uint32_t pos = s0 + base + __popc(ball[i] & lt);
-                    a.out_key[pos] = key[i];
+                    a.out_key[pos] = stored_word<RENEW>(ck0, ck1, key[i]);
                     a.out_nbr[pos] = u[i];
                 }
                 base += __popc(ball[i]);
@@ -641,17 +692,17 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, int lane) {
             const uint64_t R = *reinterpret_cast<volatile unsigned long long*>(&va.bkey[v]);
             va.bkey[v] = 0;
             va.bcnt[v] = 0;
-            if (R) va.cnbr[v] = recover_nbr(a, v, g, R);
+            if (R) va.cnbr[v] = RENEW ? recover_nbr_keys(a.segs[g], a.st, v, R, ck0, ck1) : recover_nbr_seg(a.segs[g], a.st, v, R);
         }
     }
 }
 
-template <bool INPUT, bool COMPACT>
+template <bool INPUT, bool COMPACT, bool RENEW>
 __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __restrict__ pav) {
-    __shared__ WarpRows s_rows[ST / 32];
+    __shared__ WarpRows<RENEW> s_rows[ST / 32];
     const SweepArgs& a = *pav;
     const int lane = threadIdx.x & 31;
-    WarpRows& W = s_rows[threadIdx.x >> 5];
+    WarpRows<RENEW>& W = s_rows[threadIdx.x >> 5];
     const uint32_t gw = (blockIdx.x * ST + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * ST) >> 5;
     const uint32_t nR = ld_volatile_u32(&a.in.cnt[0]);
@@ -661,6 +712,8 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
         return;
     }
     const uint32_t total = nC + (nR + 31) / 32;
+    // the round whose candidates this sweep prepares (its vertex pass advanced the round)
+    const uint32_t nr = RENEW ? ld_volatile_u32(&a.st->round) : 0u;
     // a warp's first task is its own index (idle warps leave without an atomic), later
     // ones come from the counter; the next index is fetched while the current task runs
     uint32_t t = gw;
@@ -669,8 +722,8 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
     for (;; t = __shfl_sync(FULL, t_next, 0)) {
         if (t >= total) break;
         if (lane == 0) t_next = nw + atomicAdd(a.task_ctr, 1u);
-        if (t < nC) do_chunk<INPUT, COMPACT>(a, t, lane);
-        else do_rows<INPUT, COMPACT>(a, W, t - nC, nR, lane);
+        if (t < nC) do_chunk<INPUT, COMPACT, RENEW>(a, t, nr, lane);
+        else do_rows<INPUT, COMPACT, RENEW>(a, W, t - nC, nR, nr, lane);
     }
 }
 
@@ -1466,12 +1519,12 @@ int launch_vertex(void* stream, const VertexArgs* dargs, const LaunchCfg& cfg) {
     return (int)cudaGetLastError();
 }
 
-template <bool I, bool C>
+template <bool I, bool C, bool RN>
 static uint32_t sweep_grid(const LaunchCfg& cfg) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<I, C>, ST, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<I, C, RN>, ST, 0);
         blocks_per_sm = per > 0 ? per : 1;
     }
     int per = blocks_per_sm;
@@ -1481,7 +1534,8 @@ static uint32_t sweep_grid(const LaunchCfg& cfg) {
 
 template <bool I, bool C>
 static int launch_sweep_t(void* stream, const SweepArgs* dargs, const LaunchCfg& cfg) {
-    k_sweep<I, C><<<sweep_grid<I, C>(cfg), ST, 0, (cudaStream_t)stream>>>(dargs);
+    if (cfg.renew) k_sweep<I, C, true><<<sweep_grid<I, C, true>(cfg), ST, 0, (cudaStream_t)stream>>>(dargs);
+    else k_sweep<I, C, false><<<sweep_grid<I, C, false>(cfg), ST, 0, (cudaStream_t)stream>>>(dargs);
     return (int)cudaGetLastError();
 }
 static int round0_blocks_per_sm() {
@@ -1515,7 +1569,10 @@ int launch_round0_cut(void* stream, const Round0Args* d) {
     k_round0_cut<<<round0_cut_grid(), 256, 0, (cudaStream_t)stream>>>(d);
     return (int)cudaGetLastError();
 }
-int launch_sweep_cand(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<true, false>(stream, d, c); }
+int launch_sweep_cand(void* stream, const SweepArgs* d, const LaunchCfg& c) {
+    if (c.renew) return (int)cudaErrorInvalidValue;  // round 0 keeps the default order: never needed
+    return launch_sweep_t<true, false>(stream, d, c);
+}
 int launch_sweep_input(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<true, true>(stream, d, c); }
 int launch_sweep_live(void* stream, const SweepArgs* d, const LaunchCfg& c) { return launch_sweep_t<false, true>(stream, d, c); }
 
@@ -1626,7 +1683,11 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, vo
         sparams[k][0] = &ps[k];
     }
     const dim3 vgrid(vertex_grid(cfg)), vblock(VT), sblock(ST), rblock(R0T), cgrid(round0_cut_grid());
-    const dim3 lgrid(sweep_grid<false, true>(cfg)), igrid(sweep_grid<true, true>(cfg));
+    const bool rn = cfg.renew;
+    const dim3 lgrid(rn ? sweep_grid<false, true, true>(cfg) : sweep_grid<false, true, false>(cfg));
+    const dim3 igrid(rn ? sweep_grid<true, true, true>(cfg) : sweep_grid<true, true, false>(cfg));
+    void* const k_input = rn ? (void*)k_sweep<true, true, true> : (void*)k_sweep<true, true, false>;
+    void* const k_live = rn ? (void*)k_sweep<false, true, true> : (void*)k_sweep<false, true, false>;
     do {
         if ((e = add_kernel(g, &node, prev, (void*)k_init, dim3(current_sms() * 16), dim3(256), init_params))) break;
         prev = node;
@@ -1636,11 +1697,11 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, vo
         prev = node;
         if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[0]))) break;
         prev = node;
-        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<true, true>, igrid, sblock, sparams[0]))) break;
+        if ((e = add_kernel(g, &node, prev, k_input, igrid, sblock, sparams[0]))) break;
         prev = node;
         if ((e = add_kernel(g, &node, prev, (void*)k_vertex, vgrid, vblock, vparams[1]))) break;
         prev = node;
-        if ((e = add_kernel(g, &node, prev, (void*)k_sweep<false, true>, lgrid, sblock, sparams[1]))) break;
+        if ((e = add_kernel(g, &node, prev, k_live, lgrid, sblock, sparams[1]))) break;
         prev = node;
         cudaGraphConditionalHandle h;
         if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault))) break;
@@ -1657,7 +1718,7 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, vo
         for (int k = 2; k < 4 && e == cudaSuccess; k++) {
             if ((e = add_kernel(body, &bn, bp, (void*)k_vertex, vgrid, vblock, vparams[k]))) break;
             bp = bn;
-            if ((e = add_kernel(body, &bn, bp, (void*)k_sweep<false, true>, lgrid, sblock, sparams[k]))) break;
+            if ((e = add_kernel(body, &bn, bp, k_live, lgrid, sblock, sparams[k]))) break;
             bp = bn;
         }
         if (e) break;

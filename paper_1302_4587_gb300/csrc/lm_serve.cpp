@@ -422,6 +422,7 @@ int lm_submit(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, uin
     if (!ctx) return LM_EINVAL;
     if (ctx->poisoned) return LM_ECUDA;
     if (!g || !mate || !ticket) return fail(ctx, LM_EINVAL, "null graph, mate or ticket");
+    if (ctx->flags & LM_F_RENEW) return fail(ctx, LM_EINVAL, "serving does not renew the order (LM_F_RENEW)");
     if (g->ctx->device != ctx->device) return fail(ctx, LM_EINVAL, "graph lives on another device");
     int cur = -1;
     cudaGetDevice(&cur);

@@ -16,13 +16,14 @@ def to_u32(t) -> np.ndarray:
 class Lm:
     """One lm context on cuda:0 for a test session."""
 
-    def __init__(self, profile: bool = False, budget: int = 0, edge_centric: bool = False):
+    def __init__(self, profile: bool = False, budget: int = 0, edge_centric: bool = False, renew: bool = False):
         import torch
         import paper_1302_4587_gb300 as lm
         self.lm = lm
         self.torch = torch
         torch.cuda.init()
-        flags = (lm.LM_F_PROFILE if profile else 0) | (lm.LM_F_EDGE_CENTRIC if edge_centric else 0)
+        flags = ((lm.LM_F_PROFILE if profile else 0) | (lm.LM_F_EDGE_CENTRIC if edge_centric else 0)
+                 | (lm.LM_F_RENEW if renew else 0))
         self.ctx = lm.lm_create(0, None, hbm_budget_bytes=budget, flags=flags)
 
     def close(self):
