@@ -33,7 +33,7 @@ METRIC = "input edges/s to maximal matching"
 # dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
 # an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
 # capture with several metrics); None for workloads without a capture of the current kernels
-TRAFFIC = {"rmat23": 7552133209}
+TRAFFIC: dict = {}
 
 
 def _peaks():
@@ -233,7 +233,7 @@ def run_lm(args, ws, rank, local):
     pctx = lm.lm_create(local, stream, flags=lm.LM_F_PROFILE | (lm.LM_F_EDGE_CENTRIC if edge else 0) | order)
     if tuning:
         lm.lm_set_tuning(pctx, tuning["rmax"], tuning["chunk"], tuning["sweep_ctas_per_sm"],
-                         tuning["vertex_ctas_per_sm"])
+                         tuning["vertex_ctas_per_sm"], tuning["batch"])
     kms = {k: [] for k in range(lm.LM_K_COUNT)}
     total_ms = []
     for i in range(max(args.warmup, 3) + args.steps):

@@ -172,19 +172,24 @@ int  lm_wait(lm_ctx* ctx, uint64_t ticket, uint32_t timeout_ms);
 
 /* Launch parameters of a context's matching path (the paper has no
  * counterpart; they only affect speed, never the result):
- *   rmax               rows with at most this many live entries are swept 32 to a
- *                      warp; longer rows are split into chunks (1 .. 2^20)
+ *   rmax               rows with at most this many live entries are swept in
+ *                      batches, one batch to a warp; longer rows are split into
+ *                      chunks (1 .. 2^20)
  *   chunk              entries per chunk of a long row (a power of two, 2^8 .. 2^20)
+ *   batch              a batch ends after 32 rows, or where its entries cross a
+ *                      multiple of `batch` (so it holds at most rmax + batch
+ *                      entries); a power of two, 2^6 .. 2^20, or 0 = 32 rows only
  *   sweep_ctas_per_sm  CTAs per SM of the sweep kernel (0 = as many as fit, at most 16)
  *   vertex_ctas_per_sm CTAs per SM of the vertex pass (0 = 4, at most 4)
  *   ms                 lm_autotune only: median time of one call with these parameters
- * Defaults: rmax 2048, chunk 4096, sweep 0, vertex 4.  The serving thread takes
+ * Defaults: rmax 1024, chunk 1024, sweep 0, vertex 4, batch 512.  The serving thread takes
  * the context's parameters when it starts (first lm_submit). */
 typedef struct lm_tuning {
     uint32_t rmax;
     uint32_t chunk;
     uint32_t sweep_ctas_per_sm;
     uint32_t vertex_ctas_per_sm;
+    uint32_t batch;
     double   ms;
 } lm_tuning;
 

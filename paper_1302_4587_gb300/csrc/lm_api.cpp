@@ -173,6 +173,7 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
     for (int k = 0; k < 4; k++) {
         c.add(&nw.R[k], V);
         c.add(&nw.C[k], C);
+        c.add(&nw.B[k], V);
     }
     for (int b = 0; b < 2; b++) {
         c.add(&nw.key[b], E);
@@ -223,6 +224,7 @@ Lists lists_of(Engine& e, int k) {
     Lists l;
     l.R = e.ws.R[k];
     l.C = e.ws.C[k];
+    l.B = e.ws.B[k];
     l.capR = e.ws.cap_v;
     l.capC = e.ws.cap_c;
     l.cnt = &e.st->lcnt[k][0];
@@ -315,6 +317,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         v.grounds = match ? job.grounds : nullptr;
         v.rmax = e.cfg.rmax;
         v.chunk_shift = e.cfg.chunk_shift;
+        v.batch_shift = e.cfg.batch_shift;
         v.st = e.st;
     };
     auto sargs = [&](SweepArgs& c, int in_set, uint32_t par, bool input) {
@@ -897,6 +900,10 @@ bool cfg_from(const lm_tuning* t, LaunchCfg* c) {
     if (!t || t->rmax < 1 || t->rmax > (1u << 20)) return false;
     if (t->chunk < 256 || t->chunk > (1u << 20) || (t->chunk & (t->chunk - 1))) return false;
     if (t->sweep_ctas_per_sm > 16 || t->vertex_ctas_per_sm > 4) return false;
+    if (t->batch && (t->batch < 64 || t->batch > (1u << 20) || (t->batch & (t->batch - 1)))) return false;
+    c->batch_shift = 32;
+    if (t->batch)
+        for (c->batch_shift = 0; (1u << c->batch_shift) < t->batch;) c->batch_shift++;
     c->rmax = t->rmax;
     c->chunk_shift = 0;
     while ((1u << c->chunk_shift) < t->chunk) c->chunk_shift++;
@@ -909,6 +916,7 @@ void tuning_of(const LaunchCfg& c, lm_tuning* t) {
     t->chunk = 1u << c.chunk_shift;
     t->sweep_ctas_per_sm = c.sweep_ctas_per_sm;
     t->vertex_ctas_per_sm = c.vertex_ctas_per_sm;
+    t->batch = c.batch_shift >= 32 ? 0u : 1u << c.batch_shift;
     t->ms = 0.0;
 }
 }  // namespace
@@ -933,9 +941,9 @@ int lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uin
                 uint32_t* const* mates, lm_tuning* best) {
     if (!ctx) return LM_EINVAL;
     if (count == 0 || !g || !seeds || !mates) return fail(ctx, LM_EINVAL, "nothing to tune on");
-    // candidates: task sizes from many short tasks to few long ones, sweep at full or
-    // three-quarter occupancy
-    static const uint32_t sizes[][2] = {{64, 1024}, {256, 2048}, {2048, 4096}, {8192, 16384}};
+    // candidates (rmax, chunk, batch): task sizes from many short tasks to few long
+    // ones, sweep at full or three-quarter occupancy
+    static const uint32_t sizes[][3] = {{256, 1024, 256}, {512, 1024, 256}, {1024, 1024, 512}, {2048, 4096, 1024}};
     static const uint32_t sweeps[] = {0, 3};
     lm_tuning keep;
     lm_get_tuning(ctx, &keep);
@@ -943,7 +951,7 @@ int lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uin
     top.ms = -1.0;
     for (const auto& sz : sizes) {
         for (uint32_t sw : sweeps) {
-            lm_tuning t = {sz[0], sz[1], sw, keep.vertex_ctas_per_sm, 0.0};
+            lm_tuning t = {sz[0], sz[1], sw, keep.vertex_ctas_per_sm, sz[2], 0.0};
             int rc = lm_set_tuning(ctx, &t);
             if (rc) return rc;
             std::vector<double> ms;

@@ -32,6 +32,7 @@ struct Workspace {
     // task lists: four sets, each R [cap_v] and C [cap_c]
     uint2* R[4] = {nullptr, nullptr, nullptr, nullptr};
     uint2* C[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t* B[4] = {nullptr, nullptr, nullptr, nullptr};   // [cap_v] first row of each batch of R
     // live entries (ping-pong), union entry space
     uint64_t* key[2] = {nullptr, nullptr};   // [cap_e]
     uint32_t* nbr[2] = {nullptr, nullptr};   // [cap_e]

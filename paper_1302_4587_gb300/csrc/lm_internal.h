@@ -31,14 +31,20 @@ namespace lm {
 
 constexpr uint32_t NIL = 0xFFFFFFFFu;
 
-// Task sizes of the sweep (measured on R-MAT scale 23: batching rows of up to
-// 2048 live entries 32 to a warp beats splitting them into chunk tasks, whose
-// slots need a global atomic per step)
+// Task sizes of the sweep.  A warp walks a sweep's task list at a rate set by
+// memory latency, so the longest task bounds the sweep's tail: rows of up to
+// LM_RMAX live entries are batched (at most 32 rows, and a batch ends where
+// its entries cross a multiple of 1 << LM_BATCH_SHIFT, so no batch holds much
+// more than LM_RMAX + that many entries); longer rows are cut into chunks of
+// LM_CHUNK entries.  Measured best on R-MAT scales 21 and 23 (1024 / 512 / 1024).
 #ifndef LM_CHUNK
-#define LM_CHUNK 4096
+#define LM_CHUNK 1024
 #endif
 #ifndef LM_RMAX
-#define LM_RMAX 2048
+#define LM_RMAX 1024
+#endif
+#ifndef LM_BATCH_SHIFT
+#define LM_BATCH_SHIFT 9
 #endif
 constexpr uint32_t CHUNK = LM_CHUNK;        // long rows are split into chunks of this size
 #ifndef LM_TILE0
@@ -57,17 +63,22 @@ LM_HD void kv_max(uint64_t& k, uint32_t& u, uint64_t k2, uint32_t u2) {
 }
 
 // Task lists of one round: R holds (vertex, live length) pairs, C holds
-// (vertex, chunk index) pairs; a row's chunks are consecutive in C.
+// (vertex, chunk index) pairs; a row's chunks are consecutive in C.  R is cut
+// into batches of consecutive rows (at most 32, see LaunchCfg::batch_shift):
+// bit 31 of a row's length word marks the first row of a batch, and B lists
+// the R index of every batch's first row, in no particular order.
+constexpr uint32_t BATCH_START = 0x80000000u;
 struct Lists {
     uint2* R;
     uint2* C;
-    uint32_t capR, capC;
-    uint32_t* cnt;            // device counters {nR, nC}
+    uint32_t* B;
+    uint32_t capR, capC;      // B holds at most capR entries
+    uint32_t* cnt;            // device counters {nR, nC, nB}
 };
 
 // Device-side control block (one per engine).
 struct DevState {
-    uint32_t lcnt[4][4];      // counters {nR, nC, -, -} of the four list sets
+    uint32_t lcnt[4][4];      // counters {nR, nC, nB, -} of the four list sets
     uint32_t exit_v, exit_s;  // CTAs of the running vertex pass / sweep that have finished
     uint32_t task[4];         // task counters of the sweeps that follow a vertex pass
     uint32_t err;             // ERR_* bits
@@ -113,13 +124,14 @@ struct LaunchCfg {
     uint32_t chunk_shift = 0;
     uint32_t sweep_ctas_per_sm = 0;
     uint32_t vertex_ctas_per_sm = 4;
+    uint32_t batch_shift = LM_BATCH_SHIFT;  // 32: batches of 32 rows only
     bool renew = false;  // sweeps renew the order every round (LM_F_RENEW)
     LaunchCfg() {
         while ((1u << chunk_shift) < CHUNK) chunk_shift++;
     }
     bool operator==(const LaunchCfg& o) const {
         return rmax == o.rmax && chunk_shift == o.chunk_shift && sweep_ctas_per_sm == o.sweep_ctas_per_sm &&
-               vertex_ctas_per_sm == o.vertex_ctas_per_sm && renew == o.renew;
+               vertex_ctas_per_sm == o.vertex_ctas_per_sm && batch_shift == o.batch_shift && renew == o.renew;
     }
     bool operator!=(const LaunchCfg& o) const { return !(*this == o); }
 };
@@ -157,6 +169,8 @@ struct VertexArgs {
     uint32_t* glive;          // live unmatched rows per graph seen by this pass, NULL = none
     uint32_t rmax;            // rows of at most this many live entries go to R, longer ones to C
     uint32_t chunk_shift;     // chunks of a long row hold 1 << chunk_shift entries
+    uint32_t batch_shift;     // a batch of R ends where its entries cross a multiple of
+                              // 1 << batch_shift (32: after 32 rows only)
     DevState* st;
 };
 

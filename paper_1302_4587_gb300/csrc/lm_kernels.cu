@@ -88,6 +88,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+__device__ __forceinline__ uint32_t lanemask_le() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -199,7 +204,7 @@ __device__ __forceinline__ void block_excl_scan3(uint32_t& a, uint32_t& b, uint3
 __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__ pav) {
     const VertexArgs& a = *pav;
     __shared__ uint32_t s_tmp[3 * (VT / 32)];
-    __shared__ uint32_t s_base[3];
+    __shared__ uint32_t s_base[3];  // list bases of the block: R, C, B
     __shared__ unsigned long long s_red[3 * (VT / 32)];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     DevState* st = a.st;
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
 
     for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
         uint32_t vv[VI], LL[VI], cls[VI], uu[VI];
-        uint32_t cR = 0, cC = 0, cX = 0;
+        uint32_t cR = 0, cC = 0, eR = 0;  // this thread's R rows, chunks and R entries
         // phase 1: the row's vertex
 #pragma unroll
         for (int i = 0; i < VI; i++) {
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                     my_match++;
                 } else {
                     open_row = true;
-                    if (L <= a.rmax) { cls[i] = 1; cR++; }
+                    if (L <= a.rmax) { cls[i] = 1; cR++; eR += L; }
                     else {
                         cls[i] = 2;
                         cC += ((L - 1) >> a.chunk_shift) + 1;
@@ -299,17 +304,27 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
         }
         // block-aggregated appends to the task lists
         uint32_t tot[3];
-        block_excl_scan3(cR, cC, cX, s_tmp, tot);
+        block_excl_scan3(cR, cC, eR, s_tmp, tot);
         if (tid == 0) {
             s_base[0] = tot[0] ? atomicAdd(&a.out.cnt[0], tot[0]) : 0;
             s_base[1] = tot[1] ? atomicAdd(&a.out.cnt[1], tot[1]) : 0;
         }
         __syncthreads();
-        uint32_t pR = s_base[0] + cR, pC = s_base[1] + cC;
+        // the block's R rows form one segment of R (row k of it at s_base[0] + k,
+        // its entries from offset eR within the segment); a batch starts at every
+        // 32nd row and at each row whose entries cross a multiple of 1 << batch_shift
+        const uint32_t pR0 = s_base[0] + cR;
+        uint32_t pR = pR0, pC = s_base[1] + cC, firsts = 0;
 #pragma unroll
         for (int i = 0; i < VI; i++) {
             if (cls[i] == 1) {
-                if (pR < a.out.capR) a.out.R[pR] = make_uint2(vv[i], LL[i]); else set_err(st, ERR_BOUNDS, pR);
+                const uint32_t k = pR - s_base[0];
+                const bool first = (k & 31u) == 0 ||
+                        (a.batch_shift < 32 && (eR >> a.batch_shift) != ((eR + LL[i]) >> a.batch_shift));
+                if (pR < a.out.capR) a.out.R[pR] = make_uint2(vv[i], LL[i] | (first ? BATCH_START : 0u));
+                else set_err(st, ERR_BOUNDS, pR);
+                firsts |= (first ? 1u : 0u) << i;
+                eR += LL[i];
                 pR++;
             } else if (cls[i] == 2) {
                 const uint32_t nch = ((LL[i] - 1) >> a.chunk_shift) + 1;
@@ -317,6 +332,23 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                     if (pC < a.out.capC) a.out.C[pC] = make_uint2(vv[i], c); else set_err(st, ERR_BOUNDS, pC);
                 }
             }
+        }
+        // the batches' first rows into B, block-aggregated (the first scan's reads of
+        // s_tmp are behind the barrier above)
+        uint32_t nb = __popc(firsts), d1 = 0, d2 = 0;
+        block_excl_scan3(nb, d1, d2, s_tmp, tot);
+        if (tid == 0) s_base[2] = tot[0] ? atomicAdd(&a.out.cnt[2], tot[0]) : 0;
+        __syncthreads();
+        uint32_t pB = s_base[2] + nb;
+        pR = pR0;
+#pragma unroll
+        for (int i = 0; i < VI; i++) {
+            if (cls[i] != 1) continue;
+            if ((firsts >> i) & 1u) {
+                if (pB < a.out.capR) a.out.B[pB] = pR; else set_err(st, ERR_BOUNDS, pB);
+                pB++;
+            }
+            pR++;
         }
         __syncthreads();  // s_base / s_tmp reuse
     }
@@ -343,7 +375,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
         const uint32_t done = atomicAdd(&st->exit_v, 1u);
         if (done == closers - 1) {
             __threadfence();
-            if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; }
+            if (a.in_set < 4) { st->lcnt[a.in_set][0] = 0; st->lcnt[a.in_set][1] = 0; st->lcnt[a.in_set][2] = 0; }
             st->task[0] = 0; st->task[1] = 0; st->task[2] = 0; st->task[3] = 0;
             if (a.match) {
                 const uint32_t rows = ld_volatile_u32(&st->live_rows);
@@ -381,6 +413,7 @@ struct WarpRows {              // one warp's batch of rows
     uint32_t rcnt[32];             // survivors per row
     uint32_t rstart[32];           // union entry index of the row (output base)
     uint32_t rseg[32];             // graph of the row
+    uint32_t ru[32];               // neighbour over the heaviest surviving key (compaction sweeps)
     uint32_t rk0[RENEW ? 32 : 1], rk1[RENEW ? 32 : 1];  // renewed order: the row's keys this round
 };
 
@@ -455,16 +488,21 @@ __device__ __forceinline__ uint32_t entry_nbr(const SweepArgs& a, uint32_t g, ui
     return __ldcs(a.in_nbr + q);
 }
 
-// One row batch: 32 rows of R walked as one flattened sequence.
+// One row batch (its first row is B[b]; it ends before the next row marked as a
+// batch start, after at most 32 rows): the rows walked as one flattened sequence.
 template <bool INPUT, bool COMPACT, bool RENEW>
 __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint32_t nR, uint32_t nr, int lane) {
     const VertexArrays& va = a.va;
-    const uint32_t idx = b * 32 + lane;
+    const uint32_t idx = __ldg(a.in.B + b) + lane;
+    uint2 rv = make_uint2(NIL, 0);
+    if (idx < nR) rv = a.in.R[idx];
+    // the batch's rows: lane 0's (a batch start) up to the next batch start
+    const uint32_t starts = __ballot_sync(FULL, (rv.y & BATCH_START) != 0);
+    if (lane == 0 && idx < nR && !(starts & 1u)) set_err(a.st, ERR_BOUNDS, idx);
     uint32_t v = NIL, L = 0, s0 = 0, g = 0;
-    if (idx < nR) {
-        const uint2 rv = a.in.R[idx];
+    if (idx < nR && (starts & 1u) && (starts & lanemask_le() & ~1u) == 0) {
         v = rv.x;
-        L = rv.y;
+        L = rv.y & ~BATCH_START;
         if (v >= va.nvert || L > a.rmax) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
         else {
             s0 = va.start[v];
@@ -494,7 +532,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
     // at positions 1..j (bits of an OR-reduction), minus one; uni[i] says that no
     // row starts inside group i.
     auto fetch = [&](uint32_t f0, uint32_t (&r)[SG], uint32_t (&q)[SG], uint32_t (&u)[SG], uint64_t (&key)[SG],
-                     bool (&uni)[SG]) {
+                     bool (&uni)[SG], uint32_t (&sl)[SG]) {
 #pragma unroll
         for (int i = 0; i < SG; i++) {
             const uint32_t g0 = f0 + i * 32, f = g0 + lane;
@@ -514,6 +552,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
                 r[i] = rr;
                 q[i] = ror + (f - exr);
             }
+            sl[i] = exr > g0 ? exr - g0 : 0u;
         }
 #pragma unroll
         for (int i = 0; i < SG; i++) {
@@ -522,10 +561,10 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
             key[i] = entry_word<INPUT>(a, W.rseg[r[i]], q[i]);
         }
     };
-    uint32_t r[SG], q[SG], u[SG];
+    uint32_t r[SG], q[SG], u[SG], sl[SG];  // sl: the group lane where the entry's row starts
     uint64_t key[SG];
     bool uni[SG];
-    fetch(0, r, q, u, key, uni);
+    fetch(0, r, q, u, key, uni, sl);
     for (uint32_t f0 = 0; f0 < F; f0 += 32 * SG) {
         if (COMPACT) {
             bool keep[SG];
@@ -555,47 +594,70 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
                     const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i] >> 32));
                     const uint32_t lo =
                         __reduce_max_sync(FULL, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
-                    uint32_t base = 0;
-                    if (lane == 0) {
-                        if (COMPACT) base = atomicAdd(&W.rcnt[r[i]], (uint32_t)__popc(ball));
-                        atomicMax(&W.rkey[r[i]], ((unsigned long long)hi << 32) | lo);
-                    }
+                    const uint64_t K = ((uint64_t)hi << 32) | lo;
                     if (COMPACT) {
-                        base = __shfl_sync(FULL, base, 0);
+                        uint32_t base = 0;
+                        if (surv) base = W.rcnt[r[i]];
+                        __syncwarp();
                         if (surv) {
                             const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & lt);
                             a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
                             a.out_nbr[pos] = u[i];
                         }
+                        // keys are distinct: exactly one lane (a survivor) holds the maximum
+                        if (key[i] == K) {
+                            W.rcnt[r[i]] = base + __popc(ball);
+                            if (K > W.rkey[r[i]]) { W.rkey[r[i]] = K; W.ru[r[i]] = u[i]; }
+                        }
+                    } else if (key[i] == K && K > W.rkey[r[i]]) {
+                        W.rkey[r[i]] = K;
                     }
+                    __syncwarp();
                 }
                 continue;
             }
-            const uint32_t grp = __match_any_sync(FULL, surv ? r[i] : 64u + lane);
-            if (surv) {
-                const int leader = __ffs(grp) - 1;
-                const uint32_t hi = __reduce_max_sync(grp, (uint32_t)(key[i] >> 32));
-                const uint32_t lo = __reduce_max_sync(grp, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
-                uint32_t base = 0;
-                if (lane == leader) {
-                    if (COMPACT) base = atomicAdd(&W.rcnt[r[i]], (uint32_t)__popc(grp));
-                    atomicMax(&W.rkey[r[i]], ((unsigned long long)hi << 32) | lo);
-                }
-                if (COMPACT) {
-                    base = __shfl_sync(grp, base, leader);
-                    const uint32_t pos = W.rstart[r[i]] + base + __popc(grp & lt);
+            // several rows in the group, each on a contiguous run of lanes from sl[i]:
+            // maxima by a segmented shuffle scan (the run's last lane holds its row's),
+            // slots from one vote; one lane per row updates the row's counters
+            uint64_t mx = key[i];
+            uint32_t mu = u[i];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t o = __shfl_up_sync(FULL, mx, d);
+                const uint32_t ou = COMPACT ? __shfl_up_sync(FULL, mu, d) : 0u;
+                if ((uint32_t)lane >= sl[i] + d && o > mx) { mx = o; mu = ou; }
+            }
+            const uint32_t rn = __shfl_down_sync(FULL, r[i], 1);
+            const bool last = r[i] != 32 && (lane == 31 || rn != r[i]);
+            if (COMPACT) {
+                const uint32_t run = FULL << sl[i];
+                const uint32_t ball = __ballot_sync(FULL, surv);
+                const uint32_t base = r[i] != 32 ? W.rcnt[r[i]] : 0u;
+                __syncwarp();
+                if (last) W.rcnt[r[i]] = base + __popc(ball & run & lanemask_le());
+                if (surv) {
+                    const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & run & lt);
                     a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
                     a.out_nbr[pos] = u[i];
                 }
             }
+            if (last && mx > W.rkey[r[i]]) {
+                W.rkey[r[i]] = mx;
+                if (COMPACT) W.ru[r[i]] = mu;
+            }
+            __syncwarp();
         }
-        if (f0 + 32 * SG < F) fetch(f0 + 32 * SG, r, q, u, key, uni);
+        if (f0 + 32 * SG < F) fetch(f0 + 32 * SG, r, q, u, key, uni, sl);
     }
     __syncwarp();
     if (v != NIL) {
         if (COMPACT) va.len[a.par ^ 1u][v] = W.rcnt[lane];
         const uint64_t K = W.rkey[lane];
-        if (K) va.cnbr[v] = RENEW ? recover_nbr_keys(a.segs[g], a.st, v, K, rk0, rk1) : recover_nbr_seg(a.segs[g], a.st, v, K);
+        // compaction sweeps carried the neighbour along; the candidate-only sweep
+        // recovers it from the key's edge id
+        if (K) va.cnbr[v] = COMPACT ? W.ru[lane]
+                                    : RENEW ? recover_nbr_keys(a.segs[g], a.st, v, K, rk0, rk1)
+                                            : recover_nbr_seg(a.segs[g], a.st, v, K);
     }
     __syncwarp();
 }
@@ -707,11 +769,12 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
     const uint32_t nw = (gridDim.x * ST) >> 5;
     const uint32_t nR = ld_volatile_u32(&a.in.cnt[0]);
     const uint32_t nC = ld_volatile_u32(&a.in.cnt[1]);
-    if (nR > a.in.capR || nC > a.in.capC) {
+    const uint32_t nB = ld_volatile_u32(&a.in.cnt[2]);
+    if (nR > a.in.capR || nC > a.in.capC || nB > nR) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a.st, ERR_BOUNDS, nC);
         return;
     }
-    const uint32_t total = nC + (nR + 31) / 32;
+    const uint32_t total = nC + nB;
     // the round whose candidates this sweep prepares (its vertex pass advanced the round)
     const uint32_t nr = RENEW ? ld_volatile_u32(&a.st->round) : 0u;
     // a warp's first task is its own index (idle warps leave without an atomic), later

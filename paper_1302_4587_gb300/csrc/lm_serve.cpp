@@ -165,6 +165,7 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         pre.par = par;
         pre.rmax = e.cfg.rmax;
         pre.chunk_shift = e.cfg.chunk_shift;
+        pre.batch_shift = e.cfg.batch_shift;
         pre.st = e.st;
     }
     auto vpass = [&](VertexArgs& v, int in_set, int out_set, uint32_t p = 2, uint32_t rnd = 0) {
@@ -180,6 +181,7 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
         v.grounds = w.grounds;
         v.rmax = e.cfg.rmax;
         v.chunk_shift = e.cfg.chunk_shift;
+        v.batch_shift = e.cfg.batch_shift;
         v.st = e.st;
     };
     vpass(A.v_live, par, par ^ 1u);

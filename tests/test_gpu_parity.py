@@ -16,8 +16,9 @@ from helpers import dominated, is_matching, is_maximal, load_hand_cases
 pytestmark = pytest.mark.gpu
 
 TILE = 1024   # entries per round-0 tile (TILE0)
-CHUNK = 4096  # entries per chunk task of a long row
-RMAX = 2048   # longest row handled as part of a 32-row batch
+CHUNK = 1024  # entries per chunk task of a long row (default tuning)
+RMAX = 1024   # longest row handled as part of a row batch (default tuning)
+BATCH = 512   # a row batch ends where its entries cross a multiple of this (default tuning)
 
 
 @pytest.fixture(scope="module")
@@ -247,7 +248,7 @@ def _stars(sizes, seed):
 def test_row_length_boundaries(lmctx):
     # rows right at the short-row limit, the chunk size and the tile size
     sizes = [RMAX - 2, RMAX - 1, RMAX, RMAX + 1, CHUNK - 1, CHUNK, CHUNK + 1, 2 * CHUNK + 1,
-             TILE - 1, TILE, TILE + 1, 3 * TILE]
+             TILE - 1, TILE, TILE + 1, 3 * TILE, BATCH - 1, BATCH, BATCH + 1, 2047, 2049, 4095, 4097, 8193]
     for seed in (1, 2):
         _check(lmctx, _stars(sizes, seed), seed)
 

@@ -16,7 +16,7 @@ from gpu_util import NIL, Lm
 
 pytestmark = pytest.mark.gpu
 
-RMAX, CHUNK, TILE = 2048, 4096, 1024
+RMAX, CHUNK, TILE = 1024, 1024, 1024
 
 
 @pytest.fixture(scope="module", params=[False, True], ids=["graph", "stream"])
@@ -127,7 +127,8 @@ def test_tuning_keeps_the_order(rn):
         lm.lm_set_tuning(rn.ctx, rmax=64, chunk=1024)
         _check(rn, synth.er(8000, 60_000, seed=14, unit=True), 3)
     finally:
-        lm.lm_set_tuning(rn.ctx, **{k: keep[k] for k in ("rmax", "chunk", "sweep_ctas_per_sm", "vertex_ctas_per_sm")})
+        lm.lm_set_tuning(rn.ctx, **{k: keep[k] for k in ("rmax", "chunk", "sweep_ctas_per_sm", "vertex_ctas_per_sm",
+                                                          "batch")})
 
 
 def test_serving_and_edge_centric_refuse_renewal(rn):

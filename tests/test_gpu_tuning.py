@@ -13,11 +13,13 @@ from gpu_util import Lm, to_u32
 pytestmark = pytest.mark.gpu
 
 SETTINGS = [
-    (1, 256, 0, 4),            # every row of two or more entries becomes chunk tasks
-    (4, 256, 1, 1),            # tiny tasks, one CTA per SM
-    (64, 1024, 3, 2),
-    (2048, 4096, 0, 4),        # the defaults
-    (1 << 20, 1 << 20, 16, 0),  # everything in row batches, largest chunk
+    (1, 256, 0, 4, 1024),            # every row of two or more entries becomes chunk tasks
+    (4, 256, 1, 1, 64),              # tiny tasks, one CTA per SM
+    (64, 1024, 3, 2, 0),             # batches of 32 rows, however many entries
+    (1024, 1024, 0, 4, 512),         # the defaults
+    (2048, 4096, 0, 4, 1024),
+    (2048, 4096, 0, 4, 64),          # nearly every row of 64+ entries its own batch
+    (1 << 20, 1 << 20, 16, 0, 1 << 20),  # everything in row batches, largest chunk
 ]
 
 
@@ -39,7 +41,9 @@ def _graphs():
     return [(synth.rmat(scale=12, edge_factor=8, seed=5), 3),
             (synth.grid(64, 64, 0.05, seed=6), 4),
             (synth.er(3000, 12000, seed=7, unit=True), 5),
-            (_stars([3, 300, 257, 1025, 5000], 8), 6)]
+            (_stars([3, 300, 257, 1025, 5000], 8), 6),
+            # rows around batch boundaries of 64 and 1024 entries, 40 of each length
+            (_stars([k for k in (63, 64, 65, 1023, 1024, 1025, 1) for _ in range(40)], 9), 7)]
 
 
 def _check(L, g, seed):
@@ -54,14 +58,14 @@ def _check(L, g, seed):
 
 
 @pytest.mark.parametrize("profile", [False, True], ids=["graph", "stream"])
-@pytest.mark.parametrize("setting", SETTINGS, ids=lambda s: f"r{s[0]}_c{s[1]}_s{s[2]}_v{s[3]}")
+@pytest.mark.parametrize("setting", SETTINGS, ids=lambda s: f"r{s[0]}_c{s[1]}_s{s[2]}_v{s[3]}_b{s[4]}")
 def test_parity_under_every_setting(profile, setting):
     import paper_1302_4587_gb300 as lm
     L = Lm(profile=profile)
     try:
         lm.lm_set_tuning(L.ctx, *setting)
         got = lm.lm_get_tuning(L.ctx)
-        assert (got["rmax"], got["chunk"], got["sweep_ctas_per_sm"], got["vertex_ctas_per_sm"]) == setting
+        assert (got["rmax"], got["chunk"], got["sweep_ctas_per_sm"], got["vertex_ctas_per_sm"], got["batch"]) == setting
         for g, seed in _graphs():
             _check(L, g, seed)
     finally:
@@ -73,11 +77,12 @@ def test_out_of_range_settings_are_rejected():
     L = Lm()
     try:
         for bad in [(0, 4096, 0, 4), (64, 1000, 0, 4), (64, 128, 0, 4), (64, 1 << 21, 0, 4),
-                    (64, 4096, 17, 4), (64, 4096, 0, 5), ((1 << 20) + 1, 4096, 0, 4)]:
+                    (64, 4096, 17, 4), (64, 4096, 0, 5), ((1 << 20) + 1, 4096, 0, 4),
+                    (64, 4096, 0, 4, 32), (64, 4096, 0, 4, 1000), (64, 4096, 0, 4, 1 << 21)]:
             with pytest.raises(lm.LmError) as ei:
                 lm.lm_set_tuning(L.ctx, *bad)
             assert ei.value.code == lm.LM_EINVAL
-        assert lm.lm_get_tuning(L.ctx)["rmax"] == 2048  # unchanged
+        assert lm.lm_get_tuning(L.ctx)["rmax"] == 1024  # unchanged
     finally:
         L.close()
 
@@ -92,7 +97,8 @@ def test_autotune_keeps_a_candidate_and_results_stay_exact():
         hs = [L.graph(g) for g in gs]
         mates = [torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")[:g.n] for g in gs]
         best = lm.lm_autotune(L.ctx, hs, seeds, mates)
-        assert (best["rmax"], best["chunk"]) in [(64, 1024), (256, 2048), (2048, 4096), (8192, 16384)]
+        assert (best["rmax"], best["chunk"], best["batch"]) in [(256, 1024, 256), (512, 1024, 256), (1024, 1024, 512),
+                                                                (2048, 4096, 1024)]
         assert best["sweep_ctas_per_sm"] in (0, 3) and best["ms"] > 0
         now = lm.lm_get_tuning(L.ctx)
         assert (now["rmax"], now["chunk"], now["sweep_ctas_per_sm"]) == (best["rmax"], best["chunk"],
