@@ -251,10 +251,10 @@ def run_lm(args, ws, rank, local):
     achieved = bytes_sweep / (sw_ms * 1e-3) / 1e9 if sw_ms > 0 else 0.0
     cand_achieved = bytes_cand / (cd_ms * 1e-3) / 1e9 if cd_ms > 0 else 0.0
     names = {lm.LM_K_INIT: "k_init", lm.LM_K_SWEEP: "k_sweep", lm.LM_K_VERTEX: "k_vertex",
-             lm.LM_K_CAND: "k_round0", lm.LM_K_OTHER: "other (k_round0_cut, k_loop_check)"}
+             lm.LM_K_CAND: "k_round0", lm.LM_K_OTHER: "other (k_round0_cut, k_loop_check)", lm.LM_K_TAIL: "k_tail"}
     if edge:
         names = {lm.LM_K_INIT: "k_init", lm.LM_K_SWEEP: "k_ec_compact", lm.LM_K_VERTEX: "k_ec_match",
-                 lm.LM_K_CAND: "k_ec_offer", lm.LM_K_OTHER: "k_ec_close"}
+                 lm.LM_K_CAND: "k_ec_offer", lm.LM_K_OTHER: "k_ec_close", lm.LM_K_TAIL: "(none)"}
     kernels = {names[k]: {"ms_per_match": med[k], "launches_per_match": pst["kernel_launches"][k]}
                for k in range(lm.LM_K_COUNT)}
     bytes_ec = edge_model_bytes(pst, g.m) if edge else 0

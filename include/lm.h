@@ -68,6 +68,13 @@ extern "C" {
                                 the seed); round 0 is the default order.  The result can differ from
                                 the default's when weights tie.  Not with LM_F_EDGE_CENTRIC, and
                                 lm_submit refuses it (LM_EINVAL) */
+#define LM_F_ASYNC     8u   /* lm_match returns once the match is queued on the context's stream
+                                instead of after it completes: mate must be device memory and stats
+                                NULL (else LM_EINVAL), and the result is ready when the stream reaches
+                                that point (lm_sync, or any later work on the stream).  Device-side
+                                errors of queued matches are reported by lm_sync.  Not with
+                                LM_F_PROFILE or LM_F_EDGE_CENTRIC; lm_batch_match, lm_submit and
+                                lm_autotune stay synchronous */
 
 typedef struct lm_ctx lm_ctx;
 typedef struct lm_graph lm_graph;
@@ -87,7 +94,8 @@ typedef struct {
 #define LM_K_VERTEX  2   /* k_vertex: mutual-choice match over live rows + task lists */
 #define LM_K_CAND    3   /* k_round0: round-0 candidates over the input arrays in tiles */
 #define LM_K_OTHER   4   /* cut rows of round 0, loop checks, result conversion, batch set-up */
-#define LM_K_COUNT   5
+#define LM_K_TAIL    5   /* k_tail: the last rounds (few live entries) in one CTA, no launch per round */
+#define LM_K_COUNT   6
 
 typedef struct {
     uint32_t rounds;                        /* local-max iterations performed */
@@ -239,6 +247,11 @@ int  lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const ui
 #define LM_NOALLOC_SCRATCH_BYTES (9ull * LM_NOALLOC_MAX_N + 8ull * LM_NOALLOC_MAX_M)
 int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
                             uint64_t seed, uint32_t* mate, uint32_t* status, void* stream);
+
+/* Wait for every match queued on the context (LM_F_ASYNC) and report the first
+ * device-side error any of them met since the previous lm_sync (LM_ECUDA for a
+ * failed index check, LM_ETIMEOUT for a bounded wait that gave up), else LM_OK. */
+int  lm_sync(lm_ctx* ctx);
 
 /* Static description of an error code. */
 const char* lm_strerror(int code);

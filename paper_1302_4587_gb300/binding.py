@@ -21,13 +21,14 @@ LM_HOST, LM_DEVICE = 0, 1
 LM_F_PROFILE = 1
 LM_F_EDGE_CENTRIC = 2
 LM_F_RENEW = 4
+LM_F_ASYNC = 8
 LM_STATS_ROUNDS = 64
-LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_COUNT = range(6)
+LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_TAIL, LM_K_COUNT = range(7)
 
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
            "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error",
-           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune")
+           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune", "lm_sync")
 LM_NOALLOC_MAX_N, LM_NOALLOC_MAX_M = 65536, 262144
 
 
@@ -95,6 +96,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.lm_submit.argtypes = [vp, vp, u64, vp, ctypes.POINTER(u64)]
         lib.lm_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(LmStats)]
         lib.lm_wait.argtypes = [vp, u64, u32]
+        lib.lm_sync.argtypes = [vp]
         lib.lm_strerror.argtypes = [ctypes.c_int]
         lib.lm_strerror.restype = ctypes.c_char_p
         lib.lm_last_error.argtypes = [vp]
@@ -213,7 +215,7 @@ def lm_match(ctx, g, seed: int, mate=None, stats: bool = False):
         mate = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{dev}")[:n]
     p, keep, _ = _ptr(mate)
     st = LmStats()
-    _check(lib.lm_match(ctx, g, seed & (2**64 - 1), p, ctypes.byref(st)), ctx)
+    _check(lib.lm_match(ctx, g, seed & (2**64 - 1), p, ctypes.byref(st) if stats else None), ctx)
     return (keep, st.to_dict()) if stats else keep
 
 
@@ -269,6 +271,12 @@ def lm_wait(ctx, ticket: int, timeout_ms: int) -> bool:
         return False
     _check(rc, ctx)
     return True
+
+
+def lm_sync(ctx) -> None:
+    """Wait for the matches queued on an LM_F_ASYNC context; raises LmError for a
+    device-side error any of them met."""
+    _check(load().lm_sync(ctx), ctx)
 
 
 def lm_strerror(code: int) -> str:

@@ -145,6 +145,7 @@ void engine_free(Engine& e) {
     if (e.hargs) cudaFreeHost(e.hargs);
     destroy_job_graph(e.graph);
     destroy_job_graph(e.egraph);
+    if (e.staged) cudaEventDestroy(e.staged);
     cudaGetLastError();
     e = Engine();
 }
@@ -291,9 +292,17 @@ static int check_err(lm_ctx* ctx, Engine& e) {
 // conditional node that repeats while the device has not flagged the edge set
 // empty.  With profiling the same launches are issued one by one on the
 // stream, with events around each, and the host polls between rounds.
+int staging_ready(lm_ctx* ctx, Engine& e) {
+    if (!e.staged_pending) return LM_OK;
+    LM_CK(ctx, cudaEventSynchronize(e.staged));
+    e.staged_pending = false;
+    return LM_OK;
+}
+
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     Workspace& w = e.ws;
     cudaStream_t s = e.stream;
+    if (int rc = staging_ready(ctx, e)) return rc;
     static_assert(sizeof(JobArgs) <= ARG_AREA, "argument area too small");
     JobArgs& A = *reinterpret_cast<JobArgs*>(e.hargs);
     memset(&A, 0, sizeof A);
@@ -362,6 +371,12 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     sargs(A.s[3], 0, 1, false);
     JobArgs* D = reinterpret_cast<JobArgs*>(e.dargs);
     LM_CK(ctx, cudaMemcpyAsync(D, &A, sizeof A, cudaMemcpyHostToDevice, s));
+    if (job.async) {
+        // the next job may rewrite the staging only after these uploads ran
+        if (!e.staged) LM_CK(ctx, cudaEventCreateWithFlags(&e.staged, cudaEventDisableTiming));
+        LM_CK(ctx, cudaEventRecord(e.staged, s));
+        e.staged_pending = true;
+    }
 
     if (job.nseg == 0) {
         prof.begin(LM_K_INIT);
@@ -416,22 +431,32 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
             if (e.st_host->round > job.nedges + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            if (e.st_host->last_ent < TAIL_ENT) {  // as the loop check: the tail finishes the job
+                prof.begin(LM_K_TAIL);
+                LM_CK(ctx, launch_tail(s, D, e.cfg));
+                prof.end();
+                break;
+            }
             const auto waited = std::chrono::steady_clock::now() - t_start;
             if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)LOOP_LIMIT_NS)
                 return fail(ctx, LM_ETIMEOUT, "round loop exceeded its time limit");
         }
     }
+    if (job.async) return LM_OK;  // queued; lm_sync reports device errors
     LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     LM_CK(ctx, cudaStreamSynchronize(s));
     if (job.nseg && !prof.on) {
         // kernels the graph ran: rounds 0 and 1 (tile candidates + cut rows, 2 vertex passes,
-        // 2 sweeps), then per pair of rounds 2 vertex passes + 2 sweeps + 1 check; round 1
-        // leaves DevState::round at 2 and every later vertex pass advances it
-        const uint32_t pairs = (e.st_host->round >= 2) ? (e.st_host->round - 2) / 2 : 0;
+        // 2 sweeps), then per pair of rounds 2 vertex passes + 2 sweeps + 1 check, then the
+        // tail kernel; round 1 leaves DevState::round at 2 and every later vertex pass
+        // advances it (the loop's last round is the one the tail took over at, if it did)
+        const uint32_t last = e.st_host->tail ? e.st_host->tail_round : e.st_host->round;
+        const uint32_t pairs = (last >= 2) ? (last - 2) / 2 : 0;
         prof.launches[LM_K_CAND] += 1;
         prof.launches[LM_K_VERTEX] += 2 + 2 * pairs;
         prof.launches[LM_K_SWEEP] += 2 + 2 * pairs;
         prof.launches[LM_K_OTHER] += 1 + pairs;
+        prof.launches[LM_K_TAIL] += 1;
     }
     return check_err(ctx, e);
 }
@@ -529,9 +554,12 @@ int match_edges(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32
 
 // One graph on engine e, results to mate (device memory when dev_out, else host
 // memory staged through the workspace); the engine's DevState holds its statistics.
-int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof) {
+int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof,
+              bool async) {
     cudaStream_t s = e.stream;
-    int rc = ensure_ws(ctx, e, g->n, g->nent, 1);
+    int rc = staging_ready(ctx, e);
+    if (rc) return rc;
+    rc = ensure_ws(ctx, e, g->n, g->nent, 1);
     if (rc) return rc;
     rc = ensure_pinned(ctx, e, sizeof(SegIn));
     if (rc) return rc;
@@ -545,6 +573,7 @@ int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t
     job.nvlist = g->nrows;
     job.nseg = g->nent > 0 ? 1 : 0;
     job.ntiles = g->ntiles;
+    job.async = async && dev_out && !prof.on;
     if (job.nseg) {
         const SegIn sg = seg_of(g, seed, 0, 0, 0);
         memcpy(e.pinned, &sg, sizeof sg);
@@ -603,6 +632,7 @@ int lm_create(const lm_config* cfg, lm_ctx** out) {
     DevGuard g(cfg->device);
     if (!g.ok) return LM_ECUDA;
     if ((cfg->flags & LM_F_EDGE_CENTRIC) && (cfg->flags & LM_F_RENEW)) return LM_EINVAL;
+    if ((cfg->flags & LM_F_ASYNC) && (cfg->flags & (LM_F_PROFILE | LM_F_EDGE_CENTRIC))) return LM_EINVAL;
     std::unique_ptr<lm_ctx> ctx(new lm_ctx());
     ctx->device = cfg->device;
     ctx->budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (40ull << 30);
@@ -774,14 +804,37 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
     if (stats) memset(stats, 0, sizeof *stats);
     Prof prof(ctx, ctx->eng.stream);
     const bool dev_out = is_device_ptr(mate);
+    const bool async = (ctx->flags & LM_F_ASYNC) != 0;
+    if (async && (!dev_out || stats))
+        return fail(ctx, LM_EINVAL, "an asynchronous match writes device memory and returns no statistics");
     const int rc = (ctx->flags & LM_F_EDGE_CENTRIC) ? match_edges(ctx, ctx->eng, g, seed, mate, dev_out, prof)
-                                                    : match_one(ctx, ctx->eng, g, seed, mate, dev_out, prof);
+                                                    : match_one(ctx, ctx->eng, g, seed, mate, dev_out, prof, async);
     if (rc) return rc;
     if (stats) {
         fill_round_stats(*ctx->eng.st_host, stats);
         prof.fill(stats);
     }
     return LM_OK;
+}
+
+int lm_sync(lm_ctx* ctx) {
+    if (!ctx) return LM_EINVAL;
+    if (ctx->poisoned) return LM_ECUDA;
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DevGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
+    Engine& e = ctx->eng;
+    if (!e.st) return LM_OK;
+    uint32_t* any = &reinterpret_cast<DevState*>(e.st_host)->err_any;
+    LM_CK(ctx, cudaMemcpyAsync(any, &e.st->err_any, sizeof(uint32_t), cudaMemcpyDeviceToHost, e.stream));
+    LM_CK(ctx, cudaStreamSynchronize(e.stream));
+    e.staged_pending = false;
+    const uint32_t bits = *any;
+    if (!bits) return LM_OK;
+    LM_CK(ctx, cudaMemsetAsync(&e.st->err_any, 0, sizeof(uint32_t), e.stream));
+    LM_CK(ctx, cudaStreamSynchronize(e.stream));
+    if (bits & ERR_BOUNDS) return fail(ctx, LM_ECUDA, "a queued match failed a device index check");
+    return fail(ctx, LM_ETIMEOUT, "a queued match gave up a bounded device wait");
 }
 
 int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const uint64_t* seeds,
@@ -828,6 +881,8 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     gvb[count] = vb;
     const size_t b_gvb = (count + 1) * sizeof(uint32_t), b_geb = count * sizeof(uint32_t);
     const size_t b_off = count * sizeof(void*), b_seg = count * sizeof(SegIn), b_dst = count * sizeof(void*);
+    rc = staging_ready(ctx, e);
+    if (rc) return rc;
     rc = ensure_pinned(ctx, e, b_gvb + b_geb + b_off + b_seg + b_dst + 256);
     if (rc) return rc;
     char* pin = static_cast<char*>(e.pinned);

@@ -59,6 +59,8 @@ struct Engine {
     char* dargs = nullptr;           // [ARG_AREA] kernel arguments (device)
     char* hargs = nullptr;           // [ARG_AREA] their pinned staging
     void* graph = nullptr;           // executable job graph (device-driven round loop)
+    cudaEvent_t staged = nullptr;    // recorded after a queued job's uploads from pinned staging
+    bool staged_pending = false;
     void* egraph = nullptr;          // the same for the edge-centric path
     LaunchCfg cfg;                   // launch parameters of the next jobs
     LaunchCfg graph_cfg;             // the ones `graph` was built with
@@ -142,6 +144,7 @@ struct Job {
     uint32_t nvlist = 0;             // ... or, with vlist == NULL, the dense range [0, nvlist)
     uint32_t ntiles = 0;             // round-0 tiles of all graphs
     uint32_t* grounds = nullptr;
+    bool async = false;              // return once queued (LM_F_ASYNC): no final state read
 };
 // Per-kernel CUDA-event timing of one call (LM_F_PROFILE); NULL-safe helpers.
 struct Prof {
@@ -150,14 +153,18 @@ struct Prof {
     bool on;
     int kind[MAX_PROFILE_EVENTS / 2];
     int n = 0;
-    uint32_t launches[LM_K_COUNT] = {0, 0, 0, 0, 0};
+    uint32_t launches[LM_K_COUNT] = {};
     Prof(lm_ctx* c, cudaStream_t st);
     void begin(int k);
     void end();
     void fill(lm_stats* st);
 };
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof);
-int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof);
+int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof,
+              bool async = false);
+// the pinned staging (arguments, tables) is free again: the copies a queued
+// (asynchronous) job made from it have run
+int staging_ready(lm_ctx* ctx, Engine& e);
 
 }  // namespace lm
 

@@ -88,10 +88,13 @@ struct DevState {
     uint32_t live_rows;       // live rows seen by the running vertex pass
     uint32_t round;           // next round of the device-driven loop
     uint32_t max_rounds;      // the device-driven loop stops (ERR_TIMEOUT) beyond this round ...
-    uint32_t pad2;
+    uint32_t err_any;         // ERR_* bits of every job since the host last cleared them
     unsigned long long t0_ns; // ... or LOOP_LIMIT_NS after the job started
     unsigned long long live_ent;   // live entries seen by the running vertex pass
     unsigned long long matched2;   // matched vertices (= 2 |M|)
+    unsigned long long last_ent;   // live entries the last vertex pass saw (its round's)
+    uint32_t tail;            // 1: the remaining rounds run in the one-CTA tail kernel
+    uint32_t tail_round;      // the round the tail kernel took over at
     uint64_t ring_m[64];      // live edges at the start of round r
     uint64_t ring_n[64];      // live vertices at the start of round r
 };
@@ -241,6 +244,12 @@ struct EdgeArgs {
 };
 
 constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
+// once a round starts with fewer live entries than this, the rounds that remain
+// run in one kernel of one CTA (no launch per round)
+#ifndef LM_TAIL_ENT
+#define LM_TAIL_ENT 4096
+#endif
+constexpr unsigned long long TAIL_ENT = LM_TAIL_ENT;
 
 // ---------------------------------------------------------------------------
 // Host-callable launchers (defined in lm_kernels.cu).  All return a
@@ -259,6 +268,8 @@ uint64_t splitmix64_first(uint64_t seed);  // lm_api.cpp
 // (init, round 0, then a conditional loop of rounds until the device's done
 // flag is set); returns a cudaError_t value
 int build_job_graph(const JobArgs* dargs, DevState* st, const struct LaunchCfg& cfg, void** exec_out);
+// the one-CTA tail of a job (profiled path): runs the remaining rounds from rounds 2 / 3's arguments
+int launch_tail(void* stream, const JobArgs* dargs, const struct LaunchCfg& cfg);
 int launch_job_graph(void* exec, void* stream);
 // edge-centric path: the job graph (init, then a conditional loop of rounds) and the
 // per-round launches of the profiled path

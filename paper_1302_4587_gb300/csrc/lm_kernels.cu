@@ -103,8 +103,11 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 }
 // matched bit of vertex u; the bitmap is read-only during a sweep, so it may go
 // through the non-coherent (read-only) cache
+// matched bit of u.  Between kernels the read-only cache path is safe; inside the
+// tail kernel, which sets bits itself, COH reads through L2 (coherent with the atomics)
+template <bool COH = false>
 __device__ __forceinline__ bool is_dead(const VertexArrays& va, uint32_t u) {
-    return (__ldg(&va.dead[u >> 5]) >> (u & 31)) & 1u;
+    return ((COH ? __ldcg(&va.dead[u >> 5]) : __ldg(&va.dead[u >> 5])) >> (u & 31)) & 1u;
 }
 // device-scope fetch-and-add with acquire-release ordering
 __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
@@ -114,6 +117,7 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
 }
 __device__ __forceinline__ void set_err(DevState* st, uint32_t bit, uint32_t info) {
     if ((atomicOr(&st->err, bit) & bit) == 0) st->err_info = info;
+    atomicOr(&st->err_any, bit);  // not reset by the next job's init (asynchronous matches)
 }
 // warp-wide maximum of (key, neighbour); keys are unique among live entries of a row
 __device__ __forceinline__ void warp_kv_max(uint64_t& k, uint32_t& u) {
@@ -169,6 +173,7 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
         if (threadIdx.x == 0) {
             st->err = 0; st->err_info = 0; st->rounds = 0; st->done = 0;
             st->live_rows = 0; st->live_ent = 0; st->matched2 = 0;
+            st->last_ent = ~0ull; st->tail = 0; st->tail_round = 0;
             st->round = 1;
             st->max_rounds = A.max_rounds;
             st->t0_ns = globaltimer_ns();
@@ -201,8 +206,25 @@ __device__ __forceinline__ void block_excl_scan3(uint32_t& a, uint32_t& b, uint3
     c = pc + ic - c;
 }
 
-__global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__ pav) {
-    const VertexArgs& a = *pav;
+// exclusive scan of one counter over the block (x becomes its prefix); returns the total
+__device__ __forceinline__ uint32_t block_excl_scan1(uint32_t& x, uint32_t* tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ix = warp_incl_scan(x, lane);
+    if (lane == 31) tmp[warp] = ix;
+    __syncthreads();
+    uint32_t px = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < VT / 32; w++) {
+        const uint32_t y = tmp[w];
+        if (w < warp) px += y;
+        tot += y;
+    }
+    x = px + ix - x;
+    return tot;
+}
+
+// The vertex pass as CTA `cta` of `ncta` (k_vertex: the grid; the tail kernel: one CTA).
+__device__ __forceinline__ void vertex_pass(const VertexArgs& a, uint32_t cta, uint32_t ncta) {
     __shared__ uint32_t s_tmp[3 * (VT / 32)];
     __shared__ uint32_t s_base[3];  // list bases of the block: R, C, B
     __shared__ unsigned long long s_red[3 * (VT / 32)];
@@ -222,12 +244,12 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
     }
     // only CTAs with rows take part (CTA 0 closes an empty pass): idle CTAs leave
     // before touching the exit counter
-    const uint32_t working = (uint32_t)min((uint64_t)gridDim.x, ((uint64_t)total + VT * VI - 1) / (VT * VI));
+    const uint32_t working = (uint32_t)min((uint64_t)ncta, ((uint64_t)total + VT * VI - 1) / (VT * VI));
     const uint32_t closers = working ? working : 1u;
-    if (blockIdx.x >= closers) return;
+    if (cta >= closers) return;
     unsigned long long my_rows = 0, my_ent = 0, my_match = 0;
 
-    for (uint32_t base = blockIdx.x * (VT * VI); base < total; base += gridDim.x * (VT * VI)) {
+    for (uint32_t base = cta * (VT * VI); base < total; base += ncta * (VT * VI)) {
         uint32_t vv[VI], LL[VI], cls[VI], uu[VI];
         uint32_t cR = 0, cC = 0, eR = 0;  // this thread's R rows, chunks and R entries
         // phase 1: the row's vertex
@@ -335,9 +357,9 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
         }
         // the batches' first rows into B, block-aggregated (the first scan's reads of
         // s_tmp are behind the barrier above)
-        uint32_t nb = __popc(firsts), d1 = 0, d2 = 0;
-        block_excl_scan3(nb, d1, d2, s_tmp, tot);
-        if (tid == 0) s_base[2] = tot[0] ? atomicAdd(&a.out.cnt[2], tot[0]) : 0;
+        uint32_t nb = __popc(firsts);
+        const uint32_t nb_tot = block_excl_scan1(nb, s_tmp);
+        if (tid == 0) s_base[2] = nb_tot ? atomicAdd(&a.out.cnt[2], nb_tot) : 0;
         __syncthreads();
         uint32_t pB = s_base[2] + nb;
         pR = pR0;
@@ -382,6 +404,7 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
                 const unsigned long long ent = *reinterpret_cast<volatile unsigned long long*>(&st->live_ent);
                 if (round < 64) { st->ring_m[round] = ent / 2; st->ring_n[round] = rows; }
                 if (rows == 0 && !st->done) { st->done = 1; st->rounds = round; }
+                st->last_ent = ent;
                 st->live_rows = 0;
                 st->live_ent = 0;
                 if (a.round_from_state) st->round = round + 1;
@@ -392,20 +415,18 @@ __global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__ pav) {
+    vertex_pass(*pav, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------- sweep
-// Tasks: [0, nC) chunks of long rows, then batches of 32 rows of R.
-// Warps take tasks round-robin and never synchronise with each other.
-// two 32-entry groups in flight per warp at six CTAs (48 warps) per SM measured
-// faster than four groups at four CTAs: the sweep is latency-bound
-#ifndef LM_SG
-#define LM_SG 2
-#endif
+// Tasks: [0, nC) chunks of long rows, then the row batches listed in B.
+// Warps take tasks from a counter and never synchronise with each other.
 #ifndef LM_SWEEP_MINB
-#define LM_SWEEP_MINB 6
+#define LM_SWEEP_MINB 6   // CTAs per SM (40 registers a thread)
 #endif
 
 constexpr int ST = 256;        // threads per CTA (8 independent warps)
-constexpr int SG = LM_SG;      // groups of 32 entries a warp keeps in flight
 
 template <bool RENEW>
 struct WarpRows {              // one warp's batch of rows
@@ -454,13 +475,8 @@ __device__ __forceinline__ uint32_t recover_nbr_seg(const SegIn& sg, DevState* s
     return recover_nbr_keys(sg, st, v, K, sg.k0, sg.k1);
 }
 
-// the stored word of entry q (input, or live with a renewed order: ord(w) << 32 |
-// edge id; live otherwise: the key) and its key under (k0, k1)
-template <bool INPUT>
-__device__ __forceinline__ uint64_t entry_word(const SweepArgs& a, uint32_t g, uint32_t q) {
-    if (INPUT) return __ldcs(a.segs[g].pk + q);
-    return __ldcs(a.in_key + q);
-}
+// the key under (k0, k1) of a stored word (input, or live with a renewed order:
+// ord(w) << 32 | edge id; live otherwise: the key itself)
 template <bool INPUT, bool RENEW>
 __device__ __forceinline__ uint64_t word_key(uint32_t k0, uint32_t k1, uint64_t w) {
     if (INPUT || RENEW) return (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, k0, k1);
@@ -479,21 +495,109 @@ __device__ __forceinline__ uint64_t row_word_key(const SweepArgs& a, const WarpR
     if (INPUT) { const SegIn& sg = a.segs[W.rseg[r]]; return word_key<true, false>(sg.k0, sg.k1, w); }
     return w;
 }
-template <bool INPUT>
-__device__ __forceinline__ uint32_t entry_nbr(const SweepArgs& a, uint32_t g, uint32_t q) {
-    if (INPUT) {
-        const SegIn& sg = a.segs[g];
-        return __ldcs(sg.nbr + q) + sg.vbase;
+// ---- pipelined form: entry words and neighbours go through shared memory by
+// cp.async, PD groups of 32 entries in flight per warp (no registers held for
+// them), so a warp keeps loading while it tests, votes and stores.
+#ifndef LM_PIPE_D
+#define LM_PIPE_D 2
+#endif
+constexpr int PD = LM_PIPE_D;    // groups in flight
+constexpr int PS = PD + 1;       // stages: the one being read is never a copy's target
+struct WarpStage {
+    unsigned long long key[PS][32];
+    uint32_t nbr[PS][32];
+};
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(sh_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sh_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// One 32-entry group of a row batch: r = the entry's row in the batch (32: no
+// entry), sl = the group lane where that row starts, uni = one row for the whole
+// group; w = the stored word, u = the neighbour (compaction sweeps).
+template <bool INPUT, bool COMPACT, bool RENEW, bool COH>
+__device__ __forceinline__ void row_group(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t r, uint32_t sl, bool uni,
+                                          uint64_t w, uint32_t u, int lane, uint32_t lt) {
+    const VertexArrays& va = a.va;
+    uint64_t key = 0;
+    if (COMPACT) {
+        bool keep = r != 32;
+        if (keep) {
+            if (u >= va.nvert) { set_err(a.st, ERR_BOUNDS, u); keep = false; }
+            else keep = !is_dead<COH>(va, u);
+        }
+        if (keep) key = row_word_key<INPUT, RENEW>(a, W, r, w);
+    } else if (r != 32) {
+        key = row_word_key<INPUT, RENEW>(a, W, r, w);
     }
-    return __ldcs(a.in_nbr + q);
+    const bool surv = key != 0;
+    const uint32_t ball = __ballot_sync(FULL, surv);
+    if (!ball) return;
+    if (uni) {
+        // the whole group lies in one row: full-warp reductions
+        const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key >> 32));
+        const uint32_t lo = __reduce_max_sync(FULL, ((uint32_t)(key >> 32) == hi) ? (uint32_t)key : 0u);
+        const uint64_t K = ((uint64_t)hi << 32) | lo;
+        if (COMPACT) {
+            uint32_t base = 0;
+            if (surv) base = W.rcnt[r];
+            __syncwarp();
+            if (surv) {
+                const uint32_t pos = W.rstart[r] + base + __popc(ball & lt);
+                a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r], W.rk1[r], key) : key;
+                a.out_nbr[pos] = u;
+            }
+            // keys are distinct: exactly one lane (a survivor) holds the maximum
+            if (key == K) {
+                W.rcnt[r] = base + __popc(ball);
+                if (K > W.rkey[r]) { W.rkey[r] = K; W.ru[r] = u; }
+            }
+        } else if (key == K && K > W.rkey[r]) {
+            W.rkey[r] = K;
+        }
+        __syncwarp();
+        return;
+    }
+    // several rows, each on a run of lanes from sl: segmented shuffle scan
+    uint64_t mx = key;
+    uint32_t mu = u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t o = __shfl_up_sync(FULL, mx, d);
+        const uint32_t ou = COMPACT ? __shfl_up_sync(FULL, mu, d) : 0u;
+        if ((uint32_t)lane >= sl + d && o > mx) { mx = o; mu = ou; }
+    }
+    const uint32_t rn = __shfl_down_sync(FULL, r, 1);
+    const bool last = r != 32 && (lane == 31 || rn != r);
+    if (COMPACT) {
+        const uint32_t run = FULL << sl;
+        const uint32_t base = r != 32 ? W.rcnt[r] : 0u;
+        __syncwarp();
+        if (last) W.rcnt[r] = base + __popc(ball & run & lanemask_le());
+        if (surv) {
+            const uint32_t pos = W.rstart[r] + base + __popc(ball & run & lt);
+            a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r], W.rk1[r], key) : key;
+            a.out_nbr[pos] = u;
+        }
+    }
+    if (last && mx > W.rkey[r]) {
+        W.rkey[r] = mx;
+        if (COMPACT) W.ru[r] = mu;
+    }
+    __syncwarp();
 }
 
-// One row batch (its first row is B[b]; it ends before the next row marked as a
-// batch start, after at most 32 rows): the rows walked as one flattened sequence.
-template <bool INPUT, bool COMPACT, bool RENEW>
-__device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint32_t nR, uint32_t nr, int lane) {
+template <bool INPUT, bool COMPACT, bool RENEW, bool COH>
+__device__ void do_rows_p(const SweepArgs& a, WarpRows<RENEW>& W, WarpStage& S, uint32_t b, uint32_t nR, uint32_t nr,
+                          int lane) {
     const VertexArrays& va = a.va;
-    const uint32_t idx = __ldg(a.in.B + b) + lane;
+    const uint32_t idx = (COH ? __ldcg(a.in.B + b) : __ldg(a.in.B + b)) + lane;
     uint2 rv = make_uint2(NIL, 0);
     if (idx < nR) rv = a.in.R[idx];
     // the batch's rows: lane 0's (a batch start) up to the next batch start
@@ -507,7 +611,7 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
         else {
             s0 = va.start[v];
             g = va.gid ? va.gid[v] : 0u;
-            if ((uint64_t)s0 + L > a.ecap || g >= a.nsegs) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; }
+            if ((uint64_t)s0 + L > a.ecap || g >= a.nsegs) { set_err(a.st, ERR_BOUNDS, v); v = NIL; L = 0; s0 = 0; g = 0; }
         }
     }
     W.rkey[lane] = 0;
@@ -526,129 +630,62 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
     const uint32_t F = __shfl_sync(FULL, incl, 31);
     __syncwarp();
     const uint32_t lt = lanemask_lt();
-    // the entries f0 .. f0 + 32 SG - 1 of the flattened batch: row, source index,
-    // neighbour and stored word.  The row of entry g0 + j is the number of rows
-    // starting at or before g0 (a ballot) plus the rows starting inside the group
-    // at positions 1..j (bits of an OR-reduction), minus one; uni[i] says that no
-    // row starts inside group i.
-    auto fetch = [&](uint32_t f0, uint32_t (&r)[SG], uint32_t (&q)[SG], uint32_t (&u)[SG], uint64_t (&key)[SG],
-                     bool (&uni)[SG], uint32_t (&sl)[SG]) {
-#pragma unroll
-        for (int i = 0; i < SG; i++) {
-            const uint32_t g0 = f0 + i * 32, f = g0 + lane;
-            r[i] = 32;
-            q[i] = 0;
-            u[i] = NIL;
-            key[i] = 0;
-            uni[i] = true;
-            if (g0 >= F) continue;  // warp-uniform
-            const uint32_t below = __ballot_sync(FULL, ex <= g0);
-            const uint32_t starts = __reduce_or_sync(FULL, (ex > g0 && ex - g0 < 32u) ? 1u << (ex - g0) : 0u);
-            const uint32_t lim = F - g0;
-            uni[i] = (starts & (lim >= 32u ? FULL : (1u << lim) - 1u)) == 0;
-            const uint32_t rr = __popc(below) - 1 + __popc(starts & (FULL >> (31 - lane)));
-            const uint32_t exr = __shfl_sync(FULL, ex, rr & 31u), ror = __shfl_sync(FULL, ro, rr & 31u);
-            if (f < F) {
-                r[i] = rr;
-                q[i] = ror + (f - exr);
-            }
-            sl[i] = exr > g0 ? exr - g0 : 0u;
+    const uint32_t ng = (F + 31) >> 5;
+    // group k holds flattened entries 32k .. 32k + 31.  The row of entry g0 + j is
+    // the number of rows starting at or before g0 (a ballot) plus the rows starting
+    // inside the group at positions 1..j (bits of an OR-reduction), minus one.
+    auto map = [&](uint32_t g0, uint32_t& r, uint32_t& q, uint32_t& sl, bool& uni) {
+        const uint32_t below = __ballot_sync(FULL, ex <= g0);
+        const uint32_t st = __reduce_or_sync(FULL, (ex > g0 && ex - g0 < 32u) ? 1u << (ex - g0) : 0u);
+        const uint32_t lim = F - g0;
+        uni = (st & (lim >= 32u ? FULL : (1u << lim) - 1u)) == 0;
+        const uint32_t rr = __popc(below) - 1 + __popc(st & (FULL >> (31 - lane)));
+        const uint32_t exr = __shfl_sync(FULL, ex, rr & 31u), ror = __shfl_sync(FULL, ro, rr & 31u);
+        r = 32;
+        q = 0;
+        if (g0 + lane < F) {
+            r = rr;
+            q = ror + (g0 + lane - exr);
         }
-#pragma unroll
-        for (int i = 0; i < SG; i++) {
-            if (r[i] == 32) continue;
-            if (COMPACT) u[i] = entry_nbr<INPUT>(a, W.rseg[r[i]], q[i]);
-            key[i] = entry_word<INPUT>(a, W.rseg[r[i]], q[i]);
-        }
+        sl = exr > g0 ? exr - g0 : 0u;
     };
-    uint32_t r[SG], q[SG], u[SG], sl[SG];  // sl: the group lane where the entry's row starts
-    uint64_t key[SG];
-    bool uni[SG];
-    fetch(0, r, q, u, key, uni, sl);
-    for (uint32_t f0 = 0; f0 < F; f0 += 32 * SG) {
-        if (COMPACT) {
-            bool keep[SG];
-#pragma unroll
-            for (int i = 0; i < SG; i++) {
-                keep[i] = r[i] != 32;
-                if (keep[i]) {
-                    if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-                    else keep[i] = !is_dead(va, u[i]);
+    auto issue = [&](uint32_t k) {
+        if (k < ng) {
+            uint32_t r, q, sl;
+            bool uni;
+            map(k * 32, r, q, sl, uni);
+            if (r != 32) {
+                const uint32_t stg = k % PS;
+                if (INPUT) {
+                    const SegIn& sg = a.segs[W.rseg[r]];
+                    cp_async8(&S.key[stg][lane], sg.pk + q);
+                    if (COMPACT) cp_async4(&S.nbr[stg][lane], sg.nbr + q);
+                } else {
+                    cp_async8(&S.key[stg][lane], a.in_key + q);
+                    if (COMPACT) cp_async4(&S.nbr[stg][lane], a.in_nbr + q);
                 }
             }
-#pragma unroll
-            for (int i = 0; i < SG; i++) key[i] = keep[i] ? row_word_key<INPUT, RENEW>(a, W, r[i], key[i]) : 0ull;
-        } else {
-#pragma unroll
-            for (int i = 0; i < SG; i++)
-                if (r[i] != 32) key[i] = row_word_key<INPUT, RENEW>(a, W, r[i], key[i]);
         }
-        // per row: compaction slots and maximum, aggregated over the lanes of a row
+        cp_async_commit();
+    };
 #pragma unroll
-        for (int i = 0; i < SG; i++) {
-            const bool surv = key[i] != 0;
-            if (uni[i]) {
-                // the whole group lies in one row: full-warp vote and reductions
-                const uint32_t ball = __ballot_sync(FULL, surv);
-                if (ball) {
-                    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i] >> 32));
-                    const uint32_t lo =
-                        __reduce_max_sync(FULL, ((uint32_t)(key[i] >> 32) == hi) ? (uint32_t)key[i] : 0u);
-                    const uint64_t K = ((uint64_t)hi << 32) | lo;
-                    if (COMPACT) {
-                        uint32_t base = 0;
-                        if (surv) base = W.rcnt[r[i]];
-                        __syncwarp();
-                        if (surv) {
-                            const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & lt);
-                            a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
-                            a.out_nbr[pos] = u[i];
-                        }
-                        // keys are distinct: exactly one lane (a survivor) holds the maximum
-                        if (key[i] == K) {
-                            W.rcnt[r[i]] = base + __popc(ball);
-                            if (K > W.rkey[r[i]]) { W.rkey[r[i]] = K; W.ru[r[i]] = u[i]; }
-                        }
-                    } else if (key[i] == K && K > W.rkey[r[i]]) {
-                        W.rkey[r[i]] = K;
-                    }
-                    __syncwarp();
-                }
-                continue;
-            }
-            // several rows in the group, each on a contiguous run of lanes from sl[i]:
-            // maxima by a segmented shuffle scan (the run's last lane holds its row's),
-            // slots from one vote; one lane per row updates the row's counters
-            uint64_t mx = key[i];
-            uint32_t mu = u[i];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint64_t o = __shfl_up_sync(FULL, mx, d);
-                const uint32_t ou = COMPACT ? __shfl_up_sync(FULL, mu, d) : 0u;
-                if ((uint32_t)lane >= sl[i] + d && o > mx) { mx = o; mu = ou; }
-            }
-            const uint32_t rn = __shfl_down_sync(FULL, r[i], 1);
-            const bool last = r[i] != 32 && (lane == 31 || rn != r[i]);
-            if (COMPACT) {
-                const uint32_t run = FULL << sl[i];
-                const uint32_t ball = __ballot_sync(FULL, surv);
-                const uint32_t base = r[i] != 32 ? W.rcnt[r[i]] : 0u;
-                __syncwarp();
-                if (last) W.rcnt[r[i]] = base + __popc(ball & run & lanemask_le());
-                if (surv) {
-                    const uint32_t pos = W.rstart[r[i]] + base + __popc(ball & run & lt);
-                    a.out_key[pos] = RENEW ? stored_word<RENEW>(W.rk0[r[i]], W.rk1[r[i]], key[i]) : key[i];
-                    a.out_nbr[pos] = u[i];
-                }
-            }
-            if (last && mx > W.rkey[r[i]]) {
-                W.rkey[r[i]] = mx;
-                if (COMPACT) W.ru[r[i]] = mu;
-            }
-            __syncwarp();
+    for (int d = 0; d < PD; d++) issue(d);
+    for (uint32_t k = 0; k < ng; k++) {
+        cp_async_wait<PD - 1>();
+        uint32_t r, q, sl;
+        bool uni;
+        map(k * 32, r, q, sl, uni);
+        uint64_t w = 0;
+        uint32_t u = NIL;
+        if (r != 32) {
+            const uint32_t stg = k % PS;
+            w = S.key[stg][lane];
+            if (COMPACT) u = S.nbr[stg][lane] + (INPUT ? a.segs[W.rseg[r]].vbase : 0u);
         }
-        if (f0 + 32 * SG < F) fetch(f0 + 32 * SG, r, q, u, key, uni, sl);
+        issue(k + PD);
+        row_group<INPUT, COMPACT, RENEW, COH>(a, W, r, sl, uni, w, u, lane, lt);
     }
+    cp_async_wait<0>();
     __syncwarp();
     if (v != NIL) {
         if (COMPACT) va.len[a.par ^ 1u][v] = W.rcnt[lane];
@@ -662,9 +699,9 @@ __device__ void do_rows(const SweepArgs& a, WarpRows<RENEW>& W, uint32_t b, uint
     __syncwarp();
 }
 
-// One chunk of a long row (all lanes on the same row).
-template <bool INPUT, bool COMPACT, bool RENEW>
-__device__ void do_chunk(const SweepArgs& a, uint32_t t, uint32_t nr, int lane) {
+// One chunk of a long row, pipelined like the row batches.
+template <bool INPUT, bool COMPACT, bool RENEW, bool COH>
+__device__ void do_chunk_p(const SweepArgs& a, WarpStage& S, uint32_t t, uint32_t nr, int lane) {
     const VertexArrays& va = a.va;
     const uint2 c = a.in.C[t];
     const uint32_t v = c.x;
@@ -674,71 +711,66 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, uint32_t nr, int lane) 
     const uint32_t s0 = va.start[v];
     const uint32_t g = va.gid ? va.gid[v] : 0u;
     if (jb >= L || (uint64_t)s0 + L > a.ecap || g >= a.nsegs) { if (lane == 0) set_err(a.st, ERR_BOUNDS, t); return; }
-    const uint32_t off = INPUT ? s0 - a.segs[g].ebase : s0;
-    // renewed order: this round's keys, held for the chunk; default order: the graph's
-    // keys, read where they are needed (two registers fewer across the loop)
+    const SegIn& sg = a.segs[g];
+    const uint32_t off = INPUT ? s0 - sg.ebase : s0;
+    const uint32_t vb = INPUT ? sg.vbase : 0u;
     uint32_t ck0 = 0, ck1 = 0;
     if (RENEW) round_keys<true>(a, g, nr, ck0, ck1);
-    auto chunk_key = [&](uint64_t w) -> uint64_t {
-        if (RENEW) return word_key<INPUT, true>(ck0, ck1, w);
-        if (INPUT) { const SegIn& sg = a.segs[g]; return word_key<true, false>(sg.k0, sg.k1, w); }
-        return w;
-    };
+    else if (INPUT) { ck0 = sg.k0; ck1 = sg.k1; }
     uint32_t* len_next = va.len[a.par ^ 1u];
     uint64_t bk = 0;
     const uint32_t lt = lanemask_lt();
-    for (uint32_t j = jb; j < je; j += 32 * SG) {
-        uint32_t u[SG];
-        uint64_t key[SG];
-#pragma unroll
-        for (int i = 0; i < SG; i++) {
-            const uint32_t jj = j + i * 32 + lane;
-            u[i] = NIL;
-            key[i] = 0;
-            if (jj < je) {
-                if (COMPACT) u[i] = entry_nbr<INPUT>(a, g, off + jj);
-                key[i] = entry_word<INPUT>(a, g, off + jj);
+    const uint32_t ng = (je - jb + 31) >> 5;
+    auto issue = [&](uint32_t k) {
+        const uint32_t jj = jb + k * 32 + lane;
+        if (k < ng && jj < je) {
+            const uint32_t stg = k % PS;
+            if (INPUT) {
+                cp_async8(&S.key[stg][lane], sg.pk + off + jj);
+                if (COMPACT) cp_async4(&S.nbr[stg][lane], sg.nbr + off + jj);
+            } else {
+                cp_async8(&S.key[stg][lane], a.in_key + off + jj);
+                if (COMPACT) cp_async4(&S.nbr[stg][lane], a.in_nbr + off + jj);
             }
         }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < PD; d++) issue(d);
+    for (uint32_t k = 0; k < ng; k++) {
+        cp_async_wait<PD - 1>();
+        const uint32_t jj = jb + k * 32 + lane, stg = k % PS;
+        uint64_t key = 0;
+        uint32_t u = NIL;
+        if (jj < je) {
+            key = S.key[stg][lane];
+            if (COMPACT) u = S.nbr[stg][lane] + vb;
+        }
+        issue(k + PD);
         if (COMPACT) {
-            bool keep[SG];
-#pragma unroll
-            for (int i = 0; i < SG; i++) {
-                keep[i] = u[i] != NIL;
-                if (keep[i]) {
-                    if (u[i] >= va.nvert) { set_err(a.st, ERR_BOUNDS, u[i]); keep[i] = false; }
-                    else keep[i] = !is_dead(va, u[i]);
-                }
+            bool keep = jj < je;
+            if (keep) {
+                if (u >= va.nvert) { set_err(a.st, ERR_BOUNDS, u); keep = false; }
+                else keep = !is_dead<COH>(va, u);
             }
-#pragma unroll
-            for (int i = 0; i < SG; i++) key[i] = keep[i] ? chunk_key(key[i]) : 0ull;
-        } else {
-#pragma unroll
-            for (int i = 0; i < SG; i++)
-                if (j + i * 32 + lane < je) key[i] = chunk_key(key[i]);
+            key = keep ? word_key<INPUT, RENEW>(ck0, ck1, key) : 0ull;
+        } else if (jj < je) {
+            key = word_key<INPUT, RENEW>(ck0, ck1, key);
         }
-        uint32_t ball[SG], sub = 0;
-#pragma unroll
-        for (int i = 0; i < SG; i++) {
-            ball[i] = __ballot_sync(FULL, key[i] != 0);
-            sub += __popc(ball[i]);
-            if (key[i] > bk) bk = key[i];
-        }
-        if (COMPACT && sub) {
+        const uint32_t ball = __ballot_sync(FULL, key != 0);
+        if (key > bk) bk = key;
+        if (COMPACT && ball) {
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&len_next[v], sub);
+            if (lane == 0) base = atomicAdd(&len_next[v], (uint32_t)__popc(ball));
             base = __shfl_sync(FULL, base, 0);
-#pragma unroll
-            for (int i = 0; i < SG; i++) {
-                if (key[i] != 0) {
-                    const uint32_t pos = s0 + base + __popc(ball[i] & lt);
-                    a.out_key[pos] = stored_word<RENEW>(ck0, ck1, key[i]);
-                    a.out_nbr[pos] = u[i];
-                }
-                base += __popc(ball[i]);
+            if (key != 0) {
+                const uint32_t pos = s0 + base + __popc(ball & lt);
+                a.out_key[pos] = stored_word<RENEW>(ck0, ck1, key);
+                a.out_nbr[pos] = u;
             }
         }
     }
+    cp_async_wait<0>();
     // chunk maximum into the row's slot; the last chunk of the row to finish
     // reads the row maximum and recovers its neighbour
     const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(bk >> 32));
@@ -754,24 +786,25 @@ __device__ void do_chunk(const SweepArgs& a, uint32_t t, uint32_t nr, int lane) 
             const uint64_t R = *reinterpret_cast<volatile unsigned long long*>(&va.bkey[v]);
             va.bkey[v] = 0;
             va.bcnt[v] = 0;
-            if (R) va.cnbr[v] = RENEW ? recover_nbr_keys(a.segs[g], a.st, v, R, ck0, ck1) : recover_nbr_seg(a.segs[g], a.st, v, R);
+            if (R) va.cnbr[v] = RENEW ? recover_nbr_keys(sg, a.st, v, R, ck0, ck1) : recover_nbr_seg(sg, a.st, v, R);
         }
     }
 }
 
-template <bool INPUT, bool COMPACT, bool RENEW>
-__global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __restrict__ pav) {
-    __shared__ WarpRows<RENEW> s_rows[ST / 32];
-    const SweepArgs& a = *pav;
+
+// The sweep as CTA `cta` of `ncta` (k_sweep: the grid; the tail kernel: one CTA);
+// W and S are the calling warp's shared row state and copy stages.
+template <bool INPUT, bool COMPACT, bool RENEW, bool COH>
+__device__ __forceinline__ void sweep_pass(const SweepArgs& a, WarpRows<RENEW>& W, WarpStage& S, uint32_t cta,
+                                           uint32_t ncta) {
     const int lane = threadIdx.x & 31;
-    WarpRows<RENEW>& W = s_rows[threadIdx.x >> 5];
-    const uint32_t gw = (blockIdx.x * ST + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * ST) >> 5;
+    const uint32_t gw = (cta * ST + threadIdx.x) >> 5;
+    const uint32_t nw = (ncta * ST) >> 5;
     const uint32_t nR = ld_volatile_u32(&a.in.cnt[0]);
     const uint32_t nC = ld_volatile_u32(&a.in.cnt[1]);
     const uint32_t nB = ld_volatile_u32(&a.in.cnt[2]);
     if (nR > a.in.capR || nC > a.in.capC || nB > nR) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a.st, ERR_BOUNDS, nC);
+        if (cta == 0 && threadIdx.x == 0) set_err(a.st, ERR_BOUNDS, nC);
         return;
     }
     const uint32_t total = nC + nB;
@@ -785,9 +818,24 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
     for (;; t = __shfl_sync(FULL, t_next, 0)) {
         if (t >= total) break;
         if (lane == 0) t_next = nw + atomicAdd(a.task_ctr, 1u);
-        if (t < nC) do_chunk<INPUT, COMPACT, RENEW>(a, t, nr, lane);
-        else do_rows<INPUT, COMPACT, RENEW>(a, W, t - nC, nR, nr, lane);
+        if (t < nC) do_chunk_p<INPUT, COMPACT, RENEW, COH>(a, S, t, nr, lane);
+        else do_rows_p<INPUT, COMPACT, RENEW, COH>(a, W, S, t - nC, nR, nr, lane);
     }
+}
+
+template <bool INPUT, bool COMPACT, bool RENEW>
+__global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __restrict__ pav) {
+    __shared__ WarpRows<RENEW> s_rows[ST / 32];
+    __shared__ WarpStage s_stage[ST / 32];
+    // the arguments in shared memory: the many re-reads of their pointers and sizes
+    // are shared-memory loads instead of global-memory ones
+    __shared__ __align__(16) unsigned char s_args_raw[sizeof(SweepArgs)];
+    static_assert(sizeof(SweepArgs) % 4 == 0, "word copy");
+    for (uint32_t i = threadIdx.x; i < sizeof(SweepArgs) / 4; i += ST)
+        reinterpret_cast<uint32_t*>(s_args_raw)[i] = reinterpret_cast<const uint32_t*>(pav)[i];
+    __syncthreads();
+    sweep_pass<INPUT, COMPACT, RENEW, false>(*reinterpret_cast<const SweepArgs*>(s_args_raw), s_rows[threadIdx.x >> 5],
+                                      s_stage[threadIdx.x >> 5], blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- round-0 candidates in TMA-fed tiles
@@ -1137,6 +1185,22 @@ __device__ __forceinline__ void warp_max_at(unsigned long long* best, uint32_t x
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&best[x], ((unsigned long long)hi << 32) | lo);
 }
 
+// sum of x over the block, added to *dst by one thread (every thread calls it):
+// one atomic per block instead of one per warp on a single hot counter
+template <class T>
+__device__ __forceinline__ void block_add(T* dst, T x, T* s_part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if (lane == 0) s_part[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_part[w];
+        if (t) atomicAdd(dst, t);
+    }
+}
+
 __global__ void __launch_bounds__(EC_T) k_ec_offer(const EdgeArgs* __restrict__ pa) {
     const EdgeArgs& a = *pa;
     const uint32_t r = ec_round(a);
@@ -1168,8 +1232,8 @@ __global__ void __launch_bounds__(EC_T) k_ec_offer(const EdgeArgs* __restrict__ 
             fresh += atomicExch(&a.stamp[v], r + 1u) != r + 1u;
         }
     }
-    fresh = __reduce_add_sync(FULL, fresh);
-    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(&a.st->live_rows, fresh);
+    __shared__ uint32_t s_part[EC_T / 32];
+    block_add(&a.st->live_rows, fresh, s_part);
 }
 
 __global__ void __launch_bounds__(EC_T) k_ec_match(const EdgeArgs* __restrict__ pa) {
@@ -1193,40 +1257,67 @@ __global__ void __launch_bounds__(EC_T) k_ec_match(const EdgeArgs* __restrict__ 
             matched += 2;
         }
     }
-    if (matched) atomicAdd(&a.st->matched2, matched);
+    __shared__ unsigned long long s_part[EC_T / 32];
+    block_add(&a.st->matched2, matched, s_part);
 }
 
+constexpr int EC_V = 4;  // edges per thread per step of the compaction
 __global__ void __launch_bounds__(EC_T) k_ec_compact(const EdgeArgs* __restrict__ pa) {
     const EdgeArgs& a = *pa;
+    __shared__ uint32_t s_cnt[EC_T / 32];
+    __shared__ uint32_t s_base;
     const uint32_t r = ec_round(a);
     const uint32_t cnt = r == 0 ? a.m : ld_volatile_u32(&a.st->lcnt[0][r & 1u]);
     const uint32_t* L = a.live[r & 1u];
     uint32_t* N = a.live[(r + 1) & 1u];
     uint32_t* ncnt = &a.st->lcnt[0][(r + 1) & 1u];
-    const uint32_t stride = gridDim.x * blockDim.x, cr = (cnt + 31) & ~31u, lane = threadIdx.x & 31;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cr; i += stride) {
-        bool keep = false;
-        uint32_t e = 0;
-        if (i < cnt) {
-            e = r == 0 ? i : L[i];
-            if (e < a.m) {
-                const uint64_t rec = a.edges[e];
-                const uint32_t u = (uint32_t)rec, v = (uint32_t)(rec >> 32);
-                a.best[u] = 0;  // offers and stamps go back to zero for the next round
-                a.best[v] = 0;
-                a.stamp[u] = 0;
-                a.stamp[v] = 0;
-                keep = !(((__ldg(&a.dead[u >> 5]) >> (u & 31)) | (__ldg(&a.dead[v >> 5]) >> (v & 31))) & 1u);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = lanemask_lt();
+    const uint32_t step = EC_T * EC_V;
+    // block-uniform loop: each step keeps the survivors of EC_T * EC_V edges with one
+    // atomic for the whole block (slots: warp prefix + vote)
+    for (uint32_t b0 = blockIdx.x * step; b0 < cnt; b0 += gridDim.x * step) {
+        bool keep[EC_V];
+        uint32_t ee[EC_V], ball[EC_V], mine = 0;
+#pragma unroll
+        for (int k = 0; k < EC_V; k++) {
+            const uint32_t i = b0 + k * EC_T + threadIdx.x;
+            keep[k] = false;
+            ee[k] = 0;
+            if (i < cnt) {
+                const uint32_t e = r == 0 ? i : L[i];
+                ee[k] = e;
+                if (e < a.m) {
+                    const uint64_t rec = a.edges[e];
+                    const uint32_t u = (uint32_t)rec, v = (uint32_t)(rec >> 32);
+                    a.best[u] = 0;  // offers and stamps go back to zero for the next round
+                    a.best[v] = 0;
+                    a.stamp[u] = 0;
+                    a.stamp[v] = 0;
+                    keep[k] = !(((__ldg(&a.dead[u >> 5]) >> (u & 31)) | (__ldg(&a.dead[v >> 5]) >> (v & 31))) & 1u);
+                }
             }
+            ball[k] = __ballot_sync(FULL, keep[k]);
+            mine += __popc(ball[k]);
         }
-        const uint32_t ball = __ballot_sync(FULL, keep);
-        uint32_t base = 0;
-        if (lane == 0 && ball) base = atomicAdd(ncnt, (uint32_t)__popc(ball));
-        base = __shfl_sync(FULL, base, 0) + __popc(ball & lanemask_lt());
-        if (keep) {
-            if (base < a.cap) N[base] = e;
-            else set_err(a.st, ERR_BOUNDS, base);
+        if (lane == 0) s_cnt[warp] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < EC_T / 32; w++) { const uint32_t c = s_cnt[w]; s_cnt[w] = t; t += c; }
+            s_base = t ? atomicAdd(ncnt, t) : 0u;
         }
+        __syncthreads();
+        uint32_t base = s_base + s_cnt[warp];
+#pragma unroll
+        for (int k = 0; k < EC_V; k++) {
+            if (keep[k]) {
+                const uint32_t pos = base + __popc(ball[k] & lt);
+                if (pos < a.cap) N[pos] = ee[k];
+                else set_err(a.st, ERR_BOUNDS, pos);
+            }
+            base += __popc(ball[k]);
+        }
+        __syncthreads();  // s_cnt / s_base reuse
     }
 }
 
@@ -1707,8 +1798,62 @@ __global__ void k_loop_check(DevState* st, cudaGraphConditionalHandle h) {
              globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
         set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
         go = 0;
+    } else if (*reinterpret_cast<volatile unsigned long long*>(&st->last_ent) < TAIL_ENT) {
+        // few entries left: the tail kernel after the loop finishes the job
+        st->tail = 1;
+        st->tail_round = ld_volatile_u32(&st->round);
+        go = 0;
     }
     cudaGraphSetConditional(h, go);
+}
+
+// The rounds that remain once few entries are live, in one CTA: the vertex pass
+// and the sweep of rounds of both parities (the loop body's arguments) run as
+// phases separated by block barriers, with no launch per round.  force = 1 (the
+// profiled path) takes over unconditionally; otherwise only when the loop check
+// handed over.  The round cap and the time limit hold as in the loop check.
+template <bool RENEW>
+__global__ void __launch_bounds__(ST, 1) k_tail(const JobArgs* __restrict__ A, uint32_t force) {
+    __shared__ WarpRows<RENEW> s_rows[ST / 32];
+    __shared__ WarpStage s_stage[ST / 32];
+    __shared__ uint32_t s_go;
+    DevState* st = A->v[2].st;
+    if (threadIdx.x == 0) {
+        if (force) {
+            st->tail = 1;
+            st->tail_round = ld_volatile_u32(&st->round);
+        }
+        s_go = ld_volatile_u32(&st->tail) && !ld_volatile_u32(&st->done) && !ld_volatile_u32(&st->err);
+    }
+    __syncthreads();
+    if (!s_go) return;
+    WarpRows<RENEW>& W = s_rows[threadIdx.x >> 5];
+    WarpStage& S = s_stage[threadIdx.x >> 5];
+    for (;;) {
+        for (int k = 2; k < 4; k++) {
+            vertex_pass(A->v[k], 0, 1);
+            __syncthreads();
+            sweep_pass<false, true, RENEW, true>(A->s[k], W, S, 0, 1);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_go = 1;
+            if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) s_go = 0;
+            else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
+                     globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+                set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
+                s_go = 0;
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
+    }
+}
+
+int launch_tail(void* stream, const JobArgs* dargs, const LaunchCfg& cfg) {
+    if (cfg.renew) k_tail<true><<<1, ST, 0, (cudaStream_t)stream>>>(dargs, 1u);
+    else k_tail<false><<<1, ST, 0, (cudaStream_t)stream>>>(dargs, 1u);
+    return (int)cudaGetLastError();
 }
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, void* func, dim3 grid,
@@ -1787,6 +1932,13 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const LaunchCfg& cfg, vo
         if (e) break;
         void* cparams[2] = {&st, &h};
         if ((e = add_kernel(body, &bn, bp, (void*)k_loop_check, dim3(1), dim3(32), cparams))) break;
+        // after the loop: the one-CTA tail (returns at once unless the loop check handed over)
+        const JobArgs* pd = dargs;
+        uint32_t no_force = 0;
+        void* tparams[2] = {&pd, &no_force};
+        void* const k_t = rn ? (void*)k_tail<true> : (void*)k_tail<false>;
+        prev = node;
+        if ((e = add_kernel(g, &node, prev, k_t, dim3(1), dim3(ST), tparams))) break;
         cudaGraphExec_t ex = nullptr;
         if ((e = cudaGraphInstantiate(&ex, g, 0))) break;
         *exec_out = ex;
