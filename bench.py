@@ -33,7 +33,7 @@ METRIC = "input edges/s to maximal matching"
 # dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
 # an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
 # capture with several metrics); None for workloads without a capture of the current kernels
-TRAFFIC: dict = {}
+TRAFFIC = {"rmat23": 6032304784}
 
 
 def _peaks():
@@ -151,14 +151,15 @@ def make_workload(name: str):
     raise ValueError(name)
 
 
-def sweep_model_bytes(st: dict) -> int:
+def sweep_model_bytes(st: dict, nsweeps: int | None = None) -> int:
     """Algorithmic HBM bytes of the k_sweep launches of one match (round-0
-    compaction from the input arrays and every later round), from the per-round
-    live counts: a sweep over E_r entries / R_r rows reads 16 B per entry (12 B
-    entry + 4 B neighbour-state gather), writes 12 B per surviving entry, reads
-    8 B per row and writes 12 B per row of the next round."""
+    compaction from the input arrays and every later round up to the one-CTA
+    tail: the sweep of round r is launch r), from the per-round live counts: a
+    sweep over E_r entries / R_r rows reads 16 B per entry (12 B entry + 4 B
+    neighbour-state gather), writes 12 B per surviving entry, reads 8 B per row
+    and writes 12 B per row of the next round."""
     rm, rn = st["round_m"], st["round_n"]
-    R = len(rm)
+    R = len(rm) if nsweeps is None else min(len(rm), nsweeps)
     E = [2 * x for x in rm] + [0]
     N = list(rn) + [0]
     b = 0
@@ -245,7 +246,7 @@ def run_lm(args, ws, rank, local):
     lm.lm_destroy(pctx)
     med = {k: statistics.median(v) for k, v in kms.items()}
     peak, peak_kind = _peaks()
-    bytes_sweep = sweep_model_bytes(pst)
+    bytes_sweep = sweep_model_bytes(pst, pst["kernel_launches"][lm.LM_K_SWEEP])
     bytes_cand = cand_model_bytes(pst)
     sw_ms, cd_ms = med[lm.LM_K_SWEEP], med[lm.LM_K_CAND]
     achieved = bytes_sweep / (sw_ms * 1e-3) / 1e9 if sw_ms > 0 else 0.0
