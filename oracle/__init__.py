@@ -75,6 +75,9 @@ def _lib():
             lib.lmo_seq_local_max_renew.argtypes = lib.lmo_seq_local_max.argtypes
             lib.lmo_brute_mwm.restype = ctypes.c_double
             lib.lmo_brute_mwm.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, f32p]
+            lib.lmo_contract.restype = ctypes.c_int
+            lib.lmo_contract.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, f32p, u32p, u32p,
+                                         u32p, u32p, u32p, u32p, f32p, u32p, u64p]
             _LIB = lib
     return _LIB
 
@@ -167,3 +170,33 @@ def brute_mwm(n: int, eu, ev, w) -> float:
     if r < 0:
         raise ValueError("brute_mwm: n too large or allocation failed")
     return float(r)
+
+
+def contract(n: int, eu, ev, w, mate, vw=None):
+    """Contraction of the matching `mate` (Sec. 1, the multilevel use of
+    maximal matchings): (cmap[n], cvw[n'], ceu[m'], cev[m'], cw[m'])."""
+    eu, up = _u32(eu)
+    ev, vp = _u32(ev)
+    w, wp = _f32(w)
+    mate, mp = _u32(mate)
+    vwp = None
+    if vw is not None:
+        vw, vwp = _u32(vw)
+    m = eu.shape[0]
+    cmap = np.empty(max(n, 1), dtype=np.uint32)
+    cvw = np.empty(max(n, 1), dtype=np.uint32)
+    ceu = np.empty(max(m, 1), dtype=np.uint32)
+    cev = np.empty(max(m, 1), dtype=np.uint32)
+    cw = np.empty(max(m, 1), dtype=np.float32)
+    no = ctypes.c_uint32()
+    mo = ctypes.c_uint64()
+    p = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    r = _lib().lmo_contract(n, m, up, vp, wp, vwp, mp, p(cmap, ctypes.c_uint32), p(cvw, ctypes.c_uint32),
+                            p(ceu, ctypes.c_uint32), p(cev, ctypes.c_uint32), p(cw, ctypes.c_float),
+                            ctypes.byref(no), ctypes.byref(mo))
+    if r == -1:
+        raise MemoryError("oracle contract: allocation failed")
+    if r == -2:
+        raise ValueError("oracle contract: mate is not a matching of the vertex set, or an endpoint is out of range")
+    k, g = int(no.value), int(mo.value)
+    return cmap[:n].copy(), cvw[:k].copy(), ceu[:g].copy(), cev[:g].copy(), cw[:g].copy()

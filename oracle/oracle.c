@@ -27,6 +27,15 @@
  *   lmo_brute_mwm -- maximum weight matching by exhaustive dynamic
  *       programming over vertex subsets (small n only), for the
  *       1/2-approximation property cited in Sec. 1.
+ *   lmo_contract -- contraction of a matching, the step that multilevel
+ *       graph partitioning repeats on maximal matchings (Sec. 1).  Reading
+ *       (the paper names the use, not the operation): a matched pair
+ *       becomes one coarse vertex and an unmatched vertex stays alone;
+ *       coarse ids follow the smaller member's index; a coarse vertex
+ *       weighs the sum of its members; edges inside a pair vanish; the
+ *       original edges between two coarse vertices become one coarse edge,
+ *       oriented and placed as the first of them in the input order, whose
+ *       weight is their sum (taken in double, rounded to float32 once).
  *
  * Floating point: edge weights arrive as float32 (the input format); the
  * order only reinterprets their bits; sums of weights are taken in double.
@@ -258,4 +267,92 @@ double lmo_brute_mwm(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t*
     double r = best[states - 1];
     free(best);
     return r;
+}
+
+
+/* ---- contraction of a matching -------------------------------------- */
+
+typedef struct { uint64_t pair; uint32_t e; } lmo_pe;
+
+static int by_pair_then_edge(const void* a, const void* b) {
+    const lmo_pe* x = (const lmo_pe*)a;
+    const lmo_pe* y = (const lmo_pe*)b;
+    if (x->pair != y->pair) return x->pair < y->pair ? -1 : 1;
+    return x->e < y->e ? -1 : (x->e > y->e);
+}
+
+typedef struct { uint32_t lead, c, d; double sum; } lmo_ce;
+
+static int by_leader(const void* a, const void* b) {
+    const lmo_ce* x = (const lmo_ce*)a;
+    const lmo_ce* y = (const lmo_ce*)b;
+    return x->lead < y->lead ? -1 : (x->lead > y->lead);
+}
+
+/* mate: partner or LMO_NIL per vertex (must be a matching of the graph's
+ * vertex set: mate[mate[v]] == v).  vw: vertex weights, NULL = 1 each.
+ * Outputs: cmap[n] coarse id per vertex, cvw[n'] coarse vertex weights,
+ * ceu / cev / cw [m'] coarse edges; *n_out = n', *m_out = m'.
+ * Returns 0, -1 on allocation failure, -2 on an invalid mate or endpoint. */
+int lmo_contract(uint32_t n, uint64_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
+                 const uint32_t* vw, const uint32_t* mate, uint32_t* cmap, uint32_t* cvw,
+                 uint32_t* ceu, uint32_t* cev, float* cw, uint32_t* n_out, uint64_t* m_out) {
+    for (uint32_t v = 0; v < n; v++) {
+        const uint32_t u = mate[v];
+        if (u == LMO_NIL) continue;
+        if (u >= n || u == v || mate[u] != v) return -2;
+    }
+    for (uint64_t e = 0; e < m; e++)
+        if (eu[e] >= n || ev[e] >= n) return -2;
+    /* coarse ids: representatives (unmatched vertices and the smaller end of
+       each matched pair) numbered in vertex order */
+    uint32_t nc = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        const uint32_t u = mate[v];
+        if (u == LMO_NIL || v < u) cmap[v] = nc++;
+    }
+    for (uint32_t v = 0; v < n; v++) {
+        const uint32_t u = mate[v];
+        if (u != LMO_NIL && u < v) cmap[v] = cmap[u];
+    }
+    for (uint32_t c = 0; c < nc; c++) cvw[c] = 0;
+    for (uint32_t v = 0; v < n; v++) cvw[cmap[v]] += vw ? vw[v] : 1u;
+    /* crossing edges grouped by their unordered coarse pair, in edge order */
+    lmo_pe* pe = (lmo_pe*)malloc((m ? m : 1) * sizeof(lmo_pe));
+    lmo_ce* ce = (lmo_ce*)malloc((m ? m : 1) * sizeof(lmo_ce));
+    if (!pe || !ce) { free(pe); free(ce); return -1; }
+    uint64_t k = 0;
+    for (uint64_t e = 0; e < m; e++) {
+        const uint32_t c = cmap[eu[e]], d = cmap[ev[e]];
+        if (c == d) continue;
+        const uint32_t lo = c < d ? c : d, hi = c < d ? d : c;
+        pe[k].pair = ((uint64_t)lo << 32) | hi;
+        pe[k].e = (uint32_t)e;
+        k++;
+    }
+    qsort(pe, k, sizeof(lmo_pe), by_pair_then_edge);
+    uint64_t g = 0;
+    for (uint64_t i = 0; i < k;) {
+        uint64_t j = i;
+        double sum = 0.0;
+        while (j < k && pe[j].pair == pe[i].pair) { sum += (double)w[pe[j].e]; j++; }
+        const uint32_t lead = pe[i].e;  /* the group's first edge in input order */
+        ce[g].lead = lead;
+        ce[g].c = cmap[eu[lead]];
+        ce[g].d = cmap[ev[lead]];
+        ce[g].sum = sum;
+        g++;
+        i = j;
+    }
+    qsort(ce, g, sizeof(lmo_ce), by_leader);
+    for (uint64_t i = 0; i < g; i++) {
+        ceu[i] = ce[i].c;
+        cev[i] = ce[i].d;
+        cw[i] = (float)ce[i].sum;
+    }
+    *n_out = nc;
+    *m_out = g;
+    free(pe);
+    free(ce);
+    return 0;
 }
