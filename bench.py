@@ -485,6 +485,59 @@ def run_serve(args, ws, rank, local):
     }
 
 
+def run_contract(args, ws, rank, local):
+    """Contraction of the matching (lm_contract) on R-MAT 23: the matching is
+    computed first (untimed); each step contracts it from device-resident edge
+    list, weights and mate.  Metric: input edges/s contracted.  Algorithmic
+    bytes: the edge list read once (12 B per edge), the coarse map written and
+    read (8 B per vertex) and the coarse edges written (12 B each); the
+    pair table's atomics come on top of that."""
+    import torch
+    import paper_1302_4587_gb300 as lm
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g, seed, desc = make_workload("rmat23")
+    ctx = lm.lm_create(local, stream)
+    eu = torch.from_numpy(g.eu.view(np.int32)).to(dev)
+    ev = torch.from_numpy(g.ev.view(np.int32)).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    h = lm.lm_graph_create(ctx, g.n, eu, ev, w)
+    mate = torch.empty(g.n, dtype=torch.int32, device=dev)
+    lm.lm_match(ctx, h, seed, mate)
+    lm.lm_graph_destroy(h)
+    for _ in range(max(args.warmup, 3)):
+        out = lm.lm_contract(ctx, g.n, eu, ev, w, mate)
+    n2, m2 = int(out[1].shape[0]), int(out[2].shape[0])
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            lm.lm_contract(ctx, g.n, eu, ev, w, mate)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    ms = _barrier_max(e0.elapsed_time(e1) / args.steps, ws)
+    peak, peak_kind = _peaks()
+    algo = 12 * g.m + 8 * g.n + 12 * m2
+    ach = algo / (ms * 1e-3) / 1e9
+    lm.lm_destroy(ctx)
+    return {"metric": "input edges/s contracted (matching contraction)", "value": whole_job_value(g.m, ws, ms),
+            "unit": "edges/s", "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 ids / f64 sums",
+            "data": "synthetic",
+            "config": {"workload": "contract", "desc": desc + "; its greedy-equivalent local-max matching contracted",
+                       "n": g.n, "m": g.m, "coarse_n": n2, "coarse_m": m2,
+                       "l2": "inputs larger than L2 (edge list 1.55 GB)"},
+            "roofline": {"bound": "hbm", "kernel": "lm_contract (all its kernels)", "achieved": ach, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                         "bytes_per_step": algo},
+            "clocks": clk.summary(), "gpu_launches": 13 * args.steps}  # 5 kernels + 3 + 5 scan kernels per call
+
+
 def run_paper_sweep(args, ws, rank, local):
     """The shape of the paper's GPU comparison (Sec. 3.3, rgg and random-graph
     figures): for random geometric graphs and random graphs with alpha n edges
@@ -600,7 +653,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
     ap.add_argument("--workload", default="rmat23",
-                    choices=["rmat23", "rmat21", "grid", "er", "rmat23_unit", "batch", "serve", "paper_sweep"])
+                    choices=["rmat23", "rmat21", "grid", "er", "rmat23_unit", "batch", "serve", "paper_sweep",
+                             "contract"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--algo", default="segmented", choices=["segmented", "edge"],
                     help="edge: the edge-centric (Combining CRCW) path, for comparison")
@@ -620,8 +674,9 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    if args.workload in ("batch", "serve", "paper_sweep"):
-        out = {"batch": run_batch, "serve": run_serve, "paper_sweep": run_paper_sweep}[args.workload](args, ws, rank, local)
+    if args.workload in ("batch", "serve", "paper_sweep", "contract"):
+        out = {"batch": run_batch, "serve": run_serve, "paper_sweep": run_paper_sweep,
+               "contract": run_contract}[args.workload](args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         if ws > 1:

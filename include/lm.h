@@ -248,6 +248,33 @@ int  lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const ui
 int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
                             uint64_t seed, uint32_t* mate, uint32_t* status, void* stream);
 
+/* Contraction of a matching: the step multilevel graph partitioning repeats on
+ * maximal matchings (Sec. 1 names it as the matching's main use; the exact
+ * operation is this library's reading).  A matched pair becomes one coarse
+ * vertex and an unmatched vertex stays alone; coarse ids number the
+ * representatives (unmatched vertices and the smaller end of each pair) in
+ * vertex order; a coarse vertex weighs the sum of its members; edges inside a
+ * pair vanish; the original edges between two coarse vertices become one
+ * coarse edge, placed and oriented as the first of them in input order,
+ * weighing their sum (accumulated in double, rounded once to float32: the
+ * result does not depend on the accumulation order whenever that double sum is
+ * exact, e.g. for weights on a common 2^-k grid; otherwise it is within one
+ * float32 rounding of the ordered sum).  The output is itself an edge list in
+ * lm_graph_create's form, so levels chain.
+ *   n, m          vertices and edges; eu, ev, w: device uint32[m], uint32[m], float32[m]
+ *   vw            device uint32[n] vertex weights, or NULL (1 each)
+ *   mate          device uint32[n]: a matching of the vertex set (partner or LM_NIL)
+ *   cmap          device uint32[n] out: coarse id of every vertex
+ *   cvw           device uint32[n] out: coarse vertex weights (the first *n_out)
+ *   ceu, cev, cw  device uint32[m], uint32[m], float32[m] out: coarse edges (the first *m_out)
+ *   n_out, m_out  host out: coarse vertex and edge counts
+ * Runs on the context's stream and returns when the outputs are complete; the
+ * caller owns every array.  Errors: LM_EINVAL (null or host pointer; mate not
+ * a matching of the vertex set; an endpoint >= n), LM_ENOMEM, LM_ECUDA. */
+int  lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
+                 const uint32_t* vw, const uint32_t* mate, uint32_t* cmap, uint32_t* cvw, uint32_t* ceu,
+                 uint32_t* cev, float* cw, uint32_t* n_out, uint32_t* m_out);
+
 /* Wait for every match queued on the context (LM_F_ASYNC) and report the first
  * device-side error any of them met since the previous lm_sync (LM_ECUDA for a
  * failed index check, LM_ETIMEOUT for a bounded wait that gave up), else LM_OK. */

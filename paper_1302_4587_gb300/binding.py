@@ -28,7 +28,7 @@ LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_TAIL, LM_K_COUNT
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
            "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error",
-           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune", "lm_sync")
+           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune", "lm_sync", "lm_contract")
 LM_NOALLOC_MAX_N, LM_NOALLOC_MAX_M = 65536, 262144
 
 
@@ -97,6 +97,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.lm_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(LmStats)]
         lib.lm_wait.argtypes = [vp, u64, u32]
         lib.lm_sync.argtypes = [vp]
+        lib.lm_contract.argtypes = [vp, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                    ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.lm_strerror.argtypes = [ctypes.c_int]
         lib.lm_strerror.restype = ctypes.c_char_p
         lib.lm_last_error.argtypes = [vp]
@@ -277,6 +279,26 @@ def lm_sync(ctx) -> None:
     """Wait for the matches queued on an LM_F_ASYNC context; raises LmError for a
     device-side error any of them met."""
     _check(load().lm_sync(ctx), ctx)
+
+
+def lm_contract(ctx, n: int, eu, ev, w, mate, vw=None):
+    """Contract the matching `mate` of the graph (n, eu, ev, w) on the device
+    (torch CUDA tensors; int32 / float32).  Returns (cmap[n], cvw[n'], ceu[m'],
+    cev[m'], cw[m']) as CUDA tensors (views of buffers of n and m entries)."""
+    import torch
+    m = int(eu.shape[0])
+    dev = eu.device if m else mate.device
+    cmap = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cvw = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ceu = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    cev = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    cw = torch.empty(max(m, 1), dtype=torch.float32, device=dev)
+    no, mo = ctypes.c_uint32(), ctypes.c_uint32()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().lm_contract(ctx, n, m, ptr(eu), ptr(ev), ptr(w), ptr(vw), ptr(mate), ptr(cmap), ptr(cvw),
+                              ptr(ceu), ptr(cev), ptr(cw), ctypes.byref(no), ctypes.byref(mo)), ctx)
+    k, g = int(no.value), int(mo.value)
+    return cmap[:n], cvw[:k], ceu[:g], cev[:g], cw[:g]
 
 
 def lm_strerror(code: int) -> str:

@@ -146,6 +146,7 @@ void engine_free(Engine& e) {
     destroy_job_graph(e.graph);
     destroy_job_graph(e.egraph);
     if (e.staged) cudaEventDestroy(e.staged);
+    if (e.cblock) cudaFree(e.cblock);
     cudaGetLastError();
     e = Engine();
 }
@@ -815,6 +816,90 @@ int lm_match(lm_ctx* ctx, const lm_graph* g, uint64_t seed, uint32_t* mate, lm_s
         prof.fill(stats);
     }
     return LM_OK;
+}
+
+int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
+                const uint32_t* vw, const uint32_t* mate, uint32_t* cmap, uint32_t* cvw, uint32_t* ceu,
+                uint32_t* cev, float* cw, uint32_t* n_out, uint32_t* m_out) {
+    if (!ctx) return LM_EINVAL;
+    if (ctx->poisoned) return LM_ECUDA;
+    if (!n_out || !m_out) return fail(ctx, LM_EINVAL, "null count output");
+    *n_out = 0;
+    *m_out = 0;
+    if (n == 0 && m == 0) return LM_OK;
+    const void* dev_in[] = {mate, cmap, cvw};
+    for (const void* p : dev_in)
+        if (!is_device_ptr(p)) return fail(ctx, LM_EINVAL, "contraction arrays must be device memory");
+    if (m > 0) {
+        const void* dev_e[] = {eu, ev, w, ceu, cev, cw};
+        for (const void* p : dev_e)
+            if (!is_device_ptr(p)) return fail(ctx, LM_EINVAL, "contraction arrays must be device memory");
+    }
+    if (vw && !is_device_ptr(vw)) return fail(ctx, LM_EINVAL, "vertex weights must be device memory");
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    DevGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
+    Engine& e = ctx->eng;
+    cudaStream_t s = e.stream;
+    ContractArgs c;
+    memset(&c, 0, sizeof c);
+    c.n = n;
+    c.m = m;
+    c.eu = eu;
+    c.ev = ev;
+    c.w = w;
+    c.vw = vw;
+    c.mate = mate;
+    c.cmap = cmap;
+    c.cvw = cvw;
+    c.ceu = ceu;
+    c.cev = cev;
+    c.cw = cw;
+    if (contract_table_slots(m, &c.tslots)) return fail(ctx, LM_EINVAL, "too many edges");
+    const uint32_t scan_count = (n > m ? n : m) + 1;
+    c.scan_words = exclusive_scan_tmp_words(scan_count);
+    Carver cv;
+    cv.add(&c.flag, (size_t)n + 1);
+    cv.add(&c.rank, (size_t)n + 1);
+    cv.add(&c.table, c.tslots);
+    cv.add(&c.slot_of, (size_t)m + 1);
+    cv.add(&c.isl, (size_t)m + 1);
+    cv.add(&c.pos, (size_t)m + 1);
+    cv.add(&c.scan_tmp, c.scan_words);
+    cv.add(&c.err, 4);
+    if (e.cbytes < cv.total) {
+        // grow-only scratch kept by the context (no allocation per call)
+        LM_CK(ctx, cudaStreamSynchronize(s));
+        if (e.cblock) cudaFree(e.cblock);
+        e.cblock = nullptr;
+        e.cbytes = 0;
+        if (cudaMalloc(&e.cblock, cv.total) != cudaSuccess) {
+            cudaGetLastError();
+            e.cblock = nullptr;
+            return fail(ctx, LM_ENOMEM, "contraction scratch of %zu bytes", cv.total);
+        }
+        e.cbytes = cv.total;
+    }
+    cv.assign(e.cblock);
+    int rc = staging_ready(ctx, e);
+    if (!rc) rc = ensure_pinned(ctx, e, 16);
+    if (!rc) {
+        int r = launch_contract(s, c);
+        uint32_t* hp = static_cast<uint32_t*>(e.pinned);
+        cudaError_t ce = (cudaError_t)r;
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[0], c.err, 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[1], c.rank + n, 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[2], c.pos + m, 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return fail(ctx, LM_ECUDA, "contraction: %s", cudaGetErrorString(ce));
+        if (hp[0] & 1u) return fail(ctx, LM_EINVAL, "mate is not a matching of the vertex set");
+        if (hp[0] & 2u) return fail(ctx, LM_EINVAL, "an edge endpoint is >= n");
+        if (hp[0]) return fail(ctx, LM_ECUDA, "contraction table overflow");
+        *n_out = hp[1];
+        *m_out = hp[2];
+        return LM_OK;
+    }
+    return rc;
 }
 
 int lm_sync(lm_ctx* ctx) {

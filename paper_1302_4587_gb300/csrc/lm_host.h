@@ -59,6 +59,8 @@ struct Engine {
     char* dargs = nullptr;           // [ARG_AREA] kernel arguments (device)
     char* hargs = nullptr;           // [ARG_AREA] their pinned staging
     void* graph = nullptr;           // executable job graph (device-driven round loop)
+    void* cblock = nullptr;          // contraction scratch (grown on demand)
+    size_t cbytes = 0;
     cudaEvent_t staged = nullptr;    // recorded after a queued job's uploads from pinned staging
     bool staged_pending = false;
     void* egraph = nullptr;          // the same for the edge-centric path

@@ -270,6 +270,38 @@ uint64_t splitmix64_first(uint64_t seed);  // lm_api.cpp
 int build_job_graph(const JobArgs* dargs, DevState* st, const struct LaunchCfg& cfg, void** exec_out);
 // the one-CTA tail of a job (profiled path): runs the remaining rounds from rounds 2 / 3's arguments
 int launch_tail(void* stream, const JobArgs* dargs, const struct LaunchCfg& cfg);
+
+// contraction of a matching (lm_contract): one table slot per coarse pair, one
+// 32-byte sector, so the three atomics of an insert touch one sector
+struct alignas(32) PairSlot {
+    unsigned long long key;   // unordered coarse pair + 1, 0 = empty
+    uint32_t lead;            // smallest edge index of the pair
+    uint32_t pad;
+    double sum;               // weight sum of the pair
+    double pad2;
+};
+static_assert(sizeof(PairSlot) == 32, "one sector per slot");
+struct ContractArgs {
+    uint32_t n, m;
+    const uint32_t *eu, *ev;
+    const float* w;
+    const uint32_t* vw;       // NULL = 1 per vertex
+    const uint32_t* mate;
+    uint32_t *cmap, *cvw, *ceu, *cev;
+    float* cw;
+    uint32_t* flag;           // [n + 1] representative flags
+    uint32_t* rank;           // [n + 1] their exclusive prefix (rank[n] = coarse vertices)
+    uint32_t tslots;          // table slots (2 m + 1024)
+    struct PairSlot* table;   // [tslots]
+    uint32_t* slot_of;        // [m] table slot of every crossing edge, NIL otherwise
+    uint32_t* isl;            // [m + 1] leader flags
+    uint32_t* pos;            // [m + 1] their exclusive prefix (pos[m] = coarse edges)
+    uint32_t* scan_tmp;
+    size_t scan_words;
+    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n, 4: table full
+};
+int contract_table_slots(uint32_t m, uint32_t* slots);
+int launch_contract(void* stream, const ContractArgs& c);
 int launch_job_graph(void* exec, void* stream);
 // edge-centric path: the job graph (init, then a conditional loop of rounds) and the
 // per-round launches of the profiled path

@@ -1,0 +1,126 @@
+"""Contraction of a matching on the GPU (lm_contract) against the oracle's
+contraction: coarse map, vertex weights, edge list (order, orientation) and
+weights identical, after the GPU's own matching; arbitrary float weights
+within one float32 rounding; several levels of match-and-contract; the
+edge cases and refusals of the C ABI."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import NIL, Lm, to_u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lmc():
+    c = Lm()
+    yield c
+    c.close()
+
+
+def _dev(torch, a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+
+
+def _contract(L, n, eu, ev, w, mate, vw=None):
+    torch, lm = L.torch, L.lm
+    args = [_dev(torch, eu, np.int32), _dev(torch, ev, np.int32), _dev(torch, w, np.float32),
+            _dev(torch, mate.astype(np.uint32), np.int32)]
+    dvw = _dev(torch, vw.astype(np.uint32), np.int32) if vw is not None else None
+    cmap, cvw, ceu, cev, cw = lm.lm_contract(L.ctx, n, *args, vw=dvw)
+    return (to_u32(cmap), to_u32(cvw), to_u32(ceu), to_u32(cev), cw.cpu().numpy())
+
+
+def _same(got, want, exact_w=True):
+    names = ["cmap", "cvw", "ceu", "cev", "cw"]
+    for i in range(4):
+        assert np.array_equal(got[i], want[i]), names[i]
+    if exact_w:
+        assert np.array_equal(got[4].view(np.uint32), want[4].view(np.uint32)), "cw"
+    else:
+        gap = np.abs(got[4].astype(np.float64) - want[4].astype(np.float64))
+        assert (gap <= np.spacing(np.abs(want[4])).astype(np.float64)).all(), "cw beyond one rounding"
+
+
+@pytest.mark.parametrize("which", ["er", "er_unit", "grid", "rmat", "hubs"])
+def test_parity_after_the_gpu_matching(lmc, which):
+    g = {"er": lambda: synth.er(10_000, 50_000, seed=1),
+         "er_unit": lambda: synth.er(10_000, 50_000, seed=1, unit=True),
+         "grid": lambda: synth.grid(256, 256, 0.05, seed=2),
+         "rmat": lambda: synth.rmat(scale=16, edge_factor=16, seed=3),
+         "hubs": lambda: synth.rmat(scale=12, edge_factor=64, a=0.7, b=0.1, c=0.1, seed=4)}[which]()
+    mate, _ = lmc.match(g, 77)
+    assert np.array_equal(mate, oracle.greedy(g.n, g.eu, g.ev, g.w, 77))
+    vw = (np.arange(g.n) % 7 + 1).astype(np.uint32)
+    for weights in (None, vw):
+        got = _contract(lmc, g.n, g.eu, g.ev, g.w, mate, weights)
+        _same(got, oracle.contract(g.n, g.eu, g.ev, g.w, mate, weights))
+
+
+def test_arbitrary_float_weights(lmc):
+    g0 = synth.er(20_000, 120_000, seed=5)
+    rng = np.random.default_rng(5)
+    w = (rng.standard_normal(g0.m) * np.exp2(rng.integers(-30, 30, g0.m))).astype(np.float32)
+    g = synth.Graph(g0.n, g0.eu, g0.ev, w, "er_wide_weights")
+    mate, _ = lmc.match(g, 3)
+    _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate), exact_w=False)
+
+
+def test_multilevel(lmc):
+    g = synth.rmat(scale=15, edge_factor=16, seed=6)
+    n, eu, ev, w, vw = g.n, g.eu, g.ev, g.w, np.ones(g.n, np.uint32)
+    for level in range(5):
+        lev = synth.Graph(n, eu, ev, w, f"level{level}")
+        mate, _ = lmc.match(lev, 200 + level)
+        assert np.array_equal(mate, oracle.greedy(n, eu, ev, w, 200 + level)), level
+        got = _contract(lmc, n, eu, ev, w, mate, vw)
+        want = oracle.contract(n, eu, ev, w, mate, vw)
+        _same(got, want)
+        n, vw, eu, ev, w = got[1].shape[0], got[1], got[2], got[3], got[4]
+        assert int(vw.sum()) == g.n
+
+
+def test_edge_cases(lmc):
+    # no edges; empty matching (identity); a perfect matching of a small graph
+    e0 = np.zeros(0, np.uint32)
+    got = _contract(lmc, 5, e0, e0, np.zeros(0, np.float32), np.full(5, NIL, np.uint32))
+    assert got[0].tolist() == [0, 1, 2, 3, 4] and got[1].tolist() == [1] * 5 and got[2].shape[0] == 0
+    g = synth.er(3000, 12_000, seed=7)
+    ident = _contract(lmc, g.n, g.eu, g.ev, g.w, np.full(g.n, NIL, np.uint32))
+    assert np.array_equal(ident[2], g.eu) and np.array_equal(ident[3], g.ev) and np.array_equal(ident[4], g.w)
+    eu, ev = np.array([0, 1, 2, 3, 0, 1], np.uint32), np.array([1, 2, 3, 0, 2, 3], np.uint32)
+    w = np.array([1, 2, 3, 4, 5, 6], np.float32)
+    mate = np.array([1, 0, 3, 2], np.uint32)
+    _same(_contract(lmc, 4, eu, ev, w, mate), oracle.contract(4, eu, ev, w, mate))
+
+
+def test_refusals(lmc):
+    lm, torch = lmc.lm, lmc.torch
+    eu = _dev(torch, np.array([0, 1], np.uint32), np.int32)
+    ev = _dev(torch, np.array([1, 2], np.uint32), np.int32)
+    w = _dev(torch, np.array([1, 2], np.float32), np.float32)
+    bad_mates = [np.array([1, 2, NIL], np.uint32), np.array([7, NIL, NIL], np.uint32), np.array([0, NIL, NIL], np.uint32)]
+    for bm in bad_mates:
+        with pytest.raises(lm.LmError) as ei:
+            lm.lm_contract(lmc.ctx, 3, eu, ev, w, _dev(torch, bm, np.int32))
+        assert ei.value.code == lm.LM_EINVAL
+    with pytest.raises(lm.LmError) as ei:  # endpoint out of range
+        lm.lm_contract(lmc.ctx, 2, eu, ev, w, _dev(torch, np.full(2, NIL, np.uint32), np.int32))
+    assert ei.value.code == lm.LM_EINVAL
+    with pytest.raises(lm.LmError) as ei:  # host memory
+        lm.lm_contract(lmc.ctx, 3, eu.cpu(), ev.cpu(), w.cpu(), torch.full((3,), -1, dtype=torch.int32))
+    assert ei.value.code == lm.LM_EINVAL
+
+
+def test_rmat21_full_parity(lmc):
+    g = synth.rmat(scale=21, edge_factor=16, seed=3)
+    h = lmc.graph(g)
+    try:
+        mate, _ = lmc.match(g, 103, handle=h)
+    finally:
+        lmc.lm.lm_graph_destroy(h)
+    _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate))
