@@ -1,5 +1,5 @@
-// Internal declarations shared by the kernels (lm_kernels.cu) and the host
-// driver (lm_api.cpp, lm_serve.cpp).  Not part of the public ABI (include/lm.h is).
+// Internal declarations shared by the kernels (lm_kernels.cu, lm_contract.cu) and
+// the host code (lm_api.cpp, lm_serve.cpp).  Not part of the public ABI (include/lm.h is).
 //
 // Layout of one matching job (one graph, or the disjoint union of a batch):
 //   * vertices live in a union id space [0, N); graph g owns [vbase_g, vbase_g + n_g)
