@@ -10,10 +10,13 @@
 //
 // Device steps (all of them here): representatives and their prefix ranks;
 // the coarse map and vertex weights; every crossing edge inserts its unordered
-// coarse pair into an open-addressing table (64-bit key, linear probing)
-// where it lowers the pair's leader (the smallest edge index) and adds its
-// weight; leader flags over the edges and their prefix ranks give each coarse
-// edge its place; the leaders write the coarse edges.
+// coarse pair into an open-addressing table (64-bit key, linear probing): the
+// edge that creates a slot stores itself as the pair's leader and its weight
+// as the sum with plain stores, and an edge that finds its pair already there
+// marks itself; in the next kernel only those marked edges lower the leader
+// (the smallest edge index) and add their weight with atomics (most pairs have
+// one edge and need none); leader flags over the edges and their prefix ranks
+// give each coarse edge its place; the leaders write the coarse edges.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/lm.h"
@@ -24,6 +27,7 @@ namespace lm {
 namespace {
 
 constexpr uint32_t CT = 256;
+constexpr uint32_t SLOT_DUP = 0x80000000u;  // slot_of: the pair was already in the table
 constexpr uint32_t C_ERR_MATE = 1u, C_ERR_EDGE = 2u, C_ERR_TABLE = 4u;
 
 __device__ __forceinline__ uint64_t pair_hash(uint64_t k) {
@@ -71,16 +75,38 @@ __global__ void k_c_insert(const uint32_t* __restrict__ eu, const uint32_t* __re
         const unsigned long long key = ((((unsigned long long)min(c, d)) << 32) | max(c, d)) + 1ull;
         // slot: the hash's high half scaled to the table (multiply-shift), then linear probing
         uint32_t h = (uint32_t)(((pair_hash(key) >> 32) * (unsigned long long)tslots) >> 32);
-        bool placed = false;
+        bool placed = false, created = false;
         for (uint32_t probe = 0; probe < tslots; probe++) {
             const unsigned long long old = atomicCAS(&table[h].key, 0ull, key);
-            if (old == 0ull || old == key) { placed = true; break; }
+            if (old == 0ull || old == key) {
+                placed = true;
+                created = old == 0ull;
+                break;
+            }
             h = (h + 1u == tslots) ? 0u : h + 1u;
         }
         if (!placed) { atomicOr(err, C_ERR_TABLE); continue; }
-        atomicMin(&table[h].lead, e);
-        atomicAdd(&table[h].sum, (double)w[e]);
-        slot_of[e] = h;
+        if (created) {
+            // the slot's creator: leader and sum so far (others add theirs in the next kernel)
+            table[h].lead = e;
+            table[h].sum = (double)w[e];
+            slot_of[e] = h;
+        } else {
+            slot_of[e] = h | SLOT_DUP;
+        }
+    }
+}
+
+// edges whose pair was already in the table: lower the leader, add the weight
+__global__ void k_c_merge(const float* __restrict__ w, uint32_t m, PairSlot* __restrict__ table,
+                          uint32_t* __restrict__ slot_of) {
+    for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
+        const uint32_t h = slot_of[e];
+        if (h == NIL || !(h & SLOT_DUP)) continue;
+        const uint32_t hs = h & ~SLOT_DUP;
+        atomicMin(&table[hs].lead, e);
+        atomicAdd(&table[hs].sum, (double)w[e]);
+        slot_of[e] = hs;
     }
 }
 
@@ -133,7 +159,7 @@ uint32_t grid_for(uint64_t count) {
 // 1.25 per edge measured 30% slower on R-MAT 23), at least 1024
 int contract_table_slots(uint32_t m, uint32_t* slots) {
     const uint64_t t = 2ull * m + 1024;
-    if (t > 0xFFFFFFF0ull) return (int)cudaErrorInvalidValue;
+    if (t >= SLOT_DUP) return (int)cudaErrorInvalidValue;  // slot indices keep bit 31 free
     *slots = (uint32_t)t;
     return 0;
 }
@@ -152,6 +178,7 @@ int launch_contract(void* stream, const ContractArgs& c) {
     if (c.m) {
         k_c_insert<<<grid_for(c.m), CT, 0, s>>>(c.eu, c.ev, c.w, c.m, c.n, c.cmap, c.tslots, c.table,
                                                  c.slot_of, c.err);
+        k_c_merge<<<grid_for(c.m), CT, 0, s>>>(c.w, c.m, c.table, c.slot_of);
         k_c_lead<<<grid_for(c.m), CT, 0, s>>>(c.m, c.slot_of, c.table, c.isl);
     }
     if (int r = launch_exclusive_scan(s, c.isl, c.pos, c.m + 1, c.scan_tmp, c.scan_words)) return r;
