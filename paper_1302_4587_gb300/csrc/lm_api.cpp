@@ -640,9 +640,24 @@ int lm_create(const lm_config* cfg, lm_ctx** out) {
     ctx->max_slots = cfg->max_slots ? cfg->max_slots : 4096;
     ctx->flags = cfg->flags;
     ctx->eng.cfg.renew = (cfg->flags & LM_F_RENEW) != 0;
+    {
+        cudaMemPoolProps pp;
+        memset(&pp, 0, sizeof pp);
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.handleTypes = cudaMemHandleTypeNone;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = cfg->device;
+        if (cudaMemPoolCreate(&ctx->pool, &pp) != cudaSuccess) {
+            cudaGetLastError();
+            return LM_ECUDA;
+        }
+        uint64_t keep = ~0ull;  // never trim on synchronisation
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     int rc = engine_init(ctx.get(), ctx->eng, (cudaStream_t)cfg->stream);
     if (rc) {
         engine_free(ctx->eng);
+        cudaMemPoolDestroy(ctx->pool);
         return rc;
     }
     if (cfg->flags & LM_F_PROFILE) {
@@ -666,6 +681,7 @@ void lm_destroy(lm_ctx* ctx) {
     DevGuard g(ctx->device);
     engine_free(ctx->eng);
     for (int i = 0; i < ctx->nev; i++) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once no allocation is left
     cudaGetLastError();
     delete ctx;
 }
@@ -712,7 +728,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     tc.add(&scan_tmp, scan_words);
     tc.add(&err, 4);
     void* tmp = nullptr;
-    cudaError_t ce = cudaMallocAsync(&tmp, tc.total, s);
+    cudaError_t ce = cudaMallocFromPoolAsync(&tmp, tc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph staging");
     tc.assign(tmp);
     struct TmpFree {
@@ -757,7 +773,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     gc.add(&g->pk, (size_t)g->nent + 4);
     gc.add(&g->edges, (size_t)g->m + 2);
     gc.add(&g->eword, (size_t)g->m + 4);
-    ce = cudaMalloc(&g->block, gc.total);
+    ce = cudaMallocFromPoolAsync(&g->block, gc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
     gc.assign(g->block);
     g->bytes = gc.total;
@@ -779,9 +795,10 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
 void lm_graph_destroy(lm_graph* g) {
     if (!g) return;
     DevGuard dg(g->ctx->device);
-    if (g->ctx->eng.stream) cudaStreamSynchronize(g->ctx->eng.stream);
-    else cudaDeviceSynchronize();
-    if (g->block) cudaFree(g->block);
+    // the graph may still be read by work on the context's stream or the serving
+    // engine's: wait for the device, then return the block to the context's pool
+    cudaDeviceSynchronize();
+    if (g->block) cudaFreeAsync(g->block, g->ctx->eng.stream);
     cudaGetLastError();
     delete g;
 }

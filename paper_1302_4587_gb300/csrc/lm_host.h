@@ -88,6 +88,9 @@ struct lm_ctx {
     std::mutex call_mu;              // serialises calls on the context's engine
     std::mutex err_mu;
     lm::ServeState* serve = nullptr;
+    // the context's own stream-ordered memory pool (graph arrays, graph-build
+    // staging): memory a destroyed graph frees stays mapped for the next one
+    cudaMemPool_t pool = nullptr;
 };
 
 // A device graph (Sec. 2.1 representation): per-vertex offsets V into the
