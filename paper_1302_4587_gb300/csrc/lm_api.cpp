@@ -681,6 +681,8 @@ void lm_destroy(lm_ctx* ctx) {
     DevGuard g(ctx->device);
     engine_free(ctx->eng);
     for (int i = 0; i < ctx->nev; i++) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->up) cudaStreamDestroy(ctx->up);
+    if (ctx->up_ev) cudaEventDestroy(ctx->up_ev);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // released once no allocation is left
     cudaGetLastError();
     delete ctx;
@@ -736,18 +738,35 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
         cudaStream_t s;
         ~TmpFree() { if (p) cudaFreeAsync(p, s); }
     } tf{tmp, s};
-    if (mem == LM_HOST && m > 0) {
-        LM_CK(ctx, cudaMemcpyAsync(t_eu, eu, (size_t)m * 4, cudaMemcpyHostToDevice, s));
-        LM_CK(ctx, cudaMemcpyAsync(t_ev, ev, (size_t)m * 4, cudaMemcpyHostToDevice, s));
-        LM_CK(ctx, cudaMemcpyAsync(t_w, w, (size_t)m * 4, cudaMemcpyHostToDevice, s));
-        d_eu = t_eu;
-        d_ev = t_ev;
-        d_w = t_w;
-    }
     LM_CK(ctx, cudaMemsetAsync(deg, 0, nn * 4, s));
     LM_CK(ctx, cudaMemsetAsync(err, 0, 16, s));
     // validation rides on the degree count: endpoint < n, no self loop, no NaN
-    if (m > 0) LM_CK(ctx, launch_build_degrees(s, d_eu, d_ev, d_w, n, m, deg, err));
+    if (mem == LM_HOST && m > 0) {
+        // chunks of the host arrays go up on the upload stream; the context's stream
+        // counts a chunk's degrees while the next chunk is copied
+        if (!ctx->up) {
+            LM_CK(ctx, cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
+            LM_CK(ctx, cudaEventCreateWithFlags(&ctx->up_ev, cudaEventDisableTiming));
+        }
+        LM_CK(ctx, cudaEventRecord(ctx->up_ev, s));  // after the memsets (and earlier work)
+        LM_CK(ctx, cudaStreamWaitEvent(ctx->up, ctx->up_ev, 0));
+        constexpr uint32_t NCHUNK = 8;
+        const uint32_t step = ((m + NCHUNK - 1) / NCHUNK + 31) & ~31u;
+        for (uint32_t off = 0; off < m; off += step) {
+            const uint32_t cnt = std::min(step, m - off);
+            LM_CK(ctx, cudaMemcpyAsync(t_eu + off, eu + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, ctx->up));
+            LM_CK(ctx, cudaMemcpyAsync(t_ev + off, ev + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, ctx->up));
+            LM_CK(ctx, cudaMemcpyAsync(t_w + off, w + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, ctx->up));
+            LM_CK(ctx, cudaEventRecord(ctx->up_ev, ctx->up));
+            LM_CK(ctx, cudaStreamWaitEvent(s, ctx->up_ev, 0));
+            LM_CK(ctx, launch_build_degrees(s, t_eu + off, t_ev + off, t_w + off, n, cnt, deg, err));
+        }
+        d_eu = t_eu;
+        d_ev = t_ev;
+        d_w = t_w;
+    } else if (m > 0) {
+        LM_CK(ctx, launch_build_degrees(s, d_eu, d_ev, d_w, n, m, deg, err));
+    }
     int rc = ensure_pinned(ctx, e, 64);
     if (rc) return rc;
     uint32_t* hp = static_cast<uint32_t*>(e.pinned);

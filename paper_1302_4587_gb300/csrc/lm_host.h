@@ -91,6 +91,10 @@ struct lm_ctx {
     // the context's own stream-ordered memory pool (graph arrays, graph-build
     // staging): memory a destroyed graph frees stays mapped for the next one
     cudaMemPool_t pool = nullptr;
+    // upload of a host edge list in chunks on its own stream, each chunk's degree
+    // count on the context's stream while the next chunk is in flight
+    cudaStream_t up = nullptr;
+    cudaEvent_t up_ev = nullptr;
 };
 
 // A device graph (Sec. 2.1 representation): per-vertex offsets V into the
