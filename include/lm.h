@@ -256,11 +256,9 @@ int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const ui
  * vertex order; a coarse vertex weighs the sum of its members; edges inside a
  * pair vanish; the original edges between two coarse vertices become one
  * coarse edge, placed and oriented as the first of them in input order,
- * weighing their sum (accumulated in double, rounded once to float32: the
- * result does not depend on the accumulation order whenever that double sum is
- * exact, e.g. for weights on a common 2^-k grid; otherwise it is within one
- * float32 rounding of the ordered sum).  The output is itself an edge list in
- * lm_graph_create's form, so levels chain.
+ * weighing their sum (accumulated in double in input order, rounded once to
+ * float32).  The output is itself an edge list in lm_graph_create's form, so
+ * levels chain.
  *   n, m          vertices and edges; eu, ev, w: device uint32[m], uint32[m], float32[m]
  *   vw            device uint32[n] vertex weights, or NULL (1 each)
  *   mate          device uint32[n]: a matching of the vertex set (partner or LM_NIL)
@@ -270,7 +268,7 @@ int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const ui
  *   n_out, m_out  host out: coarse vertex and edge counts
  * Runs on the context's stream and returns when the outputs are complete; the
  * caller owns every array.  Errors: LM_EINVAL (null or host pointer; mate not
- * a matching of the vertex set; an endpoint >= n; m >= 2^30), LM_ENOMEM,
+ * a matching of the vertex set; an endpoint >= n; m >= 2^31), LM_ENOMEM,
  * LM_ECUDA. */
 int  lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
                  const uint32_t* vw, const uint32_t* mate, uint32_t* cmap, uint32_t* cvw, uint32_t* ceu,

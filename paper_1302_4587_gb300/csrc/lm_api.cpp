@@ -891,16 +891,25 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     c.ceu = ceu;
     c.cev = cev;
     c.cw = cw;
-    if (contract_table_slots(m, &c.tslots)) return fail(ctx, LM_EINVAL, "too many edges");
+    if (m >= (1u << 31)) return fail(ctx, LM_EINVAL, "too many edges");
     const uint32_t scan_count = (n > m ? n : m) + 1;
     c.scan_words = exclusive_scan_tmp_words(scan_count);
+    const size_t hist_words = contract_sort_tmp_words(m);
+    const size_t M = (size_t)m + 1;
     Carver cv;
     cv.add(&c.flag, (size_t)n + 1);
     cv.add(&c.rank, (size_t)n + 1);
-    cv.add(&c.table, c.tslots);
-    cv.add(&c.slot_of, (size_t)m + 1);
-    cv.add(&c.isl, (size_t)m + 1);
-    cv.add(&c.pos, (size_t)m + 1);
+    cv.add(&c.cross, M);
+    cv.add(&c.cpos, M);
+    cv.add(&c.key[0], M);
+    cv.add(&c.key[1], M);
+    cv.add(&c.val[0], M);
+    cv.add(&c.val[1], M);
+    cv.add(&c.hist, hist_words);
+    cv.add(&c.hoff, hist_words + 1);
+    cv.add(&c.isl, M);
+    cv.add(&c.pos, M);
+    cv.add(&c.gref, M);
     cv.add(&c.scan_tmp, c.scan_words);
     cv.add(&c.err, 4);
     if (e.cbytes < cv.total) {
@@ -918,24 +927,21 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     }
     cv.assign(e.cblock);
     int rc = staging_ready(ctx, e);
-    if (!rc) rc = ensure_pinned(ctx, e, 16);
-    if (!rc) {
-        int r = launch_contract(s, c);
-        uint32_t* hp = static_cast<uint32_t*>(e.pinned);
-        cudaError_t ce = (cudaError_t)r;
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[0], c.err, 4, cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[1], c.rank + n, 4, cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[2], c.pos + m, 4, cudaMemcpyDeviceToHost, s);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-        if (ce != cudaSuccess) return fail(ctx, LM_ECUDA, "contraction: %s", cudaGetErrorString(ce));
-        if (hp[0] & 1u) return fail(ctx, LM_EINVAL, "mate is not a matching of the vertex set");
-        if (hp[0] & 2u) return fail(ctx, LM_EINVAL, "an edge endpoint is >= n");
-        if (hp[0]) return fail(ctx, LM_ECUDA, "contraction table overflow");
-        *n_out = hp[1];
-        *m_out = hp[2];
-        return LM_OK;
-    }
-    return rc;
+    if (!rc) rc = ensure_pinned(ctx, e, 32);
+    if (rc) return rc;
+    uint32_t* hp = static_cast<uint32_t*>(e.pinned);
+    cudaError_t ce = (cudaError_t)launch_contract(s, c, &hp[4]);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[0], c.err, 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[1], c.rank + n, 4, cudaMemcpyDeviceToHost, s);
+    hp[2] = 0;
+    if (ce == cudaSuccess && m > 0) ce = cudaMemcpyAsync(&hp[2], c.pos + m, 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return fail(ctx, LM_ECUDA, "contraction: %s", cudaGetErrorString(ce));
+    if (hp[0] & 1u) return fail(ctx, LM_EINVAL, "mate is not a matching of the vertex set");
+    if (hp[0] & 2u) return fail(ctx, LM_EINVAL, "an edge endpoint is >= n");
+    *n_out = hp[1];
+    *m_out = hp[2];
+    return LM_OK;
 }
 
 int lm_sync(lm_ctx* ctx) {

@@ -271,16 +271,7 @@ int build_job_graph(const JobArgs* dargs, DevState* st, const struct LaunchCfg& 
 // the one-CTA tail of a job (profiled path): runs the remaining rounds from rounds 2 / 3's arguments
 int launch_tail(void* stream, const JobArgs* dargs, const struct LaunchCfg& cfg);
 
-// contraction of a matching (lm_contract): one table slot per coarse pair, one
-// 32-byte sector, so the three atomics of an insert touch one sector
-struct alignas(32) PairSlot {
-    unsigned long long key;   // unordered coarse pair + 1, 0 = empty
-    uint32_t lead;            // smallest edge index of the pair
-    uint32_t pad;
-    double sum;               // weight sum of the pair
-    double pad2;
-};
-static_assert(sizeof(PairSlot) == 32, "one sector per slot");
+// contraction of a matching (lm_contract): inputs, outputs and device scratch
 struct ContractArgs {
     uint32_t n, m;
     const uint32_t *eu, *ev;
@@ -291,17 +282,23 @@ struct ContractArgs {
     float* cw;
     uint32_t* flag;           // [n + 1] representative flags
     uint32_t* rank;           // [n + 1] their exclusive prefix (rank[n] = coarse vertices)
-    uint32_t tslots;          // table slots (2 m + 1024)
-    struct PairSlot* table;   // [tslots]
-    uint32_t* slot_of;        // [m] table slot of every crossing edge, NIL otherwise
+    uint32_t* cross;          // [m + 1] crossing-edge flags
+    uint32_t* cpos;           // [m + 1] their exclusive prefix (cpos[m] = crossing edges)
+    unsigned long long* key[2];  // [m] coarse pair of each crossing edge (radix ping-pong)
+    uint32_t* val[2];         // [m] its edge index
+    uint32_t* hist;           // [256 * blocks] digit counts of a radix pass
+    uint32_t* hoff;           // [256 * blocks + 1] their exclusive prefix
     uint32_t* isl;            // [m + 1] leader flags
     uint32_t* pos;            // [m + 1] their exclusive prefix (pos[m] = coarse edges)
+    uint32_t* gref;           // [m] a leader's group start in sorted order
     uint32_t* scan_tmp;
     size_t scan_words;
-    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n, 4: table full
+    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n
 };
-int contract_table_slots(uint32_t m, uint32_t* slots);
-int launch_contract(void* stream, const ContractArgs& c);
+size_t contract_sort_tmp_words(uint32_t m);  // words of hist (and of hoff, plus one)
+// runs every step; mc_host_slot: 2 pinned words (crossing edges and coarse vertices
+// are read back once, to size the sort); returns a cudaError_t value
+int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot);
 int launch_job_graph(void* exec, void* stream);
 // edge-centric path: the job graph (init, then a conditional loop of rounds) and the
 // per-round launches of the profiled path

@@ -1,8 +1,9 @@
 """Contraction of a matching on the GPU (lm_contract) against the oracle's
 contraction: coarse map, vertex weights, edge list (order, orientation) and
-weights identical, after the GPU's own matching; arbitrary float weights
-within one float32 rounding; several levels of match-and-contract; the
-edge cases and refusals of the C ABI."""
+weights identical, after the GPU's own matching, for generator weights and
+for arbitrary float weights and parallel edges (both sides sum in input
+order); several levels of match-and-contract; the edge cases and refusals of
+the C ABI."""
 from __future__ import annotations
 
 import numpy as np
@@ -62,12 +63,27 @@ def test_parity_after_the_gpu_matching(lmc, which):
 
 
 def test_arbitrary_float_weights(lmc):
+    # weights over sixty binary orders of magnitude, both signs: the sums are taken in
+    # input order on both sides, so they agree bit for bit even where double rounds
     g0 = synth.er(20_000, 120_000, seed=5)
     rng = np.random.default_rng(5)
     w = (rng.standard_normal(g0.m) * np.exp2(rng.integers(-30, 30, g0.m))).astype(np.float32)
     g = synth.Graph(g0.n, g0.eu, g0.ev, w, "er_wide_weights")
     mate, _ = lmc.match(g, 3)
-    _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate), exact_w=False)
+    _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate))
+
+
+def test_parallel_edges_merge_in_input_order(lmc):
+    # many parallel copies of a few pairs with weights whose double sum depends on the order
+    rng = np.random.default_rng(8)
+    n = 40
+    eu = rng.integers(0, n, 5000).astype(np.uint32)
+    ev = ((eu + 1 + rng.integers(0, 5, 5000)) % n).astype(np.uint32)
+    w = (rng.standard_normal(5000) * np.exp2(rng.integers(-40, 40, 5000))).astype(np.float32)
+    mate = np.full(n, NIL, np.uint32)
+    for a in range(0, n, 4):
+        mate[a], mate[a + 1] = a + 1, a
+    _same(_contract(lmc, n, eu, ev, w, mate), oracle.contract(n, eu, ev, w, mate))
 
 
 def test_multilevel(lmc):
