@@ -490,8 +490,8 @@ def run_contract(args, ws, rank, local):
     computed first (untimed); each step contracts it from device-resident edge
     list, weights and mate.  Metric: input edges/s contracted.  Algorithmic
     bytes: the edge list read once (12 B per edge), the coarse map written and
-    read (8 B per vertex) and the coarse edges written (12 B each); the
-    pair table's atomics come on top of that."""
+    read (8 B per vertex) and the coarse edges written (12 B each); the radix
+    sort that groups the coarse pairs moves more on top of that."""
     import torch
     import paper_1302_4587_gb300 as lm
     torch.cuda.set_device(local)
@@ -535,7 +535,7 @@ def run_contract(args, ws, rank, local):
             "roofline": {"bound": "hbm", "kernel": "lm_contract (all its kernels)", "achieved": ach, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                          "bytes_per_step": algo},
-            "clocks": clk.summary(), "gpu_launches": 13 * args.steps}  # 5 kernels + 3 + 5 scan kernels per call
+            "clocks": clk.summary(), "gpu_launches": 50 * args.steps}  # R-MAT 23: 9 kernels, 6 radix passes of 5, 3 scans
 
 
 def run_paper_sweep(args, ws, rank, local):
