@@ -538,6 +538,67 @@ def run_contract(args, ws, rank, local):
             "clocks": clk.summary(), "gpu_launches": 50 * args.steps}  # R-MAT 23: 9 kernels, 6 radix passes of 5, 3 scans
 
 
+def run_coarsen(args, ws, rank, local):
+    """The paper's motivating use (Sec. 1): multilevel coarsening by repeatedly
+    matching and contracting.  R-MAT 23, eight levels of lm_graph_create (from
+    the device-resident edge list of the level), lm_match and lm_contract; the
+    step is the whole chain.  Metric: input edges/s coarsened (the first level's
+    m over the chain's time)."""
+    import torch
+    import paper_1302_4587_gb300 as lm
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g, seed, desc = make_workload("rmat23")
+    ctx = lm.lm_create(local, stream)
+    eu0 = torch.from_numpy(g.eu.view(np.int32)).to(dev)
+    ev0 = torch.from_numpy(g.ev.view(np.int32)).to(dev)
+    w0 = torch.from_numpy(g.w).to(dev)
+    levels = 8
+
+    def chain(record):
+        n, eu, ev, w, vw = g.n, eu0, ev0, w0, None
+        for lev in range(levels):
+            h = lm.lm_graph_create(ctx, n, eu, ev, w)
+            mate = torch.empty(max(n, 1), dtype=torch.int32, device=dev)[:n]
+            if record is not None:
+                _, st = lm.lm_match(ctx, h, seed + lev, mate, stats=True)
+            else:
+                lm.lm_match(ctx, h, seed + lev, mate)
+            lm.lm_graph_destroy(h)
+            cmap, cvw, ceu, cev, cw = lm.lm_contract(ctx, n, eu, ev, w, mate, vw)
+            if record is not None:
+                record.append({"level": lev, "n": n, "m": int(eu.shape[0]), "rounds": st["rounds"],
+                               "matched": st["matched"], "coarse_n": int(cvw.shape[0]), "coarse_m": int(ceu.shape[0])})
+            n, eu, ev, w, vw = int(cvw.shape[0]), ceu.clone(), cev.clone(), cw.clone(), cvw.clone()
+
+    table = []
+    chain(table)
+    for _ in range(max(args.warmup, 3) - 1):
+        chain(None)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 5))
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            chain(None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    ms = _barrier_max(e0.elapsed_time(e1) / steps, ws)
+    lm.lm_destroy(ctx)
+    return {"metric": "input edges/s coarsened (8 levels of match + contract)", "value": whole_job_value(g.m, ws, ms),
+            "unit": "edges/s", "n_gpus": ws, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 ids / f64 sums",
+            "data": "synthetic",
+            "config": {"workload": "coarsen", "desc": desc + "; each level: graph build, match, contraction",
+                       "levels": table, "l2": "inputs larger than L2 (edge list 1.55 GB)"},
+            "clocks": clk.summary()}
+
+
 def run_paper_sweep(args, ws, rank, local):
     """The shape of the paper's GPU comparison (Sec. 3.3, rgg and random-graph
     figures): for random geometric graphs and random graphs with alpha n edges
@@ -654,7 +715,7 @@ def main():
     ap.add_argument("--impl", default="lm", choices=["lm", "reference"])
     ap.add_argument("--workload", default="rmat23",
                     choices=["rmat23", "rmat21", "grid", "er", "rmat23_unit", "batch", "serve", "paper_sweep",
-                             "contract"])
+                             "contract", "coarsen"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--algo", default="segmented", choices=["segmented", "edge"],
                     help="edge: the edge-centric (Combining CRCW) path, for comparison")
@@ -674,9 +735,9 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    if args.workload in ("batch", "serve", "paper_sweep", "contract"):
+    if args.workload in ("batch", "serve", "paper_sweep", "contract", "coarsen"):
         out = {"batch": run_batch, "serve": run_serve, "paper_sweep": run_paper_sweep,
-               "contract": run_contract}[args.workload](args, ws, rank, local)
+               "contract": run_contract, "coarsen": run_coarsen}[args.workload](args, ws, rank, local)
         if rank == 0:
             print(json.dumps(out), flush=True)
         if ws > 1:
