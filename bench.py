@@ -559,23 +559,29 @@ def run_coarsen(args, ws, rank, local):
     def chain(record):
         n, eu, ev, w, vw = g.n, eu0, ev0, w0, None
         for lev in range(levels):
+            t0 = time.perf_counter()
             h = lm.lm_graph_create(ctx, n, eu, ev, w)
             mate = torch.empty(max(n, 1), dtype=torch.int32, device=dev)[:n]
+            t1 = time.perf_counter()
             if record is not None:
                 _, st = lm.lm_match(ctx, h, seed + lev, mate, stats=True)
             else:
                 lm.lm_match(ctx, h, seed + lev, mate)
+            t2 = time.perf_counter()
             lm.lm_graph_destroy(h)
             cmap, cvw, ceu, cev, cw = lm.lm_contract(ctx, n, eu, ev, w, mate, vw)
+            t3 = time.perf_counter()
             if record is not None:
                 record.append({"level": lev, "n": n, "m": int(eu.shape[0]), "rounds": st["rounds"],
-                               "matched": st["matched"], "coarse_n": int(cvw.shape[0]), "coarse_m": int(ceu.shape[0])})
+                               "matched": st["matched"], "coarse_n": int(cvw.shape[0]), "coarse_m": int(ceu.shape[0]),
+                               "build_ms": round((t1 - t0) * 1e3, 2), "match_ms": round((t2 - t1) * 1e3, 2),
+                               "contract_ms": round((t3 - t2) * 1e3, 2)})
             n, eu, ev, w, vw = int(cvw.shape[0]), ceu.clone(), cev.clone(), cw.clone(), cvw.clone()
 
-    table = []
-    chain(table)
     for _ in range(max(args.warmup, 3) - 1):
         chain(None)
+    table = []
+    chain(table)  # per-level sizes and host-clock phase times (each call ends synchronised)
     torch.cuda.synchronize()
     _barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
