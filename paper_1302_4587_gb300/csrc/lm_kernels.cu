@@ -182,8 +182,14 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
 }
 
 // ---------------------------------------------------------------- vertex pass
-constexpr int VT = 256;  // threads
-constexpr int VI = 4;    // rows per thread per block iteration
+#ifndef LM_VI
+#define LM_VI 4
+#endif
+#ifndef LM_VMINB
+#define LM_VMINB 4
+#endif
+constexpr int VT = 256;    // threads
+constexpr int VI = LM_VI;  // rows per thread per block iteration
 
 // exclusive scan of three counters over the block (a, b, c become their
 // prefixes; tot receives the block totals)
@@ -415,7 +421,7 @@ __device__ __forceinline__ void vertex_pass(const VertexArgs& a, uint32_t cta, u
     }
 }
 
-__global__ void __launch_bounds__(VT, 4) k_vertex(const VertexArgs* __restrict__ pav) {
+__global__ void __launch_bounds__(VT, LM_VMINB) k_vertex(const VertexArgs* __restrict__ pav) {
     vertex_pass(*pav, blockIdx.x, gridDim.x);
 }
 
@@ -1663,7 +1669,8 @@ int launch_init(void* stream, const InitArgs* dargs) {
 
 // the vertex pass fits 4 CTAs per SM (launch bounds); 0 or more takes that
 static uint32_t vertex_grid(const LaunchCfg& c) {
-    const uint32_t per = (c.vertex_ctas_per_sm == 0 || c.vertex_ctas_per_sm > 4) ? 4u : c.vertex_ctas_per_sm;
+    const uint32_t per = (c.vertex_ctas_per_sm == 0 || c.vertex_ctas_per_sm > LM_VMINB) ? (uint32_t)LM_VMINB
+                                                                                    : c.vertex_ctas_per_sm;
     return (uint32_t)current_sms() * per;
 }
 
