@@ -111,7 +111,8 @@ typedef struct {
 
 /* Create a context on cfg->device working on cfg->stream.  *out receives the
  * handle, owned by the caller until lm_destroy.  Errors: LM_EINVAL (null
- * argument, bad device), LM_ECUDA. */
+ * argument, bad device, or flags that cannot go together: LM_F_RENEW or
+ * LM_F_ASYNC with LM_F_EDGE_CENTRIC, LM_F_ASYNC with LM_F_PROFILE), LM_ECUDA. */
 int  lm_create(const lm_config* cfg, lm_ctx** out);
 
 /* Destroy a context: waits for its stream, stops the serving thread, frees
