@@ -68,6 +68,7 @@ LM_HD void kv_max(uint64_t& k, uint32_t& u, uint64_t k2, uint32_t u2) {
 // bit 31 of a row's length word marks the first row of a batch, and B lists
 // the R index of every batch's first row, in no particular order.
 constexpr uint32_t BATCH_START = 0x80000000u;
+constexpr uint32_t R_LEN_KNOWN = 0x80000000u;  // vertex pass, internal: the length came with the entry
 struct Lists {
     uint2* R;
     uint2* C;

@@ -273,18 +273,22 @@ __device__ __forceinline__ void vertex_pass(const VertexArgs& a, uint32_t cta, u
                     const uint2 c = a.in.C[idx];
                     if (c.y == 0) v = c.x;
                 } else {
-                    v = a.in.R[idx - nC].x;
+                    // a short row: the sweep left its survivor count in the entry itself
+                    const uint2 rr = a.in.R[idx - nC];
+                    v = rr.x;
+                    L = (rr.y & ~BATCH_START) | R_LEN_KNOWN;
                 }
                 if (v != NIL && v >= va.nvert) { set_err(st, ERR_BOUNDS, v); v = NIL; }
             }
             vv[i] = v;
             LL[i] = L;
         }
-        // phase 2: its live length
+        // phase 2: its live length (long rows and dense ranges keep theirs in len[])
 #pragma unroll
         for (int i = 0; i < VI; i++) {
             if (vv[i] == NIL) continue;
-            if (a.vlist && a.deg0) va.len[par][vv[i]] = LL[i];
+            if (LL[i] & R_LEN_KNOWN) LL[i] &= ~R_LEN_KNOWN;
+            else if (a.vlist && a.deg0) va.len[par][vv[i]] = LL[i];
             else LL[i] = va.len[par][vv[i]];
         }
         // phase 3: the mutual-choice test (two dependent gathers)
@@ -694,7 +698,9 @@ __device__ void do_rows_p(const SweepArgs& a, WarpRows<RENEW>& W, WarpStage& S, 
     cp_async_wait<0>();
     __syncwarp();
     if (v != NIL) {
-        if (COMPACT) va.len[a.par ^ 1u][v] = W.rcnt[lane];
+        // the survivor count goes into the row's own task-list entry (read there by
+        // the next vertex pass; the batch-start bit stays for the other warps' scans)
+        if (COMPACT) a.in.R[idx].y = W.rcnt[lane] | (rv.y & BATCH_START);
         const uint64_t K = W.rkey[lane];
         // compaction sweeps carried the neighbour along; the candidate-only sweep
         // recovers it from the key's edge id
