@@ -33,7 +33,7 @@ METRIC = "input edges/s to maximal matching"
 # dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
 # an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
 # capture with several metrics); None for workloads without a capture of the current kernels
-TRAFFIC = {"rmat23": 6032304784}
+TRAFFIC = {"rmat23": 6068360297}
 
 
 def _peaks():

@@ -799,7 +799,8 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
     if (m > 0) {
         LM_CK(ctx, cudaMemcpyAsync(cursor, g->off, nn * 4, cudaMemcpyDeviceToDevice, s));
-        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges, g->eword));
+        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges, g->eword, err));
+        LM_CK(ctx, cudaMemcpyAsync(&hp[2], err, 4, cudaMemcpyDeviceToHost, s));
     }
     LM_CK(ctx, launch_build_rows(s, deg, rowidx, g->off, n, g->nrows, g->nent, g->vid, g->rdeg, g->roff));
     if (g->nrows) {
@@ -807,6 +808,10 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
         LM_CK(ctx, launch_build_tilemap(s, g->roff, g->nrows, g->nent, g->tmap, g->rbits, g->tdesc));
     }
     LM_CK(ctx, cudaStreamSynchronize(s));
+    if (m > 0 && (hp[2] & 2u)) {
+        cudaFreeAsync(g->block, s);
+        return fail(ctx, LM_ECUDA, "graph build: a fill slot fell outside the edge arrays");
+    }
     *out = g.release();
     return LM_OK;
 }

@@ -775,7 +775,11 @@ __device__ void do_chunk_p(const SweepArgs& a, WarpStage& S, uint32_t t, uint32_
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(&len_next[v], (uint32_t)__popc(ball));
             base = __shfl_sync(FULL, base, 0);
-            if (key != 0) {
+            // the survivors of all chunks fit the row's L slots; a cursor that was not
+            // reset to 0 before this sweep would carry the writes past the row
+            if (base + (uint32_t)__popc(ball) > L) {
+                if (lane == 0) set_err(a.st, ERR_BOUNDS, v);
+            } else if (key != 0) {
                 const uint32_t pos = s0 + base + __popc(ball & lt);
                 a.out_key[pos] = stored_word<RENEW>(ck0, ck1, key);
                 a.out_nbr[pos] = u;
@@ -1406,7 +1410,8 @@ __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const fl
     }
 }
 __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword) {
+                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword,
+                             uint32_t* err) {
     const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
     const uint32_t mr = (m + 31) & ~31u;
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < mr; e += stride) {
@@ -1423,7 +1428,11 @@ __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float
         }
         const uint32_t pu = warp_add(&cursor[u], u, ok, lane);
         const uint32_t pv = warp_add(&cursor[v], v, ok, lane);
-        if (ok) {
+        // the cursors start at the row offsets and the degrees were counted from the
+        // same edges, so every slot is below 2m; a stale cursor is reported, not written
+        if (ok && (pu >= 2 * m || pv >= 2 * m)) {
+            atomicOr(err, 2u);
+        } else if (ok) {
             nbr[pu] = v;
             pk[pu] = word;
             nbr[pv] = u;
@@ -1749,9 +1758,10 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
     return (int)cudaGetLastError();
 }
 int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword) {
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword,
+                      uint32_t* err) {
     k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, pk, edges,
-                                                                     eword);
+                                                                     eword, err);
     return (int)cudaGetLastError();
 }
 int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t* flags) {
