@@ -105,6 +105,19 @@ def test_grid_config(lmctx, unit):
     _check(lmctx, g, 102)
 
 
+@pytest.mark.parametrize("fam,n,alpha", [("rgg", 1 << 15, 0), ("random", 1 << 13, 4),
+                                         ("random", 1 << 13, 16), ("random", 1 << 12, 64)])
+@pytest.mark.parametrize("ctx", ["lmctx", "lmgraph"])
+def test_paper_sweep_families(request, ctx, fam, n, alpha):
+    # the families of the Sec. 3 sweep: random geometric graphs (radius
+    # 0.55 sqrt(ln n / n)) and random graphs with alpha n edges, through the
+    # profiled launches and through the CUDA graph the benchmark times
+    g = synth.rgg(n, 20) if fam == "rgg" else synth.er(n, alpha * n, seed=30)
+    assert g.m > 0
+    mate, st = _check(request.getfixturevalue(ctx), g, 104)
+    assert is_matching(g.n, g.eu, g.ev, mate) and is_maximal(g.eu, g.ev, mate)
+
+
 def test_rows_spanning_many_tiles(lmctx):
     # a star whose centre row covers ~50 tiles, plus a second hub and a path,
     # so rows start and end at every position relative to tile boundaries
