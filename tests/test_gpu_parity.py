@@ -84,6 +84,19 @@ def test_host_and_device_outputs_agree(lmctx):
     assert (a == c).all()
 
 
+@pytest.mark.parametrize("m", [1, 31, 33, 255, 257, 4099])
+def test_host_upload_in_chunks(lmctx, m):
+    # graphs from host arrays go up in eight chunks of a multiple of 32 edges,
+    # each chunk's degrees counted as it lands: sizes around that rounding
+    g = synth.pairs(max(4, m // 3), m, m, "uniform")
+    h = lmctx.graph(g, device=False)
+    try:
+        mate, _ = lmctx.match(g, 8, handle=h)
+    finally:
+        lmctx.lm.lm_graph_destroy(h)
+    assert np.array_equal(mate, oracle.greedy(g.n, g.eu, g.ev, g.w, 8))
+
+
 def test_seed_changes_unit_weight_result(lmctx):
     g = synth.er(2000, 8000, 3, unit=True)
     a, _ = _check(lmctx, g, 1)
