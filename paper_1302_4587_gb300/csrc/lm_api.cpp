@@ -794,6 +794,12 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     gc.add(&g->eword, (size_t)g->m + 4);
     ce = cudaMallocFromPoolAsync(&g->block, gc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
+    // every return before the graph is handed out gives the block back
+    struct BlockFree {
+        std::unique_ptr<lm_graph>& g;
+        cudaStream_t s;
+        ~BlockFree() { if (g && g->block) cudaFreeAsync(g->block, s); }
+    } bf{g, s};
     gc.assign(g->block);
     g->bytes = gc.total;
     LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
@@ -808,10 +814,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
         LM_CK(ctx, launch_build_tilemap(s, g->roff, g->nrows, g->nent, g->tmap, g->rbits, g->tdesc));
     }
     LM_CK(ctx, cudaStreamSynchronize(s));
-    if (m > 0 && (hp[2] & 2u)) {
-        cudaFreeAsync(g->block, s);
-        return fail(ctx, LM_ECUDA, "graph build: a fill slot fell outside the edge arrays");
-    }
+    if (m > 0 && (hp[2] & 2u)) return fail(ctx, LM_ECUDA, "graph build: a fill slot fell outside the edge arrays");
     *out = g.release();
     return LM_OK;
 }
