@@ -900,6 +900,7 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     c.cev = cev;
     c.cw = cw;
     if (m >= (1u << 31)) return fail(ctx, LM_EINVAL, "too many edges");
+    if (n == 0xFFFFFFFFu) return fail(ctx, LM_EINVAL, "n must be below 2^32 - 1");
     const uint32_t scan_count = (n > m ? n : m) + 1;
     c.scan_words = exclusive_scan_tmp_words(scan_count);
     const size_t hist_words = contract_sort_tmp_words(m);
