@@ -29,6 +29,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "input edges/s to maximal matching"
+METRIC_BATCH = "graphs/s (batched, 4096 mixed graphs)"
+METRIC_SERVE = "graphs/s (served, saturation)"
+METRIC_CONTRACT = "input edges/s contracted (matching contraction)"
+METRIC_COARSEN = "input edges/s coarsened (8 levels of match + contract)"
+METRIC_SWEEP = "speedup of lm_match over the sequential local max (max over the sweep)"
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
 # an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
@@ -377,7 +382,7 @@ def run_batch(args, ws, rank, local):
     lm.lm_destroy(ctx)
     gps = len(gs) / (ms * 1e-3)
     return {
-        "metric": "graphs/s (batched, 4096 mixed graphs)", "value": ws * gps, "unit": "graphs/s", "n_gpus": ws,
+        "metric": METRIC_BATCH, "value": ws * gps, "unit": "graphs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
         "config": {"workload": "batch", "graphs": len(gs), "sum_m": m_tot, "sum_n": sum(g.n for g in gs),
@@ -474,7 +479,7 @@ def run_serve(args, ws, rank, local):
         lm.lm_graph_destroy(h)
     lm.lm_destroy(ctx)
     return {
-        "metric": "graphs/s (served, saturation)", "value": ws * cap, "unit": "graphs/s", "n_gpus": ws,
+        "metric": METRIC_SERVE, "value": ws * cap, "unit": "graphs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": 1, "ms_per_step": span0 * 1e3 / nreq, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
         "config": {"workload": "serve", "requests_per_point": nreq, "pool_graphs": len(pool),
@@ -525,7 +530,7 @@ def run_contract(args, ws, rank, local):
     algo = 12 * g.m + 8 * g.n + 12 * m2
     ach = algo / (ms * 1e-3) / 1e9
     lm.lm_destroy(ctx)
-    return {"metric": "input edges/s contracted (matching contraction)", "value": whole_job_value(g.m, ws, ms),
+    return {"metric": METRIC_CONTRACT, "value": whole_job_value(g.m, ws, ms),
             "unit": "edges/s", "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 ids / f64 sums",
             "data": "synthetic",
@@ -596,7 +601,7 @@ def run_coarsen(args, ws, rank, local):
     _barrier(ws)
     ms = _barrier_max(e0.elapsed_time(e1) / steps, ws)
     lm.lm_destroy(ctx)
-    return {"metric": "input edges/s coarsened (8 levels of match + contract)", "value": whole_job_value(g.m, ws, ms),
+    return {"metric": METRIC_COARSEN, "value": whole_job_value(g.m, ws, ms),
             "unit": "edges/s", "n_gpus": ws, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 ids / f64 sums",
             "data": "synthetic",
@@ -655,7 +660,7 @@ def run_paper_sweep(args, ws, rank, local):
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     lm.lm_destroy(ctx)
     best = max(r["speedup"] for r in rows)
-    return {"metric": "speedup of lm_match over the sequential local max (max over the sweep)", "value": best,
+    return {"metric": METRIC_SWEEP, "value": best,
             "unit": "x", "n_gpus": ws, "steps": args.steps, "warmup": 3, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)",
             "data": "synthetic", "config": {"workload": "paper_sweep",
@@ -665,52 +670,124 @@ def run_paper_sweep(args, ws, rank, local):
             "table": rows}
 
 
-def cpu_baseline(budget_s: float = 20.0):
-    """The oracle (greedy, one thread) on a bounded sample of the workload: an
-    R-MAT graph of the same family at scale 20.  Beside it, the literal
-    sequential local max of Sec. 2 (one thread) on the same sample, the
-    sequential code the paper compares its GPU version with (Sec. 3.3)."""
-    import oracle
+def cpu_sample(workload: str):
+    """The graph the CPU-side timings use for a single-graph workload, its match
+    seed and a description: the workload itself where the oracle finishes it in
+    about a second (ER, grid), else an R-MAT graph of the same family and weight
+    kind at scale 20, a bounded sample."""
     import synth
-    g = synth.rmat(scale=20, edge_factor=16, seed=3)
+    if workload in ("er", "grid"):
+        g, seed, desc = make_workload(workload)
+        return g, seed, f"the whole workload: {desc} (m={g.m})"
+    unit = workload == "rmat23_unit"
+    g = synth.rmat(scale=20, edge_factor=16, seed=3, unit=unit)
+    return g, 103, (f"R-MAT scale 20 ef 16{', unit weights' if unit else ''} (m={g.m}), "
+                    "a bounded sample of the R-MAT family")
+
+
+def oracle_match(g, seed: int, renewed: bool):
+    """The oracle's matching of g: greedy under the fixed order, or the literal
+    round-by-round local max when the perturbation is renewed every round."""
+    import oracle
+    if renewed:
+        return oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed, renew=True)[0]
+    return oracle.greedy(g.n, g.eu, g.ev, g.w, seed)
+
+
+def cpu_baseline(workload: str = "rmat23", renewed: bool = False, budget_s: float = 20.0):
+    """The oracle (one thread) on the workload's CPU sample.  Beside it, under the
+    fixed order, the literal sequential local max of Sec. 2 (one thread) on the
+    same graph, the sequential code the paper compares its GPU version with
+    (Sec. 3.3)."""
+    import oracle
+    g, seed, desc = cpu_sample(workload)
     reps, t_tot = 0, 0.0
     while reps < 1 or (t_tot < budget_s * 0.4 and reps < 3):
         t0 = time.perf_counter()
-        oracle.greedy(g.n, g.eu, g.ev, g.w, 103)
+        oracle_match(g, seed, renewed)
         t_tot += time.perf_counter() - t0
         reps += 1
     per = t_tot / reps
-    t0 = time.perf_counter()
-    oracle.seq_local_max(g.n, g.eu, g.ev, g.w, 103)
-    per_lm = time.perf_counter() - t0
-    return {"value": g.m / per, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"R-MAT scale 20 ef 16 (m={g.m}), greedy oracle, {reps} run(s), {per:.2f} s each",
-            "sequential_local_max": {"value": g.m / per_lm, "unit": "edges/s", "cores": 1,
-                                     "sample": f"same graph, three-pass sequential local max (Sec. 2), {per_lm:.2f} s"}}
+    name = "renewed-order sequential local max (the oracle of that order)" if renewed else "greedy oracle"
+    out = {"value": g.m / per, "unit": "edges/s", "cores": 1, "kind": "oracle",
+           "sample": f"{desc}, {name}, {reps} run(s), {per:.3f} s each"}
+    if not renewed:
+        t0 = time.perf_counter()
+        oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed)
+        per_lm = time.perf_counter() - t0
+        out["sequential_local_max"] = {"value": g.m / per_lm, "unit": "edges/s", "cores": 1,
+                                       "sample": f"same graph, three-pass sequential local max (Sec. 2), {per_lm:.3f} s"}
+    return out
 
 
 def run_reference(args, ws, rank):
+    """The oracle as it stands, on one core of this host, for the workload and
+    metric the CUDA arm reports; each step is one pass over a bounded sample of
+    the workload.  Rank 0 alone runs it; other ranks return without work."""
     if rank != 0:
         return None
     import oracle
     import synth
-    g = synth.rmat(scale=20, edge_factor=16, seed=3)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.greedy(g.n, g.eu, g.ev, g.w, 103)
+    wl = args.workload
+    renewed = args.order == "renewed"
+    unit = "edges/s"
+    if wl == "paper_sweep":
+        # the sweep's metric is a ratio over the sequential local max, which is this arm
+        return {"impl": "reference", "metric": METRIC_SWEEP, "value": 1.0, "unit": "x", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)",
+                "data": "synthetic", "config": {"workload": wl, "sample": "none: the sequential local max against itself"},
+                "cpu_baseline": {"value": 1.0, "unit": "x", "cores": 1, "kind": "oracle",
+                                 "sample": "the sweep's sequential local max is the unit of its metric"},
+                "e2e": {"value": 1.0, "unit": "x", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if wl == "batch":
+        gs = synth.batch(256, seed=4)  # the first 256 graphs of the 4096-graph batch
+        metric, unit, units = METRIC_BATCH, "graphs/s", len(gs)
+        sample = f"the first 256 of the 4096 mixed graphs (m = {sum(g.m for g in gs)}), greedy oracle per graph"
+        step = lambda: [oracle_match(g, 1000 + i, renewed) for i, g in enumerate(gs)]
+    elif wl == "serve":
+        pool = [synth.request_graph(*sz, name=f"r{i}") for i, sz in enumerate(synth.request_sizes(48, seed=5))]
+        metric, unit, units = METRIC_SERVE, "graphs/s", len(pool)
+        sample = f"the 48 request graphs of the served stream (m = {sum(g.m for g in pool)}), greedy oracle per graph"
+        step = lambda: [oracle_match(g, 2000 + i, renewed) for i, g in enumerate(pool)]
+    elif wl == "contract":
+        g = synth.rmat(scale=20, edge_factor=16, seed=3)
+        mate = oracle.greedy(g.n, g.eu, g.ev, g.w, 103)  # the matching, untimed as on the GPU
+        metric, units = METRIC_CONTRACT, g.m
+        sample = f"R-MAT scale 20 ef 16 (m={g.m}), the oracle's contraction of its greedy matching"
+        step = lambda: oracle.contract(g.n, g.eu, g.ev, g.w, mate)
+    elif wl == "coarsen":
+        g = synth.rmat(scale=18, edge_factor=16, seed=3)
+        metric, units = METRIC_COARSEN, g.m
+        sample = f"R-MAT scale 18 ef 16 (m={g.m}), eight levels of greedy oracle and oracle contraction"
+
+        def step():
+            n, eu, ev, w, vw = g.n, g.eu, g.ev, g.w, None
+            for lev in range(8):
+                mate = oracle.greedy(n, eu, ev, w, 103 + lev)
+                _, cvw, eu, ev, w = oracle.contract(n, eu, ev, w, mate, vw)
+                n, vw = int(cvw.shape[0]), cvw
+    else:
+        g, seed, desc = cpu_sample(wl)
+        metric, units = METRIC, g.m
+        sample = f"{desc}, {'renewed-order sequential local max' if renewed else 'greedy oracle'} per step"
+        step = lambda: oracle_match(g, seed, renewed)
+    nsteps = max(1, min(args.steps, 5)) if wl == "coarsen" else args.steps  # as the CUDA arm's chain
+    for _ in range(min(args.warmup, 1)):
+        step()
     times = []
-    for _ in range(args.steps):
+    for _ in range(nsteps):
         t0 = time.perf_counter()
-        oracle.greedy(g.n, g.eu, g.ev, g.w, 103)
+        step()
         times.append(time.perf_counter() - t0)
     per = statistics.median(times)
-    v = g.m / per
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+    v = units / per
+    return {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": ws,
+            "steps": nsteps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": "R-MAT scale 20 ef 16 (bounded sample of the workload)"},
-            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"R-MAT scale 20 ef 16, m={g.m}, greedy oracle per step"},
-            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": wl, "order": args.order, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
@@ -731,16 +808,17 @@ def main():
     if args.algo == "edge" and args.order == "renewed":
         ap.error("the edge-centric path keeps the fixed order")
     ws, rank, local = _dist()
+    if args.impl == "reference":
+        # host cores only: rank 0 runs the oracle, the other ranks exit without work
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
     if ws > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    if args.impl == "reference":
-        out = run_reference(args, ws, rank)
-        if out is not None:
-            print(json.dumps(out), flush=True)
-        return
     if args.workload in ("batch", "serve", "paper_sweep", "contract", "coarsen"):
         out = {"batch": run_batch, "serve": run_serve, "paper_sweep": run_paper_sweep,
                "contract": run_contract, "coarsen": run_coarsen}[args.workload](args, ws, rank, local)
@@ -753,7 +831,7 @@ def main():
     out, g = run_lm(args, ws, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(args.workload, args.order == "renewed")
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
