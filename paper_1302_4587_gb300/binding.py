@@ -138,6 +138,36 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _out(a, count: int, what: str):
+    """(pointer, the buffer itself) of a caller-provided output of at least
+    `count` 4-byte elements, written in place: a contiguous, writable numpy
+    array or torch tensor (host or CUDA).  Anything else is refused here, since
+    the library writes `count` elements through the pointer."""
+    if isinstance(a, np.ndarray):
+        if a.dtype.itemsize != 4 or not a.flags.c_contiguous or not a.flags.writeable or a.size < count:
+            raise ValueError(f"{what}: needs a contiguous writable array of at least {count} 4-byte elements")
+        return a.ctypes.data, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.element_size() != 4 or not a.is_contiguous() or a.numel() < count:
+            raise ValueError(f"{what}: needs a contiguous tensor of at least {count} 4-byte elements")
+        return a.data_ptr(), a
+    raise TypeError(f"{what}: unsupported array type {type(a)}")
+
+
+# vertex count of each graph handle this binding created (output sizes are checked against it)
+_GRAPH_N: dict = {}
+
+
+def _handle(g) -> int:
+    return g.value if isinstance(g, ctypes.c_void_p) else int(g)
+
+
+def _graph_n(g) -> int:
+    n = _GRAPH_N.get(_handle(g))
+    return lm_graph_info(g)[0] if n is None else n
+
+
 def _as(a, np_dtype, torch_dtype):
     if a is None:
         return None
@@ -192,10 +222,13 @@ def lm_graph_create(ctx, n: int, eu, ev, w):
     mem = LM_DEVICE if du else LM_HOST
     out = ctypes.c_void_p()
     _check(lib.lm_graph_create(ctx, n, m, pu, pv, pw, mem, ctypes.byref(out)), ctx)
+    _GRAPH_N[out.value] = int(n)
     return out
 
 
 def lm_graph_destroy(g) -> None:
+    if g is not None:
+        _GRAPH_N.pop(_handle(g), None)
     load().lm_graph_destroy(g)
 
 
@@ -215,7 +248,7 @@ def lm_match(ctx, g, seed: int, mate=None, stats: bool = False):
         n = lm_graph_info(g)[0]
         dev = torch.cuda.current_device()
         mate = torch.empty(max(n, 1), dtype=torch.int32, device=f"cuda:{dev}")[:n]
-    p, keep, _ = _ptr(mate)
+    p, keep = _out(mate, _graph_n(g), "mate")
     st = LmStats()
     _check(lib.lm_match(ctx, g, seed & (2**64 - 1), p, ctypes.byref(st) if stats else None), ctx)
     return (keep, st.to_dict()) if stats else keep
@@ -234,8 +267,8 @@ class BatchArgs:
         self.graphs = (ctypes.c_void_p * cnt)(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in graphs])
         self.seeds = (ctypes.c_uint64 * cnt)(*[int(x) & (2**64 - 1) for x in seeds])
         ptrs, self.keep = [], []
-        for mt in mates:
-            p, k, _ = _ptr(mt)
+        for i, (g, mt) in enumerate(zip(graphs, mates)):
+            p, k = _out(mt, _graph_n(g), f"mates[{i}]")
             ptrs.append(p)
             self.keep.append(k)
         self.mates = (ctypes.c_void_p * cnt)(*ptrs)
@@ -253,7 +286,7 @@ def lm_batch_match(ctx, graphs, seeds=None, mates=None, stats: bool = False):
 
 
 def lm_submit(ctx, g, seed: int, mate) -> int:
-    p, _, _ = _ptr(mate)
+    p, _ = _out(mate, _graph_n(g), "mate")
     t = ctypes.c_uint64()
     _check(load().lm_submit(ctx, g, seed & (2**64 - 1), p, ctypes.byref(t)), ctx)
     return int(t.value)
@@ -287,6 +320,14 @@ def lm_contract(ctx, n: int, eu, ev, w, mate, vw=None):
     cev[m'], cw[m']) as CUDA tensors (views of buffers of n and m entries)."""
     import torch
     m = int(eu.shape[0])
+    # eu / ev / w hold exactly m edges; mate and vw cover at least the n vertices
+    for t, cnt, exact, what in ((eu, m, True, "eu"), (ev, m, True, "ev"), (w, m, True, "w"),
+                                (mate, n, False, "mate"), (vw, n, False, "vw")):
+        if t is None:
+            continue
+        if (not isinstance(t, torch.Tensor) or t.element_size() != 4 or not t.is_contiguous()
+                or (t.numel() != cnt if exact else t.numel() < cnt)):
+            raise ValueError(f"{what}: needs a contiguous tensor of {'' if exact else 'at least '}{cnt} 4-byte elements")
     dev = eu.device if m else mate.device
     cmap = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     cvw = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
@@ -316,8 +357,10 @@ def lm_match_small_noalloc(n: int, eu, ev, w, seed: int, mate, status, stream=No
     if int(ev.numel()) != m or int(w.numel()) != m:
         raise ValueError("eu, ev and w differ in length")
     for t in (eu, ev, w, mate, status):
-        if not (t.is_cuda and t.is_contiguous()):
-            raise ValueError("lm_match_small_noalloc takes contiguous CUDA tensors")
+        if not (t.is_cuda and t.is_contiguous() and t.element_size() == 4):
+            raise ValueError("lm_match_small_noalloc takes contiguous CUDA tensors of 4-byte elements")
+    if int(mate.numel()) < n or int(status.numel()) < 1:
+        raise ValueError("mate needs n entries and status one")
     if stream is None:
         s = None
     elif isinstance(stream, int):

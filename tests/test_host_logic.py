@@ -47,3 +47,99 @@ def test_kernels_compile_for_sm103a():
     assert out.returncode == 0, out.stderr
     for k in ("k_vertex", "k_sweep", "k_init"):
         assert k in out.stderr
+
+
+def test_output_buffers_are_checked_before_any_call():
+    # the library writes n 4-byte elements through an output pointer: the
+    # binding refuses buffers that are short, of another element size,
+    # strided or read-only instead of handing them over
+    import numpy as np
+    import torch
+    from paper_1302_4587_gb300 import binding as B
+    ok = np.empty(5, np.uint32)
+    assert B._out(ok, 5, "mate")[1] is ok
+    B._out(np.empty(6, np.int32), 5, "mate")  # longer is fine
+    for bad in (np.empty(4, np.uint32), np.empty(5, np.int64), np.empty(10, np.uint32)[::2],
+                np.frombuffer(bytes(20), np.uint32)):
+        with pytest.raises(ValueError):
+            B._out(bad, 5, "mate")
+    t = torch.empty(5, dtype=torch.int32)
+    assert B._out(t, 5, "mate")[1] is t
+    for bad in (torch.empty(4, dtype=torch.int32), torch.empty(5, dtype=torch.int64),
+                torch.empty(10, dtype=torch.int32)[::2]):
+        with pytest.raises(ValueError):
+            B._out(bad, 5, "mate")
+    with pytest.raises(TypeError):
+        B._out([0] * 5, 5, "mate")
+
+
+def test_contraction_arguments_are_checked_before_any_call():
+    import torch
+    from paper_1302_4587_gb300 import binding as B
+    i32 = lambda k: torch.zeros(k, dtype=torch.int32)
+    f32 = lambda k: torch.zeros(k, dtype=torch.float32)
+    for args in ((i32(2), i32(3), f32(2), i32(3)),                         # ev longer than eu
+                 (i32(2), i32(2), torch.zeros(2, dtype=torch.float64), i32(3)),  # 8-byte weights
+                 (i32(2), i32(2), f32(2), i32(2)),                         # mate shorter than n
+                 (i32(4)[::2], i32(2), f32(2), i32(3))):                   # strided endpoints
+        with pytest.raises(ValueError):
+            B.lm_contract(None, 3, *args)
+    with pytest.raises(ValueError):
+        B.lm_contract(None, 3, i32(2), i32(2), f32(2), i32(3), vw=i32(2))  # vertex weights short
+
+
+class _FakeLib:
+    """Stands in for the CUDA library: records calls, fills out-parameters."""
+
+    def __init__(self):
+        self.calls = []
+
+    def lm_graph_create(self, ctx, n, m, pu, pv, pw, mem, out):
+        out._obj.value = 0x1000 + n
+        self.calls.append(("create", n, m, mem))
+        return 0
+
+    def lm_graph_destroy(self, g):
+        self.calls.append(("destroy", g.value))
+
+    def lm_graph_info(self, g, n, m, b):
+        n._obj.value, m._obj.value, b._obj.value = 9, 0, 0
+        return 0
+
+    def lm_match(self, ctx, g, seed, p, st):
+        self.calls.append(("match", g.value, p))
+        return 0
+
+    def lm_batch_match(self, ctx, gs, count, seeds, mates, st):
+        self.calls.append(("batch", count))
+        return 0
+
+    def lm_submit(self, ctx, g, seed, p, t):
+        t._obj.value = 7
+        return 0
+
+
+def test_binding_marshals_graphs_and_outputs(monkeypatch):
+    import numpy as np
+    from paper_1302_4587_gb300 import binding as B
+    fake = _FakeLib()
+    monkeypatch.setattr(B, "load", lambda build=True: fake)
+    eu, ev = np.array([0, 1], np.uint32), np.array([1, 2], np.uint32)
+    h = B.lm_graph_create(None, 5, eu, ev, np.array([1, 2], np.float32))
+    assert fake.calls[-1] == ("create", 5, 2, B.LM_HOST)
+    mate = np.empty(5, np.uint32)
+    assert B.lm_match(None, h, 1, mate) is mate
+    assert fake.calls[-1] == ("match", h.value, mate.ctypes.data)
+    with pytest.raises(ValueError):
+        B.lm_match(None, h, 1, np.empty(4, np.uint32))
+    job = B.BatchArgs([h, h], [1, 2], [mate, np.empty(6, np.uint32)])
+    assert B.lm_batch_match(None, job)[0] is mate and fake.calls[-1] == ("batch", 2)
+    with pytest.raises(ValueError):
+        B.BatchArgs([h], [1], [np.empty(3, np.uint32)])
+    assert B.lm_submit(None, h, 3, mate) == 7
+    B.lm_graph_destroy(h)
+    assert fake.calls[-1] == ("destroy", h.value)
+    # a handle the binding no longer knows is sized through lm_graph_info (n = 9 here)
+    with pytest.raises(ValueError):
+        B.lm_match(None, h, 1, mate)
+    B.lm_match(None, h, 1, np.empty(9, np.uint32))
