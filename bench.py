@@ -37,8 +37,11 @@ METRIC_SWEEP = "speedup of lm_match over the sequential local max (max over the 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the k_sweep launches of one match, from
 # an ncu capture on R-MAT scale 21 scaled by the entries processed (R-MAT 23 is too large to
-# capture with several metrics); None for workloads without a capture of the current kernels
-TRAFFIC = {"rmat23": 6068360297}
+# capture with several metrics), for workloads with a capture of the current kernel
+TRAFFIC = {}
+# the last capture, taken before the chunk path of k_sweep checked its output slots (a
+# compare per 32-entry group; no load or store added); reported beside the roofline, not as it
+TRAFFIC_PRIOR = {"rmat23": 6068360297}
 
 
 def _peaks():
@@ -314,6 +317,7 @@ def run_lm(args, ws, rank, local):
                      {"bound": "hbm", "kernel": "k_sweep (all launches of one match)",
                       "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                       "frac": achieved / peak, "traffic": TRAFFIC.get(args.workload) if not order else None,
+                      "traffic_before_slot_check": TRAFFIC_PRIOR.get(args.workload) if not order else None,
                       "bytes_per_match": bytes_sweep, "ms_per_match": sw_ms,
                       "launches_per_match": pst["kernel_launches"][lm.LM_K_SWEEP],
                       "profiled_total_ms": statistics.median(total_ms)}),
