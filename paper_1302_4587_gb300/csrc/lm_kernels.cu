@@ -1881,8 +1881,7 @@ int launch_tail(void* stream, const JobArgs* dargs, const LaunchCfg& cfg) {
 
 static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, void* func, dim3 grid,
                               dim3 block, void** params, unsigned smem = 0) {
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
+    cudaKernelNodeParams kp{};
     kp.func = func;
     kp.gridDim = grid;
     kp.blockDim = block;
@@ -1984,7 +1983,7 @@ int launch_edge_round(void* stream, const EdgeArgs* d, int phase) {
 }
 
 // init -> while (live) { offer, match, compact, check }
-int build_edge_graph(const InitArgs* init, const EdgeArgs* dargs, DevState* st, void** exec_out) {
+int build_edge_graph(const InitArgs* init, const EdgeArgs* dargs, DevState* /*st*/, void** exec_out) {
     *exec_out = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
