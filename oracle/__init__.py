@@ -1,8 +1,8 @@
 """ORACLE -- test infrastructure only.
 
 A plain CPU restatement of what the local-max matching path computes, used by
-``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg,
-and by nothing else.  It shares no code with the CUDA library and never
+``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline and
+reference legs, and by nothing else.  It shares no code with the CUDA library and never
 imports it.  The arithmetic lives in ``oracle.c`` (plain C, compiled on first
 use into ``oracle/_build/``); this module only marshals numpy arrays.
 
@@ -12,7 +12,9 @@ Passages followed (see the header of ``oracle.c`` for each function):
   * ``greedy``        -- Sec. 3, the greedy algorithm (the oracle for mate[]);
   * ``seq_local_max`` -- Sec. 2, sequential model, three passes per iteration;
   * ``brute_mwm``     -- exact maximum weight matching for small n, used for
-    the 1/2-approximation property (Sec. 1).
+    the 1/2-approximation property (Sec. 1);
+  * ``contract``      -- contraction of a matching into the coarser graph, the
+    multilevel step that motivates the matching (Sec. 1).
 """
 from __future__ import annotations
 

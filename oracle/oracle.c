@@ -3,7 +3,8 @@
  *
  * Plain, slow, obviously correct CPU code for what the local-max matching
  * path computes.  Only the tests, the smoke check and the benchmark's CPU
- * baseline may load this file's library; the product path never does.  It
+ * baseline and reference legs may load this file's library; the product path
+ * never does.  It
  * shares no code with the CUDA library: the edge order, the permutation and
  * both matching algorithms below are written out here on their own.
  *
