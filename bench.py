@@ -698,6 +698,30 @@ def oracle_match(g, seed: int, renewed: bool):
     return oracle.greedy(g.n, g.eu, g.ev, g.w, seed)
 
 
+def _host_cpu() -> dict:
+    """The host's core count and CPU model (from /proc/cpuinfo where it names one)."""
+    import platform
+    model, impl, part = "", "", ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip().lower(), v.strip()
+            if k in ("model name", "cpu model") and v and not model:
+                model = v
+            elif k == "cpu implementer" and not impl:
+                impl = v
+            elif k == "cpu part" and not part:
+                part = v
+    except OSError:
+        pass
+    if not model and impl:
+        # Arm cores name themselves by implementer and part number only
+        known = {("0x41", "0xd4f"): "Arm Neoverse V2", ("0x41", "0xd40"): "Arm Neoverse V1",
+                 ("0x41", "0xd0c"): "Arm Neoverse N1", ("0x41", "0xd49"): "Arm Neoverse N2"}
+        model = known.get((impl.lower(), part.lower()), f"Arm implementer {impl} part {part}")
+    return {"nproc": os.cpu_count(), "cpu": model or platform.machine(), "arch": platform.machine()}
+
+
 def cpu_baseline(workload: str = "rmat23", renewed: bool = False, budget_s: float = 20.0):
     """The oracle (one thread) on the workload's CPU sample.  Beside it, under the
     fixed order, the literal sequential local max of Sec. 2 (one thread) on the
@@ -714,7 +738,7 @@ def cpu_baseline(workload: str = "rmat23", renewed: bool = False, budget_s: floa
     per = t_tot / reps
     name = "renewed-order sequential local max (the oracle of that order)" if renewed else "greedy oracle"
     out = {"value": g.m / per, "unit": "edges/s", "cores": 1, "kind": "oracle",
-           "sample": f"{desc}, {name}, {reps} run(s), {per:.3f} s each"}
+           "sample": f"{desc}, {name}, {reps} run(s), {per:.3f} s each", "host": _host_cpu()}
     if not renewed:
         t0 = time.perf_counter()
         oracle.seq_local_max(g.n, g.eu, g.ev, g.w, seed)
@@ -790,7 +814,8 @@ def run_reference(args, ws, rank):
             "steps": nsteps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64 keys / u32 ids (integer)", "data": "synthetic",
             "config": {"workload": wl, "order": args.order, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": _host_cpu()},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
