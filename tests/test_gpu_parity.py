@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from gpu_util import NIL, Lm, to_u32
-from helpers import dominated, is_matching, is_maximal, load_hand_cases
+from helpers import is_matching, is_maximal, load_hand_cases
 
 pytestmark = pytest.mark.gpu
 
