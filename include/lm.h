@@ -179,6 +179,28 @@ int  lm_poll(lm_ctx* ctx, uint64_t ticket, int* done, lm_stats* stats);
  * ticket stays valid).  Does not release the ticket: call lm_poll after. */
 int  lm_wait(lm_ctx* ctx, uint64_t ticket, uint32_t timeout_ms);
 
+/* Limits of every later lm_match / lm_batch_match on the context (and of served
+ * requests that run alone).  Sec. 2 bounds the rounds of local max by O(log m)
+ * only in expectation; with a fixed order a graph can need Theta(n) rounds (a
+ * path with monotone weights), so a caller who must bound how long the GPU is
+ * held sets either limit:
+ *   max_rounds     the match gives up with LM_ETIMEOUT once it has run more than
+ *                  this many rounds without emptying the edge set (0 = no cap
+ *                  beyond m + 2, which a match never reaches: every round matches
+ *                  the heaviest live edge).  Checked after every second round,
+ *                  so up to one round more may run.
+ *   time_limit_ms  the match gives up with LM_ETIMEOUT once its rounds have run
+ *                  longer than this (0 = 120 s).  Checked with the cap.
+ * A match that gives up leaves mate undefined; the context stays usable.
+ * Errors: LM_EINVAL (null ctx). */
+int  lm_set_limits(lm_ctx* ctx, uint32_t max_rounds, uint32_t time_limit_ms);
+
+/* Fault injection for tests of the error paths (read by lm_create from the
+ * environment; nothing on the GPU is made to fail):
+ *   LM_FAULT=alloc      every device allocation the new context makes after
+ *                       lm_create fails as out of memory (calls return LM_ENOMEM)
+ *   LM_FAULT=alloc:N    only the next N of them fail. */
+
 /* Launch parameters of a context's matching path (the paper has no
  * counterpart; they only affect speed, never the result):
  *   rmax               rows with at most this many live entries are swept in
@@ -231,18 +253,24 @@ int  lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const ui
  *   eu, ev, w : device arrays uint32[m], uint32[m], float32[m] as in lm_graph_create
  *   mate      : device uint32[n]; when the kernel ends, v's partner or LM_NIL
  *   status    : device uint32[1]; when the kernel ends, 0 = ok, 1 = an edge had an
- *               endpoint >= n, a self loop or a NaN weight (then every mate[v]
- *               is LM_NIL), 2 = round cap exceeded (not expected)
+ *               endpoint >= n, a self loop or a NaN weight, 2 = round cap exceeded
+ *               (not expected: every round matches an edge); in both error cases
+ *               every mate[v] is LM_NIL
  *   stream    : cudaStream_t, NULL = the default stream
  * Nothing needs to start at zero: each call initialises the scratch it reads.
  * There is one scratch per device, so two calls on one device whose kernels
  * can overlap (different streams, or threads without ordering) race on it and
  * corrupt each other's results: order them, e.g. issue them on one stream.
  * The first call on a device resolves the scratch's address there (with that
- * device current); make that first call before any stream capture on it.
+ * device current); make that first call before any stream capture on it.  The
+ * address is kept for the life of the process: after cudaDeviceReset (or any
+ * other teardown of the device's primary context) it is stale and further
+ * calls on that device are invalid.
+ * All five arrays must be global memory of the current device (checked with
+ * cudaPointerGetAttributes; eu, ev, w may be NULL when m = 0, mate when n = 0).
  * Errors (returned at once): LM_EINVAL (n or m beyond the limits, a null
- * pointer, current device index >= 64), LM_ECUDA (the address lookup or the
- * launch failed). */
+ * pointer, an array that is not memory of the current device, current device
+ * index >= 64), LM_ECUDA (the address lookup or the launch failed). */
 #define LM_NOALLOC_MAX_N 65536u
 #define LM_NOALLOC_MAX_M 262144u
 #define LM_NOALLOC_SCRATCH_BYTES (9ull * LM_NOALLOC_MAX_N + 8ull * LM_NOALLOC_MAX_M)

@@ -11,7 +11,7 @@ from .binding import (LM_DEVICE, LM_EAGAIN, LM_ECUDA, LM_EINVAL, LM_ENOMEM, LM_E
                       LM_K_VERTEX, LM_NIL, LM_NOALLOC_MAX_M, LM_NOALLOC_MAX_N, LM_OK, EXPORTS, BatchArgs, LmError, LmStats,
                       lm_batch_match, lm_create, lm_destroy, lm_graph_create, lm_graph_destroy, lm_graph_info,
                       lm_match, lm_match_small_noalloc, lm_poll, lm_strerror, lm_submit, lm_wait, load,
-                      LmTuning, lm_autotune, lm_get_tuning, lm_set_tuning, lm_sync, lm_contract)
+                      LmTuning, lm_autotune, lm_get_tuning, lm_set_tuning, lm_sync, lm_contract, lm_set_limits)
 from ._build import build
 
 __all__ = [n for n in dir() if n.startswith(("lm_", "LM_"))] + ["BatchArgs", "LmError", "LmStats", "LmTuning", "EXPORTS", "load", "build"]

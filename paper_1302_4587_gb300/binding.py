@@ -28,7 +28,8 @@ LM_K_INIT, LM_K_SWEEP, LM_K_VERTEX, LM_K_CAND, LM_K_OTHER, LM_K_TAIL, LM_K_COUNT
 # names exported by include/lm.h (the loader checks that every one is present)
 EXPORTS = ("lm_create", "lm_destroy", "lm_graph_create", "lm_graph_destroy", "lm_graph_info", "lm_match",
            "lm_batch_match", "lm_submit", "lm_poll", "lm_wait", "lm_strerror", "lm_last_error",
-           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune", "lm_sync", "lm_contract")
+           "lm_match_small_noalloc", "lm_get_tuning", "lm_set_tuning", "lm_autotune", "lm_sync", "lm_contract",
+           "lm_set_limits")
 LM_NOALLOC_MAX_N, LM_NOALLOC_MAX_M = 65536, 262144
 
 
@@ -104,6 +105,7 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.lm_last_error.argtypes = [vp]
         lib.lm_last_error.restype = ctypes.c_char_p
         lib.lm_match_small_noalloc.argtypes = [u32, u32, vp, vp, vp, u64, vp, vp, vp]
+        lib.lm_set_limits.argtypes = [vp, u32, u32]
         lib.lm_get_tuning.argtypes = [vp, ctypes.POINTER(LmTuning)]
         lib.lm_set_tuning.argtypes = [vp, ctypes.POINTER(LmTuning)]
         lib.lm_autotune.argtypes = [vp, ctypes.POINTER(vp), u32, ctypes.POINTER(u64), ctypes.POINTER(vp),
@@ -356,9 +358,14 @@ def lm_match_small_noalloc(n: int, eu, ev, w, seed: int, mate, status, stream=No
     m = int(eu.numel())
     if int(ev.numel()) != m or int(w.numel()) != m:
         raise ValueError("eu, ev and w differ in length")
+    import torch
+    dev = torch.cuda.current_device()
     for t in (eu, ev, w, mate, status):
         if not (t.is_cuda and t.is_contiguous() and t.element_size() == 4):
             raise ValueError("lm_match_small_noalloc takes contiguous CUDA tensors of 4-byte elements")
+        if t.device.index != dev:
+            raise ValueError(f"lm_match_small_noalloc runs on the current device (cuda:{dev}); "
+                             f"a tensor lives on {t.device}")
     if int(mate.numel()) < n or int(status.numel()) < 1:
         raise ValueError("mate needs n entries and status one")
     if stream is None:
@@ -369,6 +376,13 @@ def lm_match_small_noalloc(n: int, eu, ev, w, seed: int, mate, status, stream=No
         s = stream.cuda_stream
     _check(lib.lm_match_small_noalloc(n, m, eu.data_ptr(), ev.data_ptr(), w.data_ptr(), seed & (2**64 - 1),
                                       mate.data_ptr(), status.data_ptr(), s))
+
+
+def lm_set_limits(ctx, max_rounds: int = 0, time_limit_ms: int = 0) -> None:
+    """Round cap and time limit of the context's later matches (0 = the defaults:
+    no cap beyond m + 2 rounds, 120 s); a match beyond either raises LmError
+    with code LM_ETIMEOUT."""
+    _check(load().lm_set_limits(ctx, max_rounds, time_limit_ms), ctx)
 
 
 def lm_get_tuning(ctx) -> dict:

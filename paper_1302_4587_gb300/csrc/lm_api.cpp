@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -67,6 +68,23 @@ int fail(lm_ctx* ctx, int code, const char* fmt, ...) {
         if (code == LM_ECUDA) ctx->poisoned = true;
     }
     return code;
+}
+
+bool fault_alloc(lm_ctx* ctx) {
+    if (!ctx) return false;
+    int64_t left = ctx->fault_alloc.load();
+    while (left != 0) {
+        if (left < 0 || ctx->fault_alloc.compare_exchange_weak(left, left - 1)) return true;
+    }
+    return false;
+}
+
+void job_limits(const lm_ctx* ctx, uint32_t nedges, uint32_t* max_rounds, unsigned long long* limit_ns) {
+    // every round matches at least the heaviest live edge, so m + 2 rounds never run out
+    uint32_t r = nedges + 2;
+    if (ctx && ctx->lim_rounds && ctx->lim_rounds < r) r = ctx->lim_rounds;
+    *max_rounds = r;
+    *limit_ns = (ctx && ctx->lim_ns) ? ctx->lim_ns : LOOP_LIMIT_NS;
 }
 
 int cuda_fail(lm_ctx* ctx, cudaError_t e, const char* where) {
@@ -194,7 +212,7 @@ int ensure_ws(lm_ctx* ctx, Engine& e, uint32_t nv, uint32_t ne, uint32_t ng) {
         w.block = nullptr;
     }
     void* p = nullptr;
-    cudaError_t err = cudaMalloc(&p, c.total);
+    cudaError_t err = fault_alloc(ctx) ? cudaErrorMemoryAllocation : cudaMalloc(&p, c.total);
     if (err != cudaSuccess) {
         cudaGetLastError();
         e.ws = Workspace();
@@ -313,7 +331,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
     A.init.bcnt = job.va.bcnt;
     A.init.bkey = job.va.bkey;
     A.init.n = job.va.nvert;
-    A.init.max_rounds = job.nedges + 2;
+    job_limits(ctx, job.nedges, &A.init.max_rounds, &A.init.limit_ns);
     A.init.st = e.st;
     auto vargs = [&](VertexArgs& v, int in_set, int out_set, uint32_t par, uint32_t match) {
         v.va = job.va;
@@ -417,7 +435,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
         prof.begin(LM_K_SWEEP);
         LM_CK(ctx, launch_sweep_live(s, &D->s[1], e.cfg));
         prof.end();
-        // the same limits as the device-driven loop: the round cap and LOOP_LIMIT_NS
+        // the same limits as the device-driven loop: the round cap and the time limit
         const auto t_start = std::chrono::steady_clock::now();
         for (uint32_t pair = 0;; pair++) {
             for (int k = 2; k < 4; k++) {
@@ -431,7 +449,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
-            if (e.st_host->round > job.nedges + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            if (e.st_host->round > A.init.max_rounds) return fail(ctx, LM_ETIMEOUT, "round cap reached");
             if (e.st_host->last_ent < TAIL_ENT) {  // as the loop check: the tail finishes the job
                 prof.begin(LM_K_TAIL);
                 LM_CK(ctx, launch_tail(s, D, e.cfg));
@@ -439,7 +457,7 @@ int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof) {
                 break;
             }
             const auto waited = std::chrono::steady_clock::now() - t_start;
-            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)LOOP_LIMIT_NS)
+            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)A.init.limit_ns)
                 return fail(ctx, LM_ETIMEOUT, "round loop exceeded its time limit");
         }
     }
@@ -487,7 +505,7 @@ int match_edges(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32
     A.init.bcnt = w.bcnt;
     A.init.bkey = w.bkey;
     A.init.n = g->n;
-    A.init.max_rounds = g->m + 2;
+    job_limits(ctx, g->m, &A.init.max_rounds, &A.init.limit_ns);
     A.init.st = e.st;
     const uint64_t z = splitmix64_first(seed);
     EdgeArgs& a = A.ea;
@@ -529,9 +547,9 @@ int match_edges(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32
             LM_CK(ctx, cudaMemcpyAsync(e.st_host, e.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             LM_CK(ctx, cudaStreamSynchronize(s));
             if (e.st_host->err || e.st_host->done) break;
-            if (e.st_host->round > g->m + 3) return fail(ctx, LM_ETIMEOUT, "round cap reached");
+            if (e.st_host->round > A.init.max_rounds) return fail(ctx, LM_ETIMEOUT, "round cap reached");
             const auto waited = std::chrono::steady_clock::now() - t_start;
-            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)LOOP_LIMIT_NS)
+            if (std::chrono::duration_cast<std::chrono::nanoseconds>(waited).count() > (long long)A.init.limit_ns)
                 return fail(ctx, LM_ETIMEOUT, "round loop exceeded its time limit");
         }
     }
@@ -640,6 +658,15 @@ int lm_create(const lm_config* cfg, lm_ctx** out) {
     ctx->max_slots = cfg->max_slots ? cfg->max_slots : 4096;
     ctx->flags = cfg->flags;
     ctx->eng.cfg.renew = (cfg->flags & LM_F_RENEW) != 0;
+    // host-side fault injection for tests of the error paths: LM_FAULT=alloc makes
+    // every later device allocation of this context fail, alloc:N the next N
+    if (const char* f = getenv("LM_FAULT")) {
+        if (!strncmp(f, "alloc", 5)) {
+            long long k = -1;
+            if (f[5] == ':') k = strtoll(f + 6, nullptr, 10);
+            ctx->fault_alloc = k;
+        }
+    }
     {
         cudaMemPoolProps pp;
         memset(&pp, 0, sizeof pp);
@@ -730,7 +757,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     tc.add(&scan_tmp, scan_words);
     tc.add(&err, 4);
     void* tmp = nullptr;
-    cudaError_t ce = cudaMallocFromPoolAsync(&tmp, tc.total, ctx->pool, s);
+    cudaError_t ce = fault_alloc(ctx) ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&tmp, tc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph staging");
     tc.assign(tmp);
     struct TmpFree {
@@ -792,7 +819,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     gc.add(&g->pk, (size_t)g->nent + 4);
     gc.add(&g->edges, (size_t)g->m + 2);
     gc.add(&g->eword, (size_t)g->m + 4);
-    ce = cudaMallocFromPoolAsync(&g->block, gc.total, ctx->pool, s);
+    ce = fault_alloc(ctx) ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&g->block, gc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph arrays");
     // every return before the graph is handed out gives the block back
     struct BlockFree {
@@ -927,7 +954,7 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
         if (e.cblock) cudaFree(e.cblock);
         e.cblock = nullptr;
         e.cbytes = 0;
-        if (cudaMalloc(&e.cblock, cv.total) != cudaSuccess) {
+        if (fault_alloc(ctx) || cudaMalloc(&e.cblock, cv.total) != cudaSuccess) {
             cudaGetLastError();
             e.cblock = nullptr;
             return fail(ctx, LM_ENOMEM, "contraction scratch of %zu bytes", cv.total);
@@ -1111,6 +1138,14 @@ void tuning_of(const LaunchCfg& c, lm_tuning* t) {
     t->ms = 0.0;
 }
 }  // namespace
+
+int lm_set_limits(lm_ctx* ctx, uint32_t max_rounds, uint32_t time_limit_ms) {
+    if (!ctx) return LM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->call_mu);
+    ctx->lim_rounds = max_rounds;
+    ctx->lim_ns = (uint64_t)time_limit_ms * 1000000ull;
+    return LM_OK;
+}
 
 int lm_get_tuning(const lm_ctx* ctx, lm_tuning* out) {
     if (!ctx || !out) return LM_EINVAL;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -95,6 +96,13 @@ struct lm_ctx {
     // count on the context's stream while the next chunk is in flight
     cudaStream_t up = nullptr;
     cudaEvent_t up_ev = nullptr;
+    // limits of every match (lm_set_limits): a round cap (0 = none beyond m + 2)
+    // and a time limit in ns (0 = LOOP_LIMIT_NS)
+    uint32_t lim_rounds = 0;
+    uint64_t lim_ns = 0;
+    // host-side fault injection read from LM_FAULT at lm_create: the next
+    // fault_alloc device allocations fail as out of memory (-1: all of them)
+    std::atomic<int64_t> fault_alloc{0};
 };
 
 // A device graph (Sec. 2.1 representation): per-vertex offsets V into the
@@ -122,6 +130,10 @@ struct lm_graph {
 namespace lm {
 
 int fail(lm_ctx* ctx, int code, const char* fmt, ...);
+// true when fault injection (LM_FAULT=alloc[:N]) makes the next device allocation fail
+bool fault_alloc(lm_ctx* ctx);
+// round cap and time limit (ns) of a job over `nedges` edges on this context
+void job_limits(const lm_ctx* ctx, uint32_t nedges, uint32_t* max_rounds, unsigned long long* limit_ns);
 int cuda_fail(lm_ctx* ctx, cudaError_t e, const char* where);
 bool is_device_ptr(const void* p);
 uint64_t splitmix64_first(uint64_t seed);

@@ -90,7 +90,8 @@ struct DevState {
     uint32_t round;           // next round of the device-driven loop
     uint32_t max_rounds;      // the device-driven loop stops (ERR_TIMEOUT) beyond this round ...
     uint32_t err_any;         // ERR_* bits of every job since the host last cleared them
-    unsigned long long t0_ns; // ... or LOOP_LIMIT_NS after the job started
+    unsigned long long t0_ns; // ... or limit_ns after the job started
+    unsigned long long limit_ns;
     unsigned long long live_ent;   // live entries seen by the running vertex pass
     unsigned long long matched2;   // matched vertices (= 2 |M|)
     unsigned long long last_ent;   // live entries the last vertex pass saw (its round's)
@@ -219,6 +220,7 @@ struct InitArgs {
     unsigned long long* bkey;
     uint32_t n;
     uint32_t max_rounds;
+    unsigned long long limit_ns;  // the job's time limit (ERR_TIMEOUT once exceeded)
     DevState* st;
 };
 struct JobArgs {
@@ -244,7 +246,7 @@ struct EdgeArgs {
     DevState* st;
 };
 
-constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s
+constexpr unsigned long long LOOP_LIMIT_NS = 120000000000ull;  // 120 s: the default time limit of a job
 // once a round starts with fewer live entries than this, the rounds that remain
 // run in one kernel of one CTA (no launch per round)
 #ifndef LM_TAIL_ENT

@@ -176,6 +176,7 @@ __global__ void k_init(const InitArgs* __restrict__ pa) {
             st->last_ent = ~0ull; st->tail = 0; st->tail_round = 0;
             st->round = 1;
             st->max_rounds = A.max_rounds;
+            st->limit_ns = A.limit_ns ? A.limit_ns : LOOP_LIMIT_NS;
             st->t0_ns = globaltimer_ns();
         }
     }
@@ -1365,7 +1366,7 @@ __global__ void k_ec_check(const EdgeArgs* __restrict__ pa, cudaGraphConditional
     unsigned int go = 1;
     if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) go = 0;
     else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
-             globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+             globaltimer_ns() - st->t0_ns > st->limit_ns) {
         set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
         go = 0;
     }
@@ -1812,13 +1813,13 @@ int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32
 // ---------------------------------------------------------------- device-driven loop
 // Decides whether the conditional loop of a job graph runs another pair of
 // rounds: not once the edge set is empty or an error was recorded; after the
-// round cap or LOOP_LIMIT_NS it records ERR_TIMEOUT and stops.
+// round cap or the job's time limit it records ERR_TIMEOUT and stops.
 __global__ void k_loop_check(DevState* st, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     unsigned int go = 1;
     if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) go = 0;
     else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
-             globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+             globaltimer_ns() - st->t0_ns > st->limit_ns) {
         set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
         go = 0;
     } else if (*reinterpret_cast<volatile unsigned long long*>(&st->last_ent) < TAIL_ENT) {
@@ -1863,7 +1864,7 @@ __global__ void __launch_bounds__(ST, 1) k_tail(const JobArgs* __restrict__ A, u
             s_go = 1;
             if (ld_volatile_u32(&st->done) || ld_volatile_u32(&st->err)) s_go = 0;
             else if (ld_volatile_u32(&st->round) > ld_volatile_u32(&st->max_rounds) ||
-                     globaltimer_ns() - st->t0_ns > LOOP_LIMIT_NS) {
+                     globaltimer_ns() - st->t0_ns > st->limit_ns) {
                 set_err(st, ERR_TIMEOUT, ld_volatile_u32(&st->round));
                 s_go = 0;
             }
@@ -2120,6 +2121,10 @@ __global__ void __launch_bounds__(NA_T, 1) k_match_small(uint32_t n, uint32_t m,
         cur ^= 1u;
         __syncthreads();
     }
+    __syncthreads();
+    // a round cap that tripped leaves no partial result behind: every vertex unmatched
+    if (s_err & 2u)
+        for (uint32_t v = tid; v < n; v += NA_T) mate[v] = NIL;
     if (tid == 0) *status = s_err;
 }
 
@@ -2143,6 +2148,20 @@ extern "C" int lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu
         return LM_ECUDA;
     }
     if (dev < 0 || dev >= NA_MAX_DEVICES) return LM_EINVAL;
+    // every array must be global memory of the current device: a pointer into host
+    // memory or into another GPU would be dereferenced by the kernel as it is
+    const void* arrays[5] = {eu, ev, w, mate, status};
+    const bool needed[5] = {m > 0, m > 0, m > 0, n > 0, true};
+    for (int i = 0; i < 5; i++) {
+        if (!needed[i]) continue;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, arrays[i]) != cudaSuccess) {
+            cudaGetLastError();
+            return LM_EINVAL;
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return LM_EINVAL;
+    }
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);

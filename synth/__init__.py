@@ -192,7 +192,7 @@ def batch(count: int = 4096, seed: int = 4, n_lo: int = 64, n_hi: int = 65536,
     """Mixed batch: n = floor(exp(U[ln n_lo, ln n_hi])), average degree d ~ U[d_lo, d_hi],
     target m = floor(n d / 2), generator chosen uniformly from {ER, grid, R-MAT}."""
     par = draws(derive(seed, 20), 4 * count)
-    out = []
+    shapes = []
     for i in range(count):
         x0, x1, x2, x3 = (par[4 * i + k] for k in range(4))
         n = int(math.floor(math.exp(math.log(n_lo) + _uniform(x0) * (math.log(n_hi) - math.log(n_lo)))))
@@ -200,10 +200,21 @@ def batch(count: int = 4096, seed: int = 4, n_lo: int = 64, n_hi: int = 65536,
         d = d_lo + _uniform(x1) * (d_hi - d_lo)
         m = int(math.floor(n * d / 2))
         m = min(m, n * (n - 1) // 2)
-        kind = int(_uniform(x2) * 3)
-        gseed = int(x3)
-        out.append(_graph_of_kind(kind, n, m, gseed, f"b{i}"))
-    return out
+        shapes.append((int(_uniform(x2) * 3), n, m, int(x3), f"b{i}"))
+    return _generate(shapes)
+
+
+def _generate(shapes, threads: int | None = None) -> list[Graph]:
+    """Graphs of the given (kind, n, m, graph seed, name) shapes.  Each graph
+    depends on its own shape only, so they are drawn on a thread pool (the C
+    generators release the interpreter lock) with the same result as one by one."""
+    from concurrent.futures import ThreadPoolExecutor
+    if threads is None:
+        threads = min(32, os.cpu_count() or 1)
+    if threads <= 1 or len(shapes) < 2:
+        return [_graph_of_kind(*s) for s in shapes]
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda s: _graph_of_kind(*s), shapes))
 
 
 def _graph_of_kind(kind: int, n: int, m: int, gseed: int, name: str) -> Graph:
@@ -243,6 +254,11 @@ def request_sizes(count: int, seed: int = 5, m_lo: float = 1e3, m_hi: float = 4e
 
 def request_graph(kind: int, n: int, m: int, gseed: int, name: str = "req") -> Graph:
     return _graph_of_kind(kind, n, m, gseed, name)
+
+
+def request_pool(count: int, seed: int = 5, m_lo: float = 1e3, m_hi: float = 4e6) -> list[Graph]:
+    """The graphs of request_sizes(count, seed, m_lo, m_hi), named r0, r1, ..."""
+    return _generate([(*sz, f"r{i}") for i, sz in enumerate(request_sizes(count, seed, m_lo, m_hi))])
 
 
 def arrivals(count: int, rate_per_s: float, seed: int = 5) -> np.ndarray:
