@@ -863,12 +863,17 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
 // bitmap into a shared-memory stage with bulk asynchronous copies completed on
 // the stage's "full" mbarrier; tile descriptors (precomputed per graph) are
 // loaded R0AHEAD tiles early and the copies run up to R0S stages ahead of the
-// consumers.  The consumer warps derive each entry's row from the bitmap
-// (prefix counts of row starts), maximise keys per row in shared memory, and
-// let the entry holding a row's maximum name the row's candidate.  Only the
-// first and the last row of a tile can be cut by a tile boundary: their maxima
-// meet in bkey[] and k_round0_cut resolves them after the pass.  A stage goes
-// back to the producer through its "empty" mbarrier; every wait is bounded.
+// consumers.  Each consumer lane takes 4 consecutive entries of the tile and
+// derives their rows from the bitmap.  A row's candidate is its entry of
+// largest key K = ord(w) << 32 | perm_seed(e); the maximum is taken on ord(w)
+// alone (32-bit, no hashing), per lane, then per row across the lanes of a
+// warp by a segmented scan, then per row across warps with one shared-memory
+// atomic where a row ends; the entries that reach their row's maximum ord
+// claim the row, and only a row claimed twice (equal weights) compares
+// perm_seed of its tied entries.  Only the first and the last row of a tile
+// can be cut by a tile boundary: their maxima meet in bkey[] and k_round0_cut
+// resolves them after the pass.  A stage goes back to the producer through its
+// "empty" mbarrier; every wait is bounded.
 
 #ifndef LM_R0S
 #define LM_R0S 2
@@ -882,13 +887,11 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
 constexpr int R0S = LM_R0S;                         // pipeline stages
 constexpr int R0C = LM_R0C;                         // consumer threads
 constexpr int R0T = R0C + 32;                       // and one producer warp (one thread of it works)
-constexpr int R0G = (int)TILE0 / R0C;               // 32-entry groups per consumer warp
 constexpr int R0RPT = ((int)TILE0 + 1 + R0C - 1) / R0C;  // rows per consumer thread when finishing
 constexpr int R0W = (int)TILE0 / 32;                // bitmap words of a tile
-constexpr int R0WPL = R0W / 32;                     // bitmap words per lane in the consumers' scan
 constexpr int R0AHEAD = 4;                          // tile descriptors in flight ahead of the copies
-static_assert(TILE0 % 1024 == 0, "tile size: a multiple of 1024 entries");
-static_assert(R0C % 32 == 0 && TILE0 % R0C == 0 && R0G >= 1, "consumer warps must split the tile in 32-entry groups");
+static_assert(TILE0 == 1024 && R0C == 256, "each consumer lane takes 4 entries of a 1024-entry tile");
+static_assert(R0W == 32, "one bitmap word per lane");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -943,10 +946,13 @@ struct alignas(16) R0Stage {
     // written by the producer before the copies are issued
     uint32_t valid, seg, j0, nent, shift;
 };
+constexpr uint32_t R0_EMPTY = 0xFFFFFFFFu;  // rwin: no claim yet
+constexpr uint32_t R0_TIED = 0xFFFFFFFEu;   // rwin: claimed twice, perm_seed decides
 struct R0Smem {
     R0Stage stage[R0S];
-    unsigned long long kmax[TILE0 + 1];   // per row of the current tile: heaviest key
-    uint32_t knbr[TILE0 + 1];             // per row: neighbour over that entry
+    uint32_t rord[TILE0 + 1];    // per row of the current tile: largest ord(w) (0 between tiles)
+    uint32_t rwin[TILE0 + 1];    // per row: tile position of its heaviest entry, R0_EMPTY or R0_TIED
+    uint32_t rperm[TILE0 + 1];   // per tied row: largest perm_seed among its entries of ord rord (0 between tiles)
     unsigned long long full[R0S], empty[R0S];
 };
 
@@ -1036,10 +1042,50 @@ __device__ void r0_producer(R0Smem& s, const Round0Args& a) {
     }
 }
 
+// lane-local maxima of ord over a lane's 4 entries, one slot per row segment of
+// the lane: segment t holds the entries after the t-th row start inside the lane
+struct R0Lane {
+    uint32_t bo[4];    // largest ord of segment t (0: none)
+    uint32_t bj;       // 2 bits per segment: lane position of that entry
+    uint32_t tie;      // bit t: two entries of segment t share the largest ord
+};
+__device__ __forceinline__ void r0_lane_max(const uint32_t o[4], uint32_t hb, R0Lane& L) {
+    L.bo[0] = L.bo[1] = L.bo[2] = L.bo[3] = 0;
+    L.bj = 0;
+    L.tie = 0;
+    if ((hb & 0xEu) == 0) {
+        // one segment (the common case: no row starts inside the lane)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (o[j] > L.bo[0]) { L.bo[0] = o[j]; L.bj = (uint32_t)j; L.tie = 0; }
+            else if (o[j] != 0 && o[j] == L.bo[0]) L.tie = 1;
+        }
+        return;
+    }
+    uint32_t t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (j > 0) t += (hb >> j) & 1u;
+#pragma unroll
+        for (int q = 0; q <= j; q++) {
+            if (t == (uint32_t)q) {
+                if (o[j] > L.bo[q]) {
+                    L.bo[q] = o[j];
+                    L.bj = (L.bj & ~(3u << (2 * q))) | ((uint32_t)j << (2 * q));
+                    L.tie &= ~(1u << q);
+                } else if (o[j] != 0 && o[j] == L.bo[q]) {
+                    L.tie |= 1u << q;
+                }
+            }
+        }
+    }
+}
+
 __device__ void r0_consumer(R0Smem& s, const Round0Args& a, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
     const VertexArrays& va = a.va;
     DevState* st = a.st;
+    const uint32_t base = (uint32_t)warp * 128u + (uint32_t)lane * 4u;  // the lane's first entry in a tile
     for (uint32_t i = 0;; i++) {
         const int k = (int)(i % R0S);
         const uint32_t use = i / R0S;
@@ -1052,84 +1098,119 @@ __device__ void r0_consumer(R0Smem& s, const Round0Args& a, int tid) {
         if (!S.valid) return;
         const uint32_t j0 = S.j0, nent = S.nent, shift = S.shift;
         const SegIn& g = a.segs[S.seg];
-        const uint32_t vbase = g.vbase, k0 = g.k0, k1 = g.k1;
+        const uint32_t vbase = g.vbase;
 
-        // row structure from the bitmap: every warp scans the tile's words itself
-        uint32_t wex[R0WPL], sum = 0;
-#pragma unroll
-        for (int q = 0; q < R0WPL; q++) {
-            wex[q] = sum;
-            sum += __popc(S.bits[lane * R0WPL + q]);
-        }
-        const uint32_t incl = warp_incl_scan(sum, lane);
-#pragma unroll
-        for (int q = 0; q < R0WPL; q++) wex[q] += incl - sum;
-        const uint32_t starts = __shfl_sync(FULL, incl, 31);
+        // rows of the tile: the row of entry e is the number of row starts at
+        // positions 1 .. e (entry 0 is in row 0, whether or not a row starts there)
         const uint32_t b0 = S.bits[0] & 1u;
-        const uint32_t nrt = starts + 1u - b0;  // rows with entries in the tile
+        const uint32_t wx = __popc(S.bits[lane]);
+        const uint32_t nrt = __reduce_add_sync(FULL, wx) - b0 + 1u;  // rows with entries in the tile
+        const uint32_t wb = __reduce_add_sync(FULL, lane < warp * 4 ? wx : 0u) - (warp > 0 ? b0 : 0u);
+        uint32_t hb = (S.bits[base >> 5] >> (base & 31u)) & 0xFu;     // row starts among the lane's entries
+        if (base == 0) hb &= ~1u;
         const bool cutL = (j0 + nent < g.nent) && !(S.bits[R0W] & 1u);
         const bool cut0 = !b0 || (nrt == 1 && cutL);
 
-        // entries: R0G groups of 32 per warp
-        uint64_t key[R0G];
-        uint32_t lr[R0G], u[R0G], word[R0G];
+        // the entries' ord(w): the high words of their stored words
+        uint32_t o[4];
+        {
+            const uint4 qa = *reinterpret_cast<const uint4*>(&S.pk[base]);
+            const uint4 qb = *reinterpret_cast<const uint4*>(&S.pk[base + 2]);
+            o[0] = qa.y; o[1] = qa.w; o[2] = qb.y; o[3] = qb.w;
 #pragma unroll
-        for (int i2 = 0; i2 < R0G; i2++) {
-            const int grp = warp * R0G + i2;  // warp-uniform
-            const uint32_t q = (uint32_t)grp * 32u + lane;
-            const int src = grp / R0WPL, sub = grp % R0WPL;
-            uint32_t pre = 0;
-#pragma unroll
-            for (int qq = 0; qq < R0WPL; qq++) {
-                const uint32_t p1 = __shfl_sync(FULL, wex[qq], src);
-                if (qq == sub) pre = p1;
-            }
-            word[i2] = S.bits[grp];
-            lr[i2] = pre + __popc(word[i2] & (FULL >> (31 - lane))) - b0;
-            key[i2] = 0;
-            u[i2] = NIL;
-            if (q < nent) {
-                const unsigned long long w = S.pk[q];
-                key[i2] = (w & 0xFFFFFFFF00000000ull) | perm_seed((uint32_t)w, k0, k1);
-                u[i2] = S.nbr[q] + vbase;
-            }
+            for (int j = 0; j < 4; j++)
+                if (base + j >= nent) o[j] = 0;
         }
+        R0Lane L;
+        r0_lane_max(o, hb, L);
+        const uint32_t nseg = 1u + __popc(hb & 0xEu);
+        // phase 1: the largest ord of every row into rord
+        const bool mixed = __any_sync(FULL, (hb & (lane == 0 ? 0xEu : 0xFu)) != 0);
+        uint32_t R;  // row of the lane's segment 0
+        if (!mixed) {
+            // the warp's 128 entries lie in one row
+            R = wb + __shfl_sync(FULL, hb & 1u, 0);
+            const uint32_t hi = __reduce_max_sync(FULL, L.bo[0]);
+            if (lane == 0 && hi) atomicMax(&s.rord[R], hi);
+        } else {
+            const uint32_t c = __popc(hb);
+            R = wb + warp_incl_scan(c, lane) - c + (hb & 1u);
+            // segmented inclusive maximum over the lanes of the lane's last segment
+            uint32_t v = nseg == 1 ? L.bo[0] : nseg == 2 ? L.bo[1] : nseg == 3 ? L.bo[2] : L.bo[3];
+            uint32_t f = hb != 0;
 #pragma unroll
-        for (int i2 = 0; i2 < R0G; i2++) {
-            if ((word[i2] & 0xFFFFFFFEu) == 0) {
-                // the whole group lies in one row
-                if (__any_sync(FULL, key[i2] != 0)) {
-                    const uint32_t hi = __reduce_max_sync(FULL, (uint32_t)(key[i2] >> 32));
-                    const uint32_t lo =
-                        __reduce_max_sync(FULL, ((uint32_t)(key[i2] >> 32) == hi) ? (uint32_t)key[i2] : 0u);
-                    if (lane == 0) atomicMax(&s.kmax[lr[i2]], ((unsigned long long)hi << 32) | lo);
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t ov = __shfl_up_sync(FULL, v, d), of = __shfl_up_sync(FULL, f, d);
+                if (lane >= d && !f) { v = max(v, ov); f = of; }
+            }
+            const uint32_t vprev = __shfl_up_sync(FULL, v, 1);
+            const uint32_t nhead = __shfl_down_sync(FULL, hb & 1u, 1);
+            if (nseg > 1) {
+                // the lane's first segment ends a row (continued from the lanes before
+                // unless it starts at the lane's first entry); middle ones are whole rows
+                const uint32_t first = max(L.bo[0], (lane > 0 && !(hb & 1u)) ? vprev : 0u);
+                if (first) atomicMax(&s.rord[R], first);
+#pragma unroll
+                for (uint32_t t = 1; t < 3; t++)
+                    if (t + 1 < nseg && L.bo[t]) atomicMax(&s.rord[R + t], L.bo[t]);
+            }
+            // the row of the last segment ends here when the next lane starts a row
+            if ((lane == 31 || nhead) && v) atomicMax(&s.rord[R + nseg - 1], v);
+        }
+        cbar();
+        // phase 2: the entries at their row's largest ord claim the row; a second
+        // claim (or a tie inside a lane) marks the row tied
+        bool tied = false;
+#pragma unroll
+        for (uint32_t t = 0; t < 4; t++) {
+            if (t < nseg && L.bo[t] && L.bo[t] == s.rord[R + t]) {
+                const uint32_t p = base + ((L.bj >> (2 * t)) & 3u);
+                const uint32_t old = atomicCAS(&s.rwin[R + t], R0_EMPTY, p);
+                if (old != R0_EMPTY || ((L.tie >> t) & 1u)) {
+                    atomicExch(&s.rwin[R + t], R0_TIED);
+                    tied = true;
                 }
-            } else if (key[i2]) {
-                atomicMax(&s.kmax[lr[i2]], (unsigned long long)key[i2]);
             }
         }
-        cbar();
-        // the entry that holds its row's maximum names the row's candidate (keys are distinct)
+        if (cbar_or(tied)) {
+            // phase 3 (equal weights only): perm_seed decides among the tied entries
+            const uint32_t k0 = g.k0, k1 = g.k1;
+            uint32_t mine = 0;   // bit j: entry j of the lane is tied at its row's maximum
 #pragma unroll
-        for (int i2 = 0; i2 < R0G; i2++)
-            if (key[i2] && key[i2] == s.kmax[lr[i2]]) s.knbr[lr[i2]] = u[i2];
-        cbar();
+            for (int j = 0; j < 4; j++) {
+                const uint32_t t = __popc(hb & 0xEu & ((2u << j) - 1u));
+                if (o[j] && o[j] == s.rord[R + t] && s.rwin[R + t] == R0_TIED) {
+                    mine |= 1u << j;
+                    atomicMax(&s.rperm[R + t], perm_seed((uint32_t)S.pk[base + j], k0, k1));
+                }
+            }
+            cbar();
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t t = __popc(hb & 0xEu & ((2u << j) - 1u));
+                if (((mine >> j) & 1u) && perm_seed((uint32_t)S.pk[base + j], k0, k1) == s.rperm[R + t])
+                    s.rwin[R + t] = base + (uint32_t)j;
+            }
+            cbar();
+        }
 
-        // rows: candidates
+        // phase 4: rows -- the winner names the candidate; cut rows leave their key in bkey
 #pragma unroll
         for (int q = 0; q < R0RPT; q++) {
             const uint32_t r = (uint32_t)(tid + q * R0C);
             if (r < nrt) {
                 const uint32_t v = S.rvid[shift + r] + vbase;
-                const unsigned long long K = s.kmax[r];
-                s.kmax[r] = 0;
-                if (v >= va.nvert) {
+                const uint32_t ow = s.rord[r], p = s.rwin[r];
+                s.rord[r] = 0;
+                s.rwin[r] = R0_EMPTY;
+                s.rperm[r] = 0;
+                if (v >= va.nvert || p >= nent) {
                     set_err(st, ERR_BOUNDS, v);
                     continue;
                 }
                 const bool cut = (r == 0 && cut0) || (r == nrt - 1 && cutL);
-                if (!cut) va.cnbr[v] = s.knbr[r];
-                else atomicMax(&va.bkey[v], K);
+                if (!cut) va.cnbr[v] = S.nbr[p] + vbase;
+                else atomicMax(&va.bkey[v], ((unsigned long long)ow << 32) | perm_seed((uint32_t)S.pk[p], g.k0, g.k1));
             }
         }
         cbar();
@@ -1142,7 +1223,11 @@ __global__ void __launch_bounds__(R0T, LM_R0MINB) k_round0(const Round0Args* __r
     R0Smem& s = *reinterpret_cast<R0Smem*>(r0_raw);
     const Round0Args& a = *pa;
     const int tid = threadIdx.x;
-    for (uint32_t r = tid; r <= TILE0; r += R0T) s.kmax[r] = 0;
+    for (uint32_t r = tid; r <= TILE0; r += R0T) {
+        s.rord[r] = 0;
+        s.rwin[r] = R0_EMPTY;
+        s.rperm[r] = 0;
+    }
     if (tid == 0) {
         for (int k = 0; k < R0S; k++) {
             mbar_init(&s.full[k], 1);
