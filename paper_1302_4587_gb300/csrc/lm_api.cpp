@@ -607,6 +607,97 @@ int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t
     return LM_OK;
 }
 
+// Many graphs on engine e in the same launches (lm_batch_match, and groups of
+// served requests): their vertex and entry ranges are laid side by side in one
+// union id space, each graph keeping its own seed and edge ids.  mates[i] is
+// device or host memory; rounds[i] and matched2[i] receive graph i's round count
+// and matched vertices.
+int match_batch(lm_ctx* ctx, Engine& e, const lm_graph* const* gs, uint32_t count, const uint64_t* seeds,
+                uint32_t* const* mates, uint32_t* rounds, unsigned long long* matched2, Prof& prof) {
+    uint64_t nv = 0, ne = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        nv += gs[i]->n;
+        ne += gs[i]->nent;
+    }
+    if (nv > 0xFFFFFFF0ull || ne > 0xFFFFFFF0ull) return fail(ctx, LM_EINVAL, "batch too large for 32-bit union ids");
+    cudaStream_t s = e.stream;
+    int rc = ensure_ws(ctx, e, (uint32_t)nv, (uint32_t)ne, count);
+    if (rc) return rc;
+    Workspace& w = e.ws;
+    // host tables: graph vertex / entry bases, offsets, segments, destinations
+    std::vector<uint32_t> gvb(count + 1), geb(count);
+    std::vector<const uint32_t*> goff(count);
+    std::vector<SegIn> segs(count);
+    std::vector<uint32_t*> dst(count);
+    std::vector<char> host_dst(count);
+    uint32_t vb = 0, eb = 0, tb = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        gvb[i] = vb;
+        geb[i] = eb;
+        goff[i] = gs[i]->off;
+        segs[i] = seg_of(gs[i], seeds[i], vb, eb, tb);
+        tb += gs[i]->ntiles;
+        host_dst[i] = !is_device_ptr(mates[i]);
+        dst[i] = host_dst[i] ? w.cnbr + vb : mates[i];  // host results are staged in the cnbr array
+        vb += gs[i]->n;
+        eb += gs[i]->nent;
+    }
+    gvb[count] = vb;
+    const size_t b_gvb = (count + 1) * sizeof(uint32_t), b_geb = count * sizeof(uint32_t);
+    const size_t b_off = count * sizeof(void*), b_seg = count * sizeof(SegIn), b_dst = count * sizeof(void*);
+    rc = staging_ready(ctx, e);
+    if (rc) return rc;
+    rc = ensure_pinned(ctx, e, b_gvb + b_geb + b_off + b_seg + b_dst + 256);
+    if (rc) return rc;
+    char* pin = static_cast<char*>(e.pinned);
+    size_t o = 0;
+    auto stage = [&](void* dev, const void* src, size_t bytes) -> cudaError_t {
+        memcpy(pin + o, src, bytes);
+        cudaError_t r = cudaMemcpyAsync(dev, pin + o, bytes, cudaMemcpyHostToDevice, s);
+        o = align_up(o + bytes, 16);
+        return r;
+    };
+    LM_CK(ctx, stage(w.gvbase, gvb.data(), b_gvb));
+    LM_CK(ctx, stage(w.gebase, geb.data(), b_geb));
+    LM_CK(ctx, stage(w.goff, goff.data(), b_off));
+    LM_CK(ctx, stage(w.segs, segs.data(), b_seg));
+    LM_CK(ctx, stage(w.gdst, dst.data(), b_dst));
+    LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, count * sizeof(uint32_t), s));
+    LM_CK(ctx, cudaMemsetAsync(w.gmatched, 0, count * sizeof(unsigned long long), s));
+    prof.begin(LM_K_OTHER);
+    LM_CK(ctx, launch_union_setup(s, w.gvbase, w.gebase, w.goff, count, (uint32_t)nv, w.start, w.gid, w.len[0]));
+    prof.end();
+    Job job;
+    job.va = vertex_arrays(e, (uint32_t)nv, nullptr, true, w.mate);
+    job.nedges = (uint32_t)(ne / 2);
+    job.ecap = (uint32_t)ne;
+    job.vlist = nullptr;
+    job.rdeg = nullptr;
+    job.nvlist = (uint32_t)nv;
+    job.nseg = ne > 0 ? count : 0;
+    job.ntiles = tb;
+    job.grounds = w.grounds;
+    rc = run_job(ctx, e, job, prof);
+    if (rc) return rc;
+    prof.begin(LM_K_OTHER);
+    LM_CK(ctx, launch_to_local_batch(s, w.mate, w.gvbase, count, w.gdst, w.gmatched, (uint32_t)nv));
+    prof.end();
+    bool any_host = false;
+    for (uint32_t i = 0; i < count; i++) any_host |= host_dst[i] != 0;
+    std::vector<uint32_t> hmate;
+    if (any_host) {
+        hmate.resize(nv);
+        LM_CK(ctx, cudaMemcpyAsync(hmate.data(), w.cnbr, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    }
+    LM_CK(ctx, cudaMemcpyAsync(rounds, w.grounds, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LM_CK(ctx, cudaMemcpyAsync(matched2, w.gmatched, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    LM_CK(ctx, cudaStreamSynchronize(s));
+    if (any_host)
+        for (uint32_t i = 0; i < count; i++)
+            if (host_dst[i] && gs[i]->n) memcpy(mates[i], hmate.data() + gvb[i], (size_t)gs[i]->n * sizeof(uint32_t));
+    return LM_OK;
+}
+
 }  // namespace lm
 
 namespace {
@@ -1006,97 +1097,19 @@ int lm_batch_match(lm_ctx* ctx, const lm_graph* const* gs, uint32_t count, const
     if (ctx->poisoned) return LM_ECUDA;
     if (count == 0) return LM_OK;
     if (!gs || !seeds || !mates) return fail(ctx, LM_EINVAL, "null array");
-    uint64_t nv = 0, ne = 0;
     for (uint32_t i = 0; i < count; i++) {
         if (!gs[i] || !mates[i]) return fail(ctx, LM_EINVAL, "null graph or mate at %u", i);
         if (gs[i]->ctx->device != ctx->device) return fail(ctx, LM_EINVAL, "graph %u lives on another device", i);
-        nv += gs[i]->n;
-        ne += gs[i]->nent;
     }
-    if (nv > 0xFFFFFFF0ull || ne > 0xFFFFFFF0ull) return fail(ctx, LM_EINVAL, "batch too large for 32-bit union ids");
     std::lock_guard<std::mutex> lk(ctx->call_mu);
     DevGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, LM_ECUDA, "cudaSetDevice failed");
-    Engine& e = ctx->eng;
-    cudaStream_t s = e.stream;
     if (stats) memset(stats, 0, sizeof(lm_stats) * count);
-    int rc = ensure_ws(ctx, e, (uint32_t)nv, (uint32_t)ne, count);
-    if (rc) return rc;
-    Workspace& w = e.ws;
-    // host tables: graph vertex / entry bases, offsets, segments, destinations
-    std::vector<uint32_t> gvb(count + 1), geb(count);
-    std::vector<const uint32_t*> goff(count);
-    std::vector<SegIn> segs(count);
-    std::vector<uint32_t*> dst(count);
-    std::vector<char> host_dst(count);
-    uint32_t vb = 0, eb = 0, tb = 0;
-    for (uint32_t i = 0; i < count; i++) {
-        gvb[i] = vb;
-        geb[i] = eb;
-        goff[i] = gs[i]->off;
-        segs[i] = seg_of(gs[i], seeds[i], vb, eb, tb);
-        tb += gs[i]->ntiles;
-        host_dst[i] = !is_device_ptr(mates[i]);
-        dst[i] = host_dst[i] ? w.cnbr + vb : mates[i];  // host results are staged in the cnbr array
-        vb += gs[i]->n;
-        eb += gs[i]->nent;
-    }
-    gvb[count] = vb;
-    const size_t b_gvb = (count + 1) * sizeof(uint32_t), b_geb = count * sizeof(uint32_t);
-    const size_t b_off = count * sizeof(void*), b_seg = count * sizeof(SegIn), b_dst = count * sizeof(void*);
-    rc = staging_ready(ctx, e);
-    if (rc) return rc;
-    rc = ensure_pinned(ctx, e, b_gvb + b_geb + b_off + b_seg + b_dst + 256);
-    if (rc) return rc;
-    char* pin = static_cast<char*>(e.pinned);
-    size_t o = 0;
-    auto stage = [&](void* dev, const void* src, size_t bytes) -> cudaError_t {
-        memcpy(pin + o, src, bytes);
-        cudaError_t r = cudaMemcpyAsync(dev, pin + o, bytes, cudaMemcpyHostToDevice, s);
-        o = align_up(o + bytes, 16);
-        return r;
-    };
-    LM_CK(ctx, stage(w.gvbase, gvb.data(), b_gvb));
-    LM_CK(ctx, stage(w.gebase, geb.data(), b_geb));
-    LM_CK(ctx, stage(w.goff, goff.data(), b_off));
-    LM_CK(ctx, stage(w.segs, segs.data(), b_seg));
-    LM_CK(ctx, stage(w.gdst, dst.data(), b_dst));
-    LM_CK(ctx, cudaMemsetAsync(w.grounds, 0, count * sizeof(uint32_t), s));
-    LM_CK(ctx, cudaMemsetAsync(w.gmatched, 0, count * sizeof(unsigned long long), s));
-    Prof prof(ctx, s);
-    prof.begin(LM_K_OTHER);
-    LM_CK(ctx, launch_union_setup(s, w.gvbase, w.gebase, w.goff, count, (uint32_t)nv, w.start, w.gid, w.len[0]));
-    prof.end();
-    Job job;
-    job.va = vertex_arrays(e, (uint32_t)nv, nullptr, true, w.mate);
-    job.nedges = (uint32_t)(ne / 2);
-    job.ecap = (uint32_t)ne;
-    job.vlist = nullptr;
-    job.rdeg = nullptr;
-    job.nvlist = (uint32_t)nv;
-    job.nseg = ne > 0 ? count : 0;
-    job.ntiles = tb;
-    job.grounds = w.grounds;
-    rc = run_job(ctx, e, job, prof);
-    if (rc) return rc;
-    prof.begin(LM_K_OTHER);
-    LM_CK(ctx, launch_to_local_batch(s, w.mate, w.gvbase, count, w.gdst, w.gmatched, (uint32_t)nv));
-    prof.end();
-    bool any_host = false;
-    for (uint32_t i = 0; i < count; i++) any_host |= host_dst[i] != 0;
-    std::vector<uint32_t> hmate;
-    if (any_host) {
-        hmate.resize(nv);
-        LM_CK(ctx, cudaMemcpyAsync(hmate.data(), w.cnbr, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    }
+    Prof prof(ctx, ctx->eng.stream);
     std::vector<uint32_t> grounds(count);
     std::vector<unsigned long long> gm(count);
-    LM_CK(ctx, cudaMemcpyAsync(grounds.data(), w.grounds, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    LM_CK(ctx, cudaMemcpyAsync(gm.data(), w.gmatched, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    LM_CK(ctx, cudaStreamSynchronize(s));
-    if (any_host)
-        for (uint32_t i = 0; i < count; i++)
-            if (host_dst[i] && gs[i]->n) memcpy(mates[i], hmate.data() + gvb[i], (size_t)gs[i]->n * sizeof(uint32_t));
+    const int rc = match_batch(ctx, ctx->eng, gs, count, seeds, mates, grounds.data(), gm.data(), prof);
+    if (rc) return rc;
     if (stats) {
         // per graph: rounds, |M|, initial sizes; per call (copied into every entry): launches and timings
         lm_stats whole;

@@ -181,6 +181,9 @@ struct Prof {
     void fill(lm_stats* st);
 };
 int run_job(lm_ctx* ctx, Engine& e, Job& job, Prof& prof);
+// count graphs in the same launches (see lm_api.cpp); rounds[i], matched2[i] per graph
+int match_batch(lm_ctx* ctx, Engine& e, const lm_graph* const* gs, uint32_t count, const uint64_t* seeds,
+                uint32_t* const* mates, uint32_t* rounds, unsigned long long* matched2, Prof& prof);
 int match_one(lm_ctx* ctx, Engine& e, const lm_graph* g, uint64_t seed, uint32_t* mate, bool dev_out, Prof& prof,
               bool async = false);
 // the pinned staging (arguments, tables) is free again: the copies a queued

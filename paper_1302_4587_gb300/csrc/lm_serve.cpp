@@ -11,7 +11,9 @@
 // range of union vertex ids and one of union entries) fits and a slot is
 // free, in arrival order, and leaves after the first round in which it has no
 // live unmatched row: its result is converted to local vertex ids and written
-// to the caller's buffer.  Every request keeps its own seed and edge ids and
+// to the caller's buffer.  When nothing is in flight, a short queue instead runs
+// to completion as one job graph (the batched path, or the plain one for a
+// single request): at light load that answers sooner than round-by-round steps.  Every request keeps its own seed and edge ids and
 // shares no vertex with another, so its result does not depend on what else
 // is in flight.
 //
@@ -107,6 +109,7 @@ constexpr size_t MAX_QUEUE = 1u << 20;
 
 constexpr uint32_t MAX_FRESH = 64;  // admissions per step (kernel arguments of one step fit the argument area)
 constexpr uint32_t MAX_ROUNDS_PER_STEP = 8;  // a step without admissions runs up to this many rounds
+constexpr size_t MAX_GROUP = 16;  // queued requests that run together as one job when nothing is in flight
 
 struct StepArgs {
     InitArgs init[MAX_FRESH];
@@ -287,20 +290,24 @@ int step(ServeState* S, const std::vector<Request*>& fresh, std::vector<Request*
 void scheduler(ServeState* S) {
     cudaSetDevice(S->ctx->device);
     for (;;) {
-        std::vector<Request*> fresh;
-        Request* lone = nullptr;
+        std::vector<Request*> fresh, group;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
             if (S->stop) return;
-            // a request with nothing else in flight or queued runs alone, as one job
-            // graph (the plain path): round-by-round stepping only pays off in a mix
-            if (S->active.empty() && S->queue.size() == 1 && !S->fatal) {
-                lone = S->queue.front();
-                S->queue.pop_front();
-                lone->state = 1;
+            // with nothing in flight, the few requests queued so far run together to
+            // completion as one job graph (one request: the plain path; several: the
+            // batched path), whose round loop stays on the device.  At light load this
+            // answers sooner than stepping round by round, which returns to the host
+            // after every round; requests arriving meanwhile queue for the next
+            // dispatch.  A longer queue, or requests in flight, go round by round with
+            // admissions between rounds (continuous batching).
+            if (S->active.empty() && S->queue.size() <= MAX_GROUP && !S->fatal) {
+                group.assign(S->queue.begin(), S->queue.end());
+                S->queue.clear();
+                for (Request* r : group) r->state = 1;
             }
-            while (!lone && !S->queue.empty() && !S->free_slots.empty() && fresh.size() < MAX_FRESH) {
+            while (group.empty() && !S->queue.empty() && !S->free_slots.empty() && fresh.size() < MAX_FRESH) {
                 Request* r = S->queue.front();
                 uint32_t vb = 0, eb = 0;
                 if (!S->vspace.alloc(r->g->n, &vb)) break;
@@ -318,18 +325,42 @@ void scheduler(ServeState* S) {
                 fresh.push_back(r);
             }
         }
-        if (lone) {
+        if (!group.empty()) {
             Prof off(nullptr, S->eng.stream);
-            const int rc = match_one(S->ctx, S->eng, lone->g, lone->seed, lone->mate, !lone->host_dst, off);
-            std::lock_guard<std::mutex> lk(S->mu);
-            lone->rc = rc;
-            if (rc == LM_OK) {
-                lone->rounds = S->eng.st_host->rounds;
-                lone->matched = S->eng.st_host->matched2 / 2;
-            } else if (rc == LM_ECUDA) {
-                S->fatal = rc;
+            const size_t k = group.size();
+            std::vector<uint32_t> rounds(k);
+            std::vector<unsigned long long> m2(k);
+            int rc;
+            if (k == 1) {
+                Request* r = group[0];
+                rc = match_one(S->ctx, S->eng, r->g, r->seed, r->mate, !r->host_dst, off);
+                if (rc == LM_OK) {
+                    rounds[0] = S->eng.st_host->rounds;
+                    m2[0] = S->eng.st_host->matched2;
+                }
+            } else {
+                std::vector<const lm_graph*> gs(k);
+                std::vector<uint64_t> seeds(k);
+                std::vector<uint32_t*> mates(k);
+                for (size_t i = 0; i < k; i++) {
+                    gs[i] = group[i]->g;
+                    seeds[i] = group[i]->seed;
+                    mates[i] = group[i]->mate;
+                }
+                rc = match_batch(S->ctx, S->eng, gs.data(), (uint32_t)k, seeds.data(), mates.data(), rounds.data(),
+                                 m2.data(), off);
             }
-            lone->state = 2;
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (rc == LM_ECUDA) S->fatal = rc;
+            for (size_t i = 0; i < k; i++) {
+                Request* r = group[i];
+                r->rc = rc;
+                if (rc == LM_OK) {
+                    r->rounds = rounds[i];
+                    r->matched = m2[i] / 2;
+                }
+                r->state = 2;
+            }
             S->cv_done.notify_all();
             continue;
         }
