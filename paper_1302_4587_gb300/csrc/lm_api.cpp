@@ -1027,14 +1027,14 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     cv.add(&c.flag, (size_t)n + 1);
     cv.add(&c.rank, (size_t)n + 1);
     cv.add(&c.cross, M);
-    cv.add(&c.cpos, M);
+    cv.add(&c.cpos, 4);
     cv.add(&c.key[0], M);
     cv.add(&c.key[1], M);
     cv.add(&c.val[0], M);
     cv.add(&c.val[1], M);
     cv.add(&c.hist, hist_words);
     cv.add(&c.hoff, hist_words + 1);
-    cv.add(&c.isl, M);
+    cv.add(&c.multi, (size_t)m / 32 + 2);
     cv.add(&c.pos, M);
     cv.add(&c.gref, M);
     cv.add(&c.scan_tmp, c.scan_words);

@@ -9,13 +9,14 @@
 // is their sum (accumulated in double in input order, rounded once to float32).
 //
 // Device steps (all of them here): representatives and their prefix ranks;
-// the coarse map and vertex weights; the crossing edges, compacted in input
-// order, get their unordered coarse pair as a key; a stable LSD radix sort
+// the coarse map and vertex weights; every edge, in input order, gets its
+// unordered coarse pair as a key (edges inside a pair a key above all pairs,
+// so that they end up last); a stable LSD radix sort
 // (8-bit digits over the key's significant bits) groups equal pairs with their
 // edges still in input order; each group's first edge is its leader and the
 // group's weight sum is taken over its edges in order; leader flags over the
-// edges and their prefix ranks give each coarse edge its place; the leaders
-// write the coarse edges.
+// edges (the crossing flags with every non-leader cleared) and their prefix
+// ranks give each coarse edge its place; the leaders write the coarse edges.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/lm.h"
@@ -60,30 +61,39 @@ __global__ void k_c_map(const uint32_t* __restrict__ mate, uint32_t n, const uin
     }
 }
 
-// crossing[e] = 1 when the edge joins two coarse vertices (endpoints validated)
-__global__ void k_c_cross(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev, uint32_t m, uint32_t n,
-                          const uint32_t* __restrict__ cmap, uint32_t* __restrict__ cross, uint32_t* __restrict__ err) {
+// every edge in input order, keyed by its unordered coarse pair
+// min(c, d) << bits | max(c, d); an edge inside a pair (or with an endpoint >= n)
+// gets the key 2^(2 bits) - 1, above every pair's, so the sort puts it at the end.
+// cross[e] = 1 for the edges between two coarse vertices (they are counted in
+// *ncross), 0 for the others.
+__global__ void k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev, uint32_t m, uint32_t n,
+                         const uint32_t* __restrict__ cmap, uint32_t bits, unsigned long long* __restrict__ key,
+                         uint32_t* __restrict__ val, uint32_t* __restrict__ cross, uint32_t* __restrict__ ncross,
+                         uint32_t* __restrict__ err) {
+    const unsigned long long none = (1ull << (2 * bits)) - 1ull;
+    uint32_t mine = 0;
     for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
         const uint32_t a = eu[e], b = ev[e];
+        unsigned long long k = none;
         uint32_t x = 0;
-        if (a >= n || b >= n) atomicOr(err, C_ERR_EDGE);
-        else x = cmap[a] != cmap[b] ? 1u : 0u;
+        if (a >= n || b >= n) {
+            atomicOr(err, C_ERR_EDGE);
+        } else {
+            const uint32_t c = cmap[a], d = cmap[b];
+            if (c != d) {
+                k = ((unsigned long long)min(c, d) << bits) | max(c, d);
+                x = 1;
+            }
+        }
+        key[e] = k;
+        val[e] = e;
         cross[e] = x;
+        mine += x;
     }
-}
-
-// the crossing edges in input order: key = min(c, d) << bits | max(c, d), value = e
-__global__ void k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev, uint32_t m,
-                         const uint32_t* __restrict__ cmap, const uint32_t* __restrict__ cross,
-                         const uint32_t* __restrict__ cpos, uint32_t bits, unsigned long long* __restrict__ key,
-                         uint32_t* __restrict__ val) {
-    for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
-        if (!cross[e]) continue;
-        const uint32_t c = cmap[eu[e]], d = cmap[ev[e]];
-        const uint32_t p = cpos[e];
-        key[p] = ((unsigned long long)min(c, d) << bits) | max(c, d);
-        val[p] = e;
-    }
+    // one atomic per warp on the count
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(ncross, mine);
 }
 
 // ---- stable LSD radix sort of (key, value) pairs, 8 bits per pass ----------
@@ -192,36 +202,49 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const unsigned long long* _
     }
 }
 
-// group heads in sorted order: the first item of every run of equal keys; the
-// head's value is the group's leader (the smallest edge index: the sort is
-// stable and the items entered in input order)
-__global__ void k_c_heads(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt,
-                          uint32_t* __restrict__ isl, uint32_t* __restrict__ gref) {
+// groups in sorted order (runs of equal keys; a run's first item is its leader,
+// the smallest edge index, since the sort is stable and the items entered in
+// input order).  Almost every group is a single edge, so instead of marking
+// the leaders (a scattered write per group) this clears the crossing flag of
+// every other member, and marks the leaders of groups with several edges
+// (a bit, and where their run starts).  The flags then say which edges lead.
+__global__ void k_c_marks(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt,
+                          uint32_t* __restrict__ lead, uint32_t* __restrict__ multi, uint32_t* __restrict__ gref) {
     for (uint32_t i = blockIdx.x * CT + threadIdx.x; i < cnt; i += gridDim.x * CT) {
-        if (i > 0 && key[i] == key[i - 1]) continue;
+        const unsigned long long k = key[i];
         const uint32_t e = val[i];
-        isl[e] = 1u;
-        gref[e] = i;
+        if (i > 0 && k == key[i - 1]) {
+            lead[e] = 0u;
+        } else if (i + 1 < cnt && key[i + 1] == k) {
+            atomicOr(&multi[e >> 5], 1u << (e & 31));
+            gref[e] = i;
+        }
     }
 }
 
-// the leaders write their coarse edge at their rank among the leaders; the weight
-// is the group's sum over its edges in input order
+// the leaders, in input order, write their coarse edge at their rank among the
+// leaders; the weight is the group's sum over its edges in input order (a single
+// edge's own weight, which double and back leaves unchanged)
 __global__ void k_c_emit(uint32_t m, const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev,
                          const float* __restrict__ w, const uint32_t* __restrict__ cmap,
-                         const uint32_t* __restrict__ isl, const uint32_t* __restrict__ pos,
-                         const uint32_t* __restrict__ gref, const unsigned long long* __restrict__ key,
-                         const uint32_t* __restrict__ val, uint32_t cnt, uint32_t* __restrict__ ceu,
-                         uint32_t* __restrict__ cev, float* __restrict__ cw) {
+                         const uint32_t* __restrict__ lead, const uint32_t* __restrict__ multi,
+                         const uint32_t* __restrict__ pos, const uint32_t* __restrict__ gref,
+                         const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt,
+                         uint32_t* __restrict__ ceu, uint32_t* __restrict__ cev, float* __restrict__ cw) {
     for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
-        if (!isl[e]) continue;
-        const uint32_t p = pos[e], i0 = gref[e];
-        const unsigned long long k = key[i0];
-        double sum = 0.0;
-        for (uint32_t i = i0; i < cnt && key[i] == k; i++) sum += (double)w[val[i]];
+        if (!lead[e]) continue;
+        const uint32_t p = pos[e];
+        float we = w[e];
+        if ((__ldg(&multi[e >> 5]) >> (e & 31)) & 1u) {
+            const uint32_t i0 = gref[e];
+            const unsigned long long k = key[i0];
+            double sum = 0.0;
+            for (uint32_t i = i0; i < cnt && key[i] == k; i++) sum += (double)w[val[i]];
+            we = (float)sum;
+        }
         ceu[p] = cmap[eu[e]];
         cev[p] = cmap[ev[e]];
-        cw[p] = (float)sum;
+        cw[p] = we;
     }
 }
 
@@ -248,34 +271,39 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     if (int r = launch_exclusive_scan(s, c.flag, c.rank, c.n + 1, c.scan_tmp, c.scan_words)) return r;
     k_c_map<<<grid_for(c.n), CT, 0, s>>>(c.mate, c.n, c.rank, c.vw, c.cmap, c.cvw);
     if (c.m == 0) return (int)cudaGetLastError();
-    // crossing edges compacted in input order
-    if ((e = cudaMemsetAsync(c.cross + c.m, 0, sizeof(uint32_t), s))) return (int)e;
-    k_c_cross<<<grid_for(c.m), CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, c.cross, c.err);
-    if (int r = launch_exclusive_scan(s, c.cross, c.cpos, c.m + 1, c.scan_tmp, c.scan_words)) return r;
-    // the crossing count decides the sort's size: read it on the host
-    if ((e = cudaMemcpyAsync(mc_host_slot, c.cpos + c.m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
+    // the coarse vertex count decides the key's width: read it on the host
     if ((e = cudaMemcpyAsync(mc_host_slot + 1, c.rank + c.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaStreamSynchronize(s))) return (int)e;
-    const uint32_t mc = mc_host_slot[0], nc = mc_host_slot[1];
-    const uint32_t bits = bits_for(nc ? nc - 1 : 0);
-    k_c_keys<<<grid_for(c.m), CT, 0, s>>>(c.eu, c.ev, c.m, c.cmap, c.cross, c.cpos, bits, c.key[0], c.val[0]);
+    const uint32_t nc = mc_host_slot[1];
+    const uint32_t bits = bits_for(nc);  // coarse ids 0 .. nc - 1 and the pair key's top value stay apart
+    // every edge keyed in input order; the stable sort keeps input order among equal keys
+    // and puts the edges inside pairs last, after the mc crossing edges
+    if ((e = cudaMemsetAsync(c.cross + c.m, 0, sizeof(uint32_t), s))) return (int)e;
+    if ((e = cudaMemsetAsync(c.cpos, 0, sizeof(uint32_t), s))) return (int)e;
+    k_c_keys<<<grid_for(c.m), CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, bits, c.key[0], c.val[0], c.cross, c.cpos,
+                                          c.err);
+    if ((e = cudaMemcpyAsync(mc_host_slot, c.cpos, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
+    if ((e = cudaStreamSynchronize(s))) return (int)e;
+    const uint32_t mc = mc_host_slot[0];
     // radix passes over the key's 2 * bits significant bits
     int cur = 0;
-    if (mc > 1) {
-        const uint32_t nblk = (mc + RS_TILE - 1) / RS_TILE;
+    const uint32_t ns = mc < c.m ? c.m : mc;  // the crossing edges and, past them, the ones inside pairs
+    if (mc > 1 || (mc && ns > mc)) {
+        const uint32_t nblk = (ns + RS_TILE - 1) / RS_TILE;
         for (uint32_t shift = 0; shift < 2 * bits; shift += 8) {
-            k_rs_hist<<<nblk, RS_T, 0, s>>>(c.key[cur], mc, shift, nblk, c.hist);
+            k_rs_hist<<<nblk, RS_T, 0, s>>>(c.key[cur], ns, shift, nblk, c.hist);
             if (int r = launch_exclusive_scan(s, c.hist, c.hoff, 256 * nblk, c.scan_tmp, c.scan_words)) return r;
-            k_rs_scatter<<<nblk, RS_T, 0, s>>>(c.key[cur], c.val[cur], mc, shift, nblk, c.hoff, c.key[cur ^ 1],
+            k_rs_scatter<<<nblk, RS_T, 0, s>>>(c.key[cur], c.val[cur], ns, shift, nblk, c.hoff, c.key[cur ^ 1],
                                                c.val[cur ^ 1]);
             cur ^= 1;
         }
     }
-    if ((e = cudaMemsetAsync(c.isl, 0, ((size_t)c.m + 1) * sizeof(uint32_t), s))) return (int)e;
-    if (mc) k_c_heads<<<grid_for(mc), CT, 0, s>>>(c.key[cur], c.val[cur], mc, c.isl, c.gref);
-    if (int r = launch_exclusive_scan(s, c.isl, c.pos, c.m + 1, c.scan_tmp, c.scan_words)) return r;
-    k_c_emit<<<grid_for(c.m), CT, 0, s>>>(c.m, c.eu, c.ev, c.w, c.cmap, c.isl, c.pos, c.gref, c.key[cur], c.val[cur],
-                                          mc, c.ceu, c.cev, c.cw);
+    // the crossing flags become the leader flags: other members are cleared
+    if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
+    if (mc) k_c_marks<<<grid_for(mc), CT, 0, s>>>(c.key[cur], c.val[cur], mc, c.cross, c.multi, c.gref);
+    if (int r = launch_exclusive_scan(s, c.cross, c.pos, c.m + 1, c.scan_tmp, c.scan_words)) return r;
+    k_c_emit<<<grid_for(c.m), CT, 0, s>>>(c.m, c.eu, c.ev, c.w, c.cmap, c.cross, c.multi, c.pos, c.gref, c.key[cur],
+                                          c.val[cur], mc, c.ceu, c.cev, c.cw);
     return (int)cudaGetLastError();
 }
 

@@ -285,14 +285,14 @@ struct ContractArgs {
     float* cw;
     uint32_t* flag;           // [n + 1] representative flags
     uint32_t* rank;           // [n + 1] their exclusive prefix (rank[n] = coarse vertices)
-    uint32_t* cross;          // [m + 1] crossing-edge flags
-    uint32_t* cpos;           // [m + 1] their exclusive prefix (cpos[m] = crossing edges)
+    uint32_t* cross;          // [m + 1] crossing-edge flags, then leader flags
+    uint32_t* cpos;           // [1] crossing edges (counted while keying)
     unsigned long long* key[2];  // [m] coarse pair of each crossing edge (radix ping-pong)
     uint32_t* val[2];         // [m] its edge index
     uint32_t* hist;           // [256 * blocks] digit counts of a radix pass
     uint32_t* hoff;           // [256 * blocks + 1] their exclusive prefix
-    uint32_t* isl;            // [m + 1] leader flags
-    uint32_t* pos;            // [m + 1] their exclusive prefix (pos[m] = coarse edges)
+    uint32_t* multi;          // [m / 32 + 2] bit e: edge e leads a group of several edges
+    uint32_t* pos;            // [m + 1] exclusive prefix of the leader flags (pos[m] = coarse edges)
     uint32_t* gref;           // [m] a leader's group start in sorted order
     uint32_t* scan_tmp;
     size_t scan_words;
