@@ -1021,21 +1021,24 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     if (n == 0xFFFFFFFFu) return fail(ctx, LM_EINVAL, "n must be below 2^32 - 1");
     const uint32_t scan_count = (n > m ? n : m) + 1;
     c.scan_words = exclusive_scan_tmp_words(scan_count);
-    const size_t hist_words = contract_sort_tmp_words(m);
     const size_t M = (size_t)m + 1;
     Carver cv;
     cv.add(&c.flag, (size_t)n + 1);
     cv.add(&c.rank, (size_t)n + 1);
-    cv.add(&c.cross, M);
-    cv.add(&c.cpos, 4);
+    const size_t W = (size_t)m / 32 + 2;
+    cv.add(&c.cross, W);
+    cv.add(&c.counts, 4);
+    cv.add(&c.cpair, 2 * (size_t)m + 8);
     cv.add(&c.key[0], M);
     cv.add(&c.key[1], M);
     cv.add(&c.val[0], M);
     cv.add(&c.val[1], M);
-    cv.add(&c.hist, hist_words);
-    cv.add(&c.hoff, hist_words + 1);
+    cv.add(&c.status, contract_status_entries(m));
+    cv.add(&c.digits, contract_digit_words());
     cv.add(&c.multi, (size_t)m / 32 + 2);
-    cv.add(&c.pos, M);
+    cv.add(&c.wlead, W);
+    cv.add(&c.wpos, W);
+    cv.add(&c.tsum, 2 * ((size_t)m / 4096 + 2));
     cv.add(&c.gref, M);
     cv.add(&c.scan_tmp, c.scan_words);
     cv.add(&c.err, 4);
@@ -1061,11 +1064,12 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[0], c.err, 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hp[1], c.rank + n, 4, cudaMemcpyDeviceToHost, s);
     hp[2] = 0;
-    if (ce == cudaSuccess && m > 0) ce = cudaMemcpyAsync(&hp[2], c.pos + m, 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && m > 0) ce = cudaMemcpyAsync(&hp[2], c.counts + 2, 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return fail(ctx, LM_ECUDA, "contraction: %s", cudaGetErrorString(ce));
     if (hp[0] & 1u) return fail(ctx, LM_EINVAL, "mate is not a matching of the vertex set");
     if (hp[0] & 2u) return fail(ctx, LM_EINVAL, "an edge endpoint is >= n");
+    if (hp[0] & 4u) return fail(ctx, LM_ETIMEOUT, "contraction: a radix pass's look-back wait gave up");
     *n_out = hp[1];
     *m_out = hp[2];
     return LM_OK;

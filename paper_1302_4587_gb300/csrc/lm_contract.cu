@@ -18,6 +18,7 @@
 // edges (the crossing flags with every non-leader cleared) and their prefix
 // ranks give each coarse edge its place; the leaders write the coarse edges.
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include "../../include/lm.h"
 #include "lm_internal.h"
@@ -61,190 +62,518 @@ __global__ void k_c_map(const uint32_t* __restrict__ mate, uint32_t n, const uin
     }
 }
 
-// every edge in input order, keyed by its unordered coarse pair
-// min(c, d) << bits | max(c, d); an edge inside a pair (or with an endpoint >= n)
-// gets the key 2^(2 bits) - 1, above every pair's, so the sort puts it at the end.
-// cross[e] = 1 for the edges between two coarse vertices (they are counted in
-// *ncross), 0 for the others.
-__global__ void k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev, uint32_t m, uint32_t n,
-                         const uint32_t* __restrict__ cmap, uint32_t bits, unsigned long long* __restrict__ key,
-                         uint32_t* __restrict__ val, uint32_t* __restrict__ cross, uint32_t* __restrict__ ncross,
-                         uint32_t* __restrict__ err) {
-    const unsigned long long none = (1ull << (2 * bits)) - 1ull;
+// the unordered coarse pair of an edge as a 64-bit word, min(c, d) << 32 | max(c, d)
+__device__ __forceinline__ unsigned long long pair_word(uint32_t c, uint32_t d) {
+    return ((unsigned long long)min(c, d) << 32) | max(c, d);
+}
+// 32-bit hash of a pair word (a 64-bit finaliser's upper half); 0xFFFFFFFF is left for
+// the edges inside a pair
+__device__ __forceinline__ uint32_t pair_hash(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDull;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ull;
+    x ^= x >> 33;
+    const uint32_t h = (uint32_t)(x >> 32);
+    return h == 0xFFFFFFFFu ? 0xFFFFFFFEu : h;
+}
+
+// Edge kernels take four consecutive edges per thread (vector loads when the
+// arrays are 16-byte aligned) and a warp 128 edges: four whole words of a bitmask
+// over the edges, lanes 8q .. 8q+7 sharing word q.
+template <bool VEC>
+__device__ __forceinline__ uint4 load4(const uint32_t* a, uint64_t i, uint32_t count) {
+    if (VEC && i + 4 <= count) return __ldg(reinterpret_cast<const uint4*>(a + i));
+    uint4 v;
+    v.x = i < count ? a[i] : 0u;
+    v.y = i + 1 < count ? a[i + 1] : 0u;
+    v.z = i + 2 < count ? a[i + 2] : 0u;
+    v.w = i + 3 < count ? a[i + 3] : 0u;
+    return v;
+}
+__device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
+// every edge in input order, keyed by a hash of its unordered coarse pair (equal
+// pairs get equal keys); an edge inside a pair (or with an endpoint >= n) gets the
+// key 0xFFFFFFFF, above every pair's, so the sort puts it at the end.  Bit e of
+// cross: edge e joins two coarse vertices (counted in counts[0]).  The keys' four
+// digits are counted into hist[0 .. 1024) for the sort.  A warp takes 64 groups of
+// four edges per step, their loads issued together.
+template <bool VEC>
+__global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev,
+                                               uint32_t m, uint32_t n, const uint32_t* __restrict__ cmap,
+                                               uint32_t* __restrict__ key, uint32_t* __restrict__ cpair,
+                                               uint32_t* __restrict__ cross, uint32_t* __restrict__ counts,
+                                               uint32_t* __restrict__ hist, uint32_t* __restrict__ err) {
+    __shared__ uint32_t h[4][256];
+    for (uint32_t i = threadIdx.x; i < 4 * 256; i += CT) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t groups = (uint32_t)(((uint64_t)m + 3) / 4);
     uint32_t mine = 0;
-    for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
-        const uint32_t a = eu[e], b = ev[e];
-        unsigned long long k = none;
-        uint32_t x = 0;
-        if (a >= n || b >= n) {
-            atomicOr(err, C_ERR_EDGE);
-        } else {
-            const uint32_t c = cmap[a], d = cmap[b];
-            if (c != d) {
-                k = ((unsigned long long)min(c, d) << bits) | max(c, d);
-                x = 1;
+    // g0: the warp's first group (a multiple of 64, so of 8)
+    for (uint64_t g0 = 2ull * (blockIdx.x * CT + threadIdx.x - lane); g0 < groups; g0 += 2ull * gridDim.x * CT) {
+        uint4 a[2], b[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const uint64_t e0 = 4 * (g0 + 32 * u + lane);
+            a[u] = load4<VEC>(eu, e0, m);
+            b[u] = load4<VEC>(ev, e0, m);
+        }
+        uint32_t cu[2][4], cv[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const uint64_t e0 = 4 * (g0 + 32 * u + lane);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t x = at(a[u], j), y = at(b[u], j);
+                const bool ok = e0 + j < m && x < n && y < n;
+                if (e0 + j < m && !ok) atomicOr(err, C_ERR_EDGE);
+                cu[u][j] = ok ? cmap[x] : 0u;
+                cv[u][j] = ok ? cmap[y] : 0u;
             }
         }
-        key[e] = k;
-        val[e] = e;
-        cross[e] = x;
-        mine += x;
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const uint64_t g = g0 + 32 * u + lane;
+            const uint64_t e0 = 4 * g;
+            uint32_t nib = 0, k[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                k[j] = 0xFFFFFFFFu;
+                if (e0 + j >= m) continue;
+                if (cu[u][j] != cv[u][j]) {
+                    k[j] = pair_hash(pair_word(cu[u][j], cv[u][j]));
+                    nib |= 1u << j;
+                }
+#pragma unroll
+                for (int d = 0; d < 4; d++) atomicAdd(&h[d][(k[j] >> (8 * d)) & 0xFFu], 1u);
+            }
+            if (e0 + 4 <= m) {  // key and cpair are 16-byte aligned scratch
+                *reinterpret_cast<uint4*>(key + e0) = make_uint4(k[0], k[1], k[2], k[3]);
+                *reinterpret_cast<uint4*>(cpair + 2 * e0) = make_uint4(cu[u][0], cv[u][0], cu[u][1], cv[u][1]);
+                *reinterpret_cast<uint4*>(cpair + 2 * e0 + 4) = make_uint4(cu[u][2], cv[u][2], cu[u][3], cv[u][3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (e0 + j < m) {
+                        key[e0 + j] = k[j];
+                        cpair[2 * (e0 + j)] = cu[u][j];
+                        cpair[2 * (e0 + j) + 1] = cv[u][j];
+                    }
+            }
+            mine += __popc(nib);
+            uint32_t w = nib << (4 * (g & 7));
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
+            if ((g & 7) == 0 && e0 < m) cross[g >> 3] = w;
+        }
     }
     // one atomic per warp on the count
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(ncross, mine);
-}
-
-// ---- stable LSD radix sort of (key, value) pairs, 8 bits per pass ----------
-// A block takes RS_TILE consecutive items.  Pass part 1 counts the block's
-// digits; a scan over (digit, block) gives every block the output offset of
-// each digit; part 2 ranks the block's items stably (warp by warp, 32 items
-// at a time in input order: lanes with the same digit by a match, earlier
-// rounds and warps by shared counters) and scatters them.
-constexpr uint32_t RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
-
-__global__ void __launch_bounds__(RS_T) k_rs_hist(const unsigned long long* __restrict__ key, uint32_t cnt,
-                                                  uint32_t shift, uint32_t nblk, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    if (lane == 0 && mine) atomicAdd(&counts[0], mine);
     __syncthreads();
-    const uint32_t base = blockIdx.x * RS_TILE;
-    for (uint32_t i = threadIdx.x; i < RS_TILE; i += RS_T) {
-        const uint32_t q = base + i;
-        if (q < cnt) atomicAdd(&h[(uint32_t)(key[q] >> shift) & 0xFFu], 1u);
+    for (uint32_t i = threadIdx.x; i < 4 * 256; i += CT) {
+        const uint32_t x = (&h[0][0])[i];
+        if (x) atomicAdd(&hist[i], x);
     }
-    __syncthreads();
-    hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];  // digit-major for the scan
 }
 
-__global__ void __launch_bounds__(RS_T) k_rs_scatter(const unsigned long long* __restrict__ key_in,
-                                                     const uint32_t* __restrict__ val_in, uint32_t cnt, uint32_t shift,
-                                                     uint32_t nblk, const uint32_t* __restrict__ offs,
-                                                     unsigned long long* __restrict__ key_out,
-                                                     uint32_t* __restrict__ val_out) {
-    __shared__ uint32_t wcnt[RS_W][256];  // items of each digit seen so far by each warp
-    __shared__ uint32_t wpre[RS_W][256];  // exclusive prefix over warps (plus the digit's block start)
-    __shared__ uint32_t dstart[256];      // block-local start of each digit
-    __shared__ unsigned long long sk[RS_TILE];
-    __shared__ uint32_t sv[RS_TILE];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t i = threadIdx.x; i < RS_W * 256; i += RS_T) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    // warp w owns items [w * 32 RS_I, (w + 1) * 32 RS_I) of the tile, 32 per round in order
-    const uint32_t tile0 = blockIdx.x * RS_TILE;
-    const uint32_t base = tile0 + warp * 32 * RS_I;
-    const uint32_t nin = cnt > tile0 ? min(RS_TILE, cnt - tile0) : 0u;
-    const uint32_t lt = (1u << lane) - 1u;
-    unsigned long long k[RS_I];
-    uint32_t v[RS_I], d[RS_I], r[RS_I];
+// ---- items of the hash-sorted order that sit in runs of equal hashes longer than
+// one (groups of several edges, and pairs whose hashes collide): a tile of 4096
+// items per block, thread t holding chunks c = 0..3 of four items at tile offset
+// 1024 c + 4 t.  One launch counts them per tile; after a scan of the counts the
+// second takes them out in order, keyed by their pair.
+constexpr uint32_t RN_TILE = 4096;
+
+// bit j: item i + j is in such a run (items at or past cnt are not)
+__device__ __forceinline__ uint32_t run_bits(const uint32_t* __restrict__ key, uint64_t i, uint32_t cnt) {
+    const uint4 k = load4<true>(key, i, cnt);
+    const uint32_t prev = i > 0 && i - 1 < cnt ? key[i - 1] : ~k.x;
+    const uint32_t next = i + 4 < cnt ? key[i + 4] : ~k.w;
+    uint32_t f = 0;
+    if (i < cnt && (prev == k.x || (i + 1 < cnt && k.y == k.x))) f |= 1u;
+    if (i + 1 < cnt && (k.x == k.y || (i + 2 < cnt && k.z == k.y))) f |= 2u;
+    if (i + 2 < cnt && (k.y == k.z || (i + 3 < cnt && k.w == k.z))) f |= 4u;
+    if (i + 3 < cnt && (k.z == k.w || next == k.w)) f |= 8u;
+    return f;
+}
+
+__global__ void __launch_bounds__(CT) k_c_runs_count(const uint32_t* __restrict__ key, uint32_t cnt,
+                                                     uint32_t* __restrict__ tcount) {
+    __shared__ uint32_t ws[CT / 32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * RN_TILE + 4 * threadIdx.x;
+    uint32_t x = 0;
 #pragma unroll
-    for (int j = 0; j < (int)RS_I; j++) {
-        const uint32_t q = base + j * 32 + lane;
-        const bool ok = q < cnt;
-        k[j] = ok ? key_in[q] : 0ull;
-        v[j] = ok ? val_in[q] : 0u;
-        d[j] = ok ? (uint32_t)(k[j] >> shift) & 0xFFu : 256u + lane;  // lanes past the end match nobody
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d[j]);
-        r[j] = 0;
-        if (ok) {
-            const uint32_t before = wcnt[warp][d[j]];
-            r[j] = before + __popc(peers & lt);
-            __syncwarp(peers);
-            if ((peers >> lane) == 1u) wcnt[warp][d[j]] = before + __popc(peers);  // the group's last lane
-        }
-        __syncwarp();
-    }
+    for (int c = 0; c < 4; c++) x += __popc(run_bits(key, base + 1024 * c, cnt));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    if (lane == 0) ws[warp] = x;
     __syncthreads();
-    {
-        const uint32_t dg = threadIdx.x;  // one digit per thread: its total, then its block-local start
-        uint32_t run = 0;
-        for (int w = 0; w < (int)RS_W; w++) run += wcnt[w][dg];
-        // exclusive scan of the 256 digit totals across the block
-        uint32_t x = run;
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)(CT / 32); w++) t += ws[w];
+        tcount[blockIdx.x] = t;
+    }
+}
+
+// the run items in sorted order (so a pair's edges keep their input order), with
+// (min, max) of their coarse pair as the key of a second sort; counts[1] = how many.
+// The tile's run items are listed in shared memory first, so that the gathers of
+// their pairs spread over all threads.
+__global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
+                                                    uint32_t cnt, const uint32_t* __restrict__ toffs,
+                                                    const uint32_t* __restrict__ cpair, uint32_t bits,
+                                                    unsigned long long* __restrict__ skey,
+                                                    uint32_t* __restrict__ sval, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t ws[4][CT / 32];
+    __shared__ uint32_t list[RN_TILE];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t tile0 = (uint64_t)blockIdx.x * RN_TILE;
+    const uint64_t base = tile0 + 4 * threadIdx.x;
+    uint32_t f[4], incl[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        f[c] = run_bits(key, base + 1024 * c, cnt);
+        uint32_t x = __popc(f[c]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
+            if (lane >= (uint32_t)o) x += y;
         }
-        __shared__ uint32_t wsum[RS_W];
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; w++) before += wsum[w];
-        const uint32_t start = before + x - run;
-        dstart[dg] = start;
-        uint32_t acc = start;
-        for (int w = 0; w < (int)RS_W; w++) {
-            wpre[w][dg] = acc;
-            acc += wcnt[w][dg];
-        }
+        incl[c] = x;
+        if (lane == 31) ws[c][warp] = x;
     }
     __syncthreads();
-    // the tile in digit order in shared memory ...
+    uint32_t run = 0;
 #pragma unroll
-    for (int j = 0; j < (int)RS_I; j++) {
-        const uint32_t q = base + j * 32 + lane;
-        if (q >= cnt) continue;
-        const uint32_t p = wpre[warp][d[j]] + r[j];
-        sk[p] = k[j];
-        sv[p] = v[j];
+    for (int c = 0; c < 4; c++) {
+        uint32_t before = 0, total = 0;
+        for (uint32_t w = 0; w < CT / 32; w++) {
+            before += w < warp ? ws[c][w] : 0u;
+            total += ws[c][w];
+        }
+        uint32_t q = run + before + incl[c] - __popc(f[c]);
+        for (uint32_t bl = f[c]; bl; bl &= bl - 1) list[q++] = 1024 * c + 4 * threadIdx.x + __ffs(bl) - 1;
+        run += total;
     }
     __syncthreads();
-    // ... then written out: consecutive threads take consecutive items, which within
-    // a digit land on consecutive addresses
-    for (uint32_t p = threadIdx.x; p < nin; p += RS_T) {
-        const unsigned long long kk = sk[p];
-        const uint32_t dg = (uint32_t)(kk >> shift) & 0xFFu;
-        const uint32_t o = offs[dg * nblk + blockIdx.x] + (p - dstart[dg]);
-        key_out[o] = kk;
-        val_out[o] = sv[p];
+    const uint32_t off = toffs[blockIdx.x];
+    for (uint32_t q = threadIdx.x; q < run; q += CT) {
+        const uint32_t e = val[tile0 + list[q]];
+        const uint2 cp = *reinterpret_cast<const uint2*>(cpair + 2 * (size_t)e);
+        const uint32_t x = cp.x, y = cp.y;
+        skey[off + q] = ((unsigned long long)min(x, y) << bits) | max(x, y);  // coarse ids take `bits` bits
+        sval[off + q] = e;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) counts[1] = off + run;
+}
+
+// ---- stable LSD radix sort of (key, value) pairs, 8 bits per pass ----------
+// One-sweep form: a first read of the keys counts the digits of every pass at
+// once, which fixes where each digit's items start in every pass's output.  A
+// pass is then one launch.  A block takes the next tile in ticket order (so the
+// tiles before it belong to blocks that are already running), ranks its items
+// stably (warp by warp, 32 items at a time in input order: lanes with the same
+// digit by a match, earlier rounds and warps by shared counters), and learns
+// how many items of each digit the tiles before it hold by looking back over
+// their published counts: a tile publishes its own count at once and the
+// inclusive count as soon as it knows it, and a look-back stops at the first
+// inclusive count.  Each wait reads a bounded number of times; a wait that runs
+// out flags the error, publishes a count so that no later tile waits on it,
+// and the block writes nothing.
+constexpr uint32_t RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_PASSES = 8;
+constexpr unsigned long long RS_AGG = 1ull << 32, RS_INC = 2ull << 32;
+constexpr uint32_t RS_SPIN = 1u << 20, RS_LB = 8;
+constexpr uint32_t C_ERR_SORT = 4u;
+
+template <class K>
+struct RsSmem {
+    uint32_t wcnt[RS_W][256];  // items of each digit seen so far by each warp, then where the warp's start
+    uint32_t gofs[256];        // output position of the tile's first item of each digit, minus dstart
+    uint32_t wsum[RS_W];
+    uint32_t tile, bad;
+    K sk[RS_TILE];
+    uint32_t sv[RS_TILE];
+};
+
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// digit counts of passes 0 .. npass-1 over all items; hist is zero on entry
+template <class K>
+__global__ void __launch_bounds__(RS_T) k_rs_count(const K* __restrict__ key, uint32_t cnt, uint32_t npass,
+                                                   uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[RS_PASSES][256];
+    for (uint32_t i = threadIdx.x; i < RS_PASSES * 256; i += RS_T) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * RS_T + threadIdx.x; i < cnt; i += gridDim.x * RS_T) {
+        const K k = key[i];
+        for (uint32_t p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < npass * 256; i += RS_T) {
+        const uint32_t x = (&h[0][0])[i];
+        if (x) atomicAdd(&hist[i], x);
     }
 }
 
-// groups in sorted order (runs of equal keys; a run's first item is its leader,
-// the smallest edge index, since the sort is stable and the items entered in
-// input order).  Almost every group is a single edge, so instead of marking
-// the leaders (a scattered write per group) this clears the crossing flag of
-// every other member, and marks the leaders of groups with several edges
-// (a bit, and where their run starts).  The flags then say which edges lead.
+// exclusive prefix of each pass's 256 digit counts (one block per pass)
+__global__ void __launch_bounds__(256) k_rs_starts(const uint32_t* __restrict__ hist, uint32_t* __restrict__ start) {
+    __shared__ uint32_t ws[8];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t v = hist[blockIdx.x * 256 + threadIdx.x];
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (uint32_t w = 0; w < warp; w++) before += ws[w];
+    start[blockIdx.x * 256 + threadIdx.x] = before + x - v;
+}
+
+// val_in NULL: the values are the items' indices.  A block takes one tile, in
+// ticket order.
+template <class K>
+__global__ void __launch_bounds__(RS_T, sizeof(K) == 4 ? 3 : 2)
+    k_rs_pass(const K* __restrict__ key_in, const uint32_t* __restrict__ val_in, uint32_t cnt, uint32_t shift,
+              const uint32_t* __restrict__ start, unsigned long long* __restrict__ status,
+              uint32_t* __restrict__ ticket, uint32_t* __restrict__ err, K* __restrict__ key_out,
+              uint32_t* __restrict__ val_out) {
+    extern __shared__ __align__(16) unsigned char rs_raw[];
+    RsSmem<K>& S = *reinterpret_cast<RsSmem<K>*>(rs_raw);
+    auto& wcnt = S.wcnt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) {
+        S.tile = atomicAdd(ticket, 1u);
+        S.bad = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < RS_W * 256; i += RS_T) (&wcnt[0][0])[i] = 0;
+    K k[RS_I];
+    uint32_t v[RS_I], r[RS_I];
+    // warp w owns items [w * 32 RS_I, (w + 1) * 32 RS_I) of a tile, 32 per round in order
+    auto load = [&](uint32_t t) {
+        const uint32_t base = t * RS_TILE + warp * 32 * RS_I;
+#pragma unroll
+        for (int j = 0; j < (int)RS_I; j++) {
+            const uint32_t q = base + j * 32 + lane;
+            const bool ok = q < cnt;
+            k[j] = ok ? key_in[q] : (K)0;
+            v[j] = ok ? (val_in ? val_in[q] : q) : 0u;  // no values: each item's own index
+        }
+    };
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    load(tile);
+    const uint32_t tile0 = tile * RS_TILE;
+    const uint32_t base = tile0 + warp * 32 * RS_I;
+    const uint32_t nin = cnt > tile0 ? min(RS_TILE, cnt - tile0) : 0u;
+#pragma unroll
+    for (int j = 0; j < (int)RS_I; j++) {
+        const bool ok = base + j * 32 + lane < cnt;
+        const uint32_t d = (uint32_t)(k[j] >> shift) & 0xFFu;
+        // the lanes holding the same digit, from one ballot per digit bit (lanes past
+        // the end match nobody)
+        uint32_t peers = __ballot_sync(0xFFFFFFFFu, ok);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
+        // the whole warp reads, then each digit's last lane writes: no branch splits
+        // the warp by digit
+        const uint32_t before = ok ? wcnt[warp][d] : 0u;
+        r[j] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && (peers >> lane) == 1u) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const uint32_t dg = threadIdx.x;  // one digit per thread
+    uint32_t run = 0;
+    for (int w = 0; w < (int)RS_W; w++) run += wcnt[w][dg];
+    unsigned long long* my = status + (size_t)tile * 256 + dg;
+    st_status(my, (tile == 0 ? RS_INC : RS_AGG) | run);
+    // exclusive scan of the 256 digit totals across the tile
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) S.wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; w++) before += S.wsum[w];
+    const uint32_t dst = before + x - run;
+    {
+        uint32_t acc = dst;
+        for (int w = 0; w < (int)RS_W; w++) {
+            const uint32_t c = wcnt[w][dg];
+            wcnt[w][dg] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    // the tile in digit order in shared memory
+#pragma unroll
+    for (int j = 0; j < (int)RS_I; j++) {
+        if (base + j * 32 + lane >= cnt) continue;
+        const uint32_t p = wcnt[warp][(uint32_t)(k[j] >> shift) & 0xFFu] + r[j];
+        S.sk[p] = k[j];
+        S.sv[p] = v[j];
+    }
+    // items of this digit in the tiles before this one, read RS_LB tiles per round
+    // trip (a look-back of one tile at a time would make its length the pass's limit)
+    uint32_t excl = 0;
+    bool ok = true, done = false;
+    for (uint32_t t = tile; t > 0 && !done;) {
+        const uint32_t nw = min(t, RS_LB);
+        unsigned long long sv[RS_LB];
+#pragma unroll
+        for (uint32_t i = 0; i < RS_LB; i++)
+            if (i < nw) sv[i] = ld_status(status + (size_t)(t - 1 - i) * 256 + dg);
+#pragma unroll
+        for (uint32_t i = 0; i < RS_LB; i++) {
+            if (i >= nw || done) continue;
+            unsigned long long y = sv[i];
+            uint32_t spin = 0;
+            while ((y >> 32) == 0 && ++spin < RS_SPIN) y = ld_status(status + (size_t)(t - 1 - i) * 256 + dg);
+            if ((y >> 32) == 0) {
+                ok = false;
+                done = true;
+                continue;
+            }
+            excl += (uint32_t)y;
+            if (y & RS_INC) done = true;
+        }
+        t -= nw;
+    }
+    if (tile > 0) st_status(my, RS_INC | (excl + run));
+    if (!ok) {
+        S.bad = 1;
+        atomicOr(err, C_ERR_SORT);
+    }
+    S.gofs[dg] = start[dg] + excl - dst;
+    __syncthreads();
+    if (S.bad) return;
+    // written out: consecutive threads take consecutive items, which within a digit
+    // land on consecutive addresses
+    for (uint32_t p = threadIdx.x; p < nin; p += RS_T) {
+        const K kk = S.sk[p];
+        const uint32_t o = S.gofs[(uint32_t)(kk >> shift) & 0xFFu] + p;
+        if (o < cnt) {
+            key_out[o] = kk;
+            val_out[o] = S.sv[p];
+        }
+    }
+}
+
+// groups in pair order (runs of equal keys; a run's first item is its leader, the
+// smallest edge index, since the sort is stable and a pair's edges entered in
+// input order).  Every other member loses its bit in cross; the leader of a
+// group of several edges gets a bit in multi and, in gsum, the float32 bits of
+// the group's weight: the sum in double over its edges in input order, rounded once.
 __global__ void k_c_marks(const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt,
-                          uint32_t* __restrict__ lead, uint32_t* __restrict__ multi, uint32_t* __restrict__ gref) {
+                          const float* __restrict__ w, uint32_t* __restrict__ cross, uint32_t* __restrict__ multi,
+                          uint32_t* __restrict__ gsum) {
     for (uint32_t i = blockIdx.x * CT + threadIdx.x; i < cnt; i += gridDim.x * CT) {
         const unsigned long long k = key[i];
         const uint32_t e = val[i];
         if (i > 0 && k == key[i - 1]) {
-            lead[e] = 0u;
+            atomicAnd(&cross[e >> 5], ~(1u << (e & 31)));
         } else if (i + 1 < cnt && key[i + 1] == k) {
+            double sum = (double)w[e];
+            uint32_t j = i + 1;
+            // members four at a time: their loads issue together, the additions stay in order
+            for (bool more = true; more;) {
+                uint32_t vj[4];
+                bool in[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    in[t] = j + t < cnt && key[j + t] == k;
+                    vj[t] = in[t] ? val[j + t] : 0u;
+                }
+                float wj[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) wj[t] = in[t] ? w[vj[t]] : 0.0f;
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    if (in[t]) sum += (double)wj[t];
+                more = in[3];
+                j += 4;
+            }
             atomicOr(&multi[e >> 5], 1u << (e & 31));
-            gref[e] = i;
+            gsum[e] = __float_as_uint((float)sum);
         }
     }
 }
 
+// leaders per word of cross (wlead[words] = 0, so that the scan's last entry is the total)
+__global__ void k_c_wcount(const uint32_t* __restrict__ cross, uint32_t words, uint32_t* __restrict__ wlead) {
+    for (uint32_t i = blockIdx.x * CT + threadIdx.x; i <= words; i += gridDim.x * CT)
+        wlead[i] = i < words ? __popc(cross[i]) : 0u;
+}
+
 // the leaders, in input order, write their coarse edge at their rank among the
-// leaders; the weight is the group's sum over its edges in input order (a single
-// edge's own weight, which double and back leaves unchanged)
-__global__ void k_c_emit(uint32_t m, const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev,
-                         const float* __restrict__ w, const uint32_t* __restrict__ cmap,
-                         const uint32_t* __restrict__ lead, const uint32_t* __restrict__ multi,
-                         const uint32_t* __restrict__ pos, const uint32_t* __restrict__ gref,
-                         const unsigned long long* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt,
-                         uint32_t* __restrict__ ceu, uint32_t* __restrict__ cev, float* __restrict__ cw) {
-    for (uint32_t e = blockIdx.x * CT + threadIdx.x; e < m; e += gridDim.x * CT) {
-        if (!lead[e]) continue;
-        const uint32_t p = pos[e];
-        float we = w[e];
-        if ((__ldg(&multi[e >> 5]) >> (e & 31)) & 1u) {
-            const uint32_t i0 = gref[e];
-            const unsigned long long k = key[i0];
-            double sum = 0.0;
-            for (uint32_t i = i0; i < cnt && key[i] == k; i++) sum += (double)w[val[i]];
-            we = (float)sum;
+// leaders, with their group's weight (a single edge's own weight, which double and
+// back leaves unchanged)
+template <bool VEC>
+__global__ void __launch_bounds__(CT) k_c_emit(uint32_t m, const uint32_t* __restrict__ cpair,
+                                               const float* __restrict__ w, const uint32_t* __restrict__ cross,
+                                               const uint32_t* __restrict__ wpos, const uint32_t* __restrict__ multi,
+                                               const uint32_t* __restrict__ gsum, uint32_t* __restrict__ ceu,
+                                               uint32_t* __restrict__ cev, float* __restrict__ cw) {
+    // a block takes 1024 edges (32 words of cross) at a time; their leaders fill one
+    // run of the output, staged here and written out contiguously
+    __shared__ uint32_t su[4 * CT], sv2[4 * CT], sw[4 * CT];
+    const uint32_t groups = (uint32_t)(((uint64_t)m + 3) / 4);
+    const uint32_t words = (uint32_t)(((uint64_t)m + 31) / 32);
+    const uint32_t* wb = reinterpret_cast<const uint32_t*>(w);
+    for (uint32_t c0 = blockIdx.x * CT; c0 < groups; c0 += gridDim.x * CT) {
+        const uint32_t g = c0 + threadIdx.x;
+        const uint32_t w0 = c0 >> 3, w1 = min(w0 + CT / 8, words);
+        const uint32_t obase = wpos[w0], ocount = wpos[w1] - obase;
+        if (g < groups) {
+            const uint64_t e0 = 4ull * g;
+            // every load of the group at once (most edges lead); cpair is aligned scratch
+            const uint32_t word = cross[g >> 3], wp = wpos[g >> 3], mw = __ldg(&multi[g >> 3]);
+            const uint4 x = load4<VEC>(wb, e0, m);
+            const uint4 p0 = load4<true>(cpair, 2 * e0, 2 * m), p1 = load4<true>(cpair, 2 * e0 + 4, 2 * m);
+            const uint32_t sh = 4 * (g & 7);
+            const uint32_t nib = (word >> sh) & 0xFu, mb = (mw >> sh) & 0xFu;
+            uint32_t p = wp - obase + __popc(word & ((1u << sh) - 1u));
+            const uint32_t cu[4] = {p0.x, p0.z, p1.x, p1.z}, cv[4] = {p0.y, p0.w, p1.y, p1.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (!((nib >> j) & 1u)) continue;
+                su[p] = cu[j];
+                sv2[p] = cv[j];
+                sw[p] = ((mb >> j) & 1u) ? gsum[(uint32_t)e0 + j] : at(x, j);
+                p++;
+            }
         }
-        ceu[p] = cmap[eu[e]];
-        cev[p] = cmap[ev[e]];
-        cw[p] = we;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < ocount; i += CT) {
+            ceu[obase + i] = su[i];
+            cev[obase + i] = sv2[i];
+            cw[obase + i] = __uint_as_float(sw[i]);
+        }
+        __syncthreads();
     }
 }
 
@@ -256,10 +585,10 @@ uint32_t bits_for(uint32_t x) {  // bits to write 0 .. x
 
 }  // namespace
 
-size_t contract_sort_tmp_words(uint32_t m) {
-    const uint64_t nblk = ((uint64_t)m + RS_TILE - 1) / RS_TILE;
-    return (size_t)(256 * nblk + 1);
+size_t contract_status_entries(uint32_t m) {
+    return (size_t)(((uint64_t)m + RS_TILE - 1) / RS_TILE) * 256 + 1;
 }
+size_t contract_digit_words() { return 2 * RS_PASSES * 256 + RS_PASSES; }
 
 int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot) {
     cudaStream_t s = (cudaStream_t)stream;
@@ -271,39 +600,105 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     if (int r = launch_exclusive_scan(s, c.flag, c.rank, c.n + 1, c.scan_tmp, c.scan_words)) return r;
     k_c_map<<<grid_for(c.n), CT, 0, s>>>(c.mate, c.n, c.rank, c.vw, c.cmap, c.cvw);
     if (c.m == 0) return (int)cudaGetLastError();
-    // the coarse vertex count decides the key's width: read it on the host
+    if ((e = cudaFuncSetAttribute(k_rs_pass<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(RsSmem<uint32_t>)))) return (int)e;
+    if ((e = cudaFuncSetAttribute(k_rs_pass<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(RsSmem<unsigned long long>)))) return (int)e;
+    // stable sort by the low `bits` bits of the keys (8-bit digits), ping-ponging
+    // between the two buffers; *cur tells which holds the result
+    // (ident: the values are the items' indices, and v0 is not read)
+    // (counted: the digits of the keys are in hist already, and the tickets zero)
+    auto radix = [&](auto* k0, auto* k1, uint32_t* v0, uint32_t* v1, uint32_t cnt, uint32_t bits, bool ident,
+                     bool counted, int* cur) -> int {
+        using K = typename std::remove_pointer<decltype(k0)>::type;
+        K* kk[2] = {k0, k1};
+        uint32_t* vv[2] = {v0, v1};
+        *cur = 0;
+        if (cnt < 2) return 0;
+        const uint32_t npass = (bits + 7) / 8;
+        const uint32_t tiles = (cnt + RS_TILE - 1) / RS_TILE;
+        uint32_t* hist = c.digits;
+        uint32_t* starts = c.digits + RS_PASSES * 256;
+        uint32_t* tickets = c.digits + 2 * RS_PASSES * 256;
+        cudaError_t ce;
+        if (!counted) {
+            if ((ce = cudaMemsetAsync(c.digits, 0, contract_digit_words() * sizeof(uint32_t), s))) return (int)ce;
+            k_rs_count<K><<<grid_for((uint64_t)cnt / 8), RS_T, 0, s>>>(k0, cnt, npass, hist);
+        }
+        k_rs_starts<<<npass, 256, 0, s>>>(hist, starts);
+        for (uint32_t p = 0; p < npass; p++) {
+            if ((ce = cudaMemsetAsync(c.status, 0, (size_t)tiles * 256 * sizeof(unsigned long long), s))) return (int)ce;
+            const uint32_t* vin = (ident && p == 0) ? nullptr : vv[*cur];
+            k_rs_pass<K><<<tiles, RS_T, sizeof(RsSmem<K>), s>>>(kk[*cur], vin, cnt, 8 * p, starts + 256 * p,
+                                                                c.status, tickets + p, c.err, kk[*cur ^ 1],
+                                                                vv[*cur ^ 1]);
+            *cur ^= 1;
+        }
+        return (int)cudaGetLastError();
+    };
+    // 1. every edge keyed by its pair's hash in input order; the stable sort keeps input
+    //    order among equal keys and puts the edges inside pairs last, after the mc crossing edges
+    uint32_t* hk[2] = {reinterpret_cast<uint32_t*>(c.key[0]), reinterpret_cast<uint32_t*>(c.key[1])};
+    const uint32_t words = (uint32_t)(((uint64_t)c.m + 31) / 32);
+    const uint32_t egrid = grid_for(((uint64_t)c.m + 3) / 4);
+    const bool vec = ((reinterpret_cast<uintptr_t>(c.eu) | reinterpret_cast<uintptr_t>(c.ev) |
+                       reinterpret_cast<uintptr_t>(c.w)) & 15u) == 0;
+    if ((e = cudaMemsetAsync(c.counts, 0, 4 * sizeof(uint32_t), s))) return (int)e;
+    if ((e = cudaMemsetAsync(c.digits, 0, contract_digit_words() * sizeof(uint32_t), s))) return (int)e;
+    const uint32_t kgrid = grid_for(((uint64_t)c.m + 7) / 8);
+    if (vec)
+        k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.digits,
+                                            c.err);
+    else
+        k_c_keys<false><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.digits,
+                                             c.err);
+    if ((e = cudaMemcpyAsync(mc_host_slot, c.counts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaMemcpyAsync(mc_host_slot + 1, c.rank + c.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaStreamSynchronize(s))) return (int)e;
-    const uint32_t nc = mc_host_slot[1];
-    const uint32_t bits = bits_for(nc);  // coarse ids 0 .. nc - 1 and the pair key's top value stay apart
-    // every edge keyed in input order; the stable sort keeps input order among equal keys
-    // and puts the edges inside pairs last, after the mc crossing edges
-    if ((e = cudaMemsetAsync(c.cross + c.m, 0, sizeof(uint32_t), s))) return (int)e;
-    if ((e = cudaMemsetAsync(c.cpos, 0, sizeof(uint32_t), s))) return (int)e;
-    k_c_keys<<<grid_for(c.m), CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, bits, c.key[0], c.val[0], c.cross, c.cpos,
-                                          c.err);
-    if ((e = cudaMemcpyAsync(mc_host_slot, c.cpos, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
-    if ((e = cudaStreamSynchronize(s))) return (int)e;
-    const uint32_t mc = mc_host_slot[0];
-    // radix passes over the key's 2 * bits significant bits
-    int cur = 0;
-    const uint32_t ns = mc < c.m ? c.m : mc;  // the crossing edges and, past them, the ones inside pairs
-    if (mc > 1 || (mc && ns > mc)) {
-        const uint32_t nblk = (ns + RS_TILE - 1) / RS_TILE;
-        for (uint32_t shift = 0; shift < 2 * bits; shift += 8) {
-            k_rs_hist<<<nblk, RS_T, 0, s>>>(c.key[cur], ns, shift, nblk, c.hist);
-            if (int r = launch_exclusive_scan(s, c.hist, c.hoff, 256 * nblk, c.scan_tmp, c.scan_words)) return r;
-            k_rs_scatter<<<nblk, RS_T, 0, s>>>(c.key[cur], c.val[cur], ns, shift, nblk, c.hoff, c.key[cur ^ 1],
-                                               c.val[cur ^ 1]);
-            cur ^= 1;
-        }
+    const uint32_t mc = mc_host_slot[0], nc = mc_host_slot[1];
+    int hc = 0;
+    if (mc > 1)
+        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, true, &hc)) return r;
+    // 2. runs of equal hash longer than one (groups of several edges, and collisions),
+    //    taken out in sorted order with their pair as the key, and sorted again by the pair
+    uint32_t nsub = 0;
+    const uint32_t bits = bits_for(nc ? nc - 1 : 0);
+    if (mc > 1) {
+        const uint32_t tiles = (mc + RN_TILE - 1) / RN_TILE;
+        const uint32_t* hv = c.val[hc];
+        uint32_t* toffs = c.tsum + ((size_t)c.m / RN_TILE + 2);
+        k_c_runs_count<<<tiles, CT, 0, s>>>(hk[hc], mc, c.tsum);
+        if (int r = launch_exclusive_scan(s, c.tsum, toffs, tiles, c.scan_tmp, c.scan_words)) return r;
+        k_c_runs_take<<<tiles, CT, 0, s>>>(hk[hc], hv, mc, toffs, c.cpair, bits, c.key[hc ^ 1],
+                                           c.val[hc ^ 1], c.counts);
+        if ((e = cudaMemcpyAsync(mc_host_slot + 2, c.counts + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)))
+            return (int)e;
+        if ((e = cudaStreamSynchronize(s))) return (int)e;
+        nsub = mc_host_slot[2];
     }
-    // the crossing flags become the leader flags: other members are cleared
+    // the subset's two buffers: the ones the hash sort did not end in, and, once the
+    // subset is taken out, the ones it did
+    unsigned long long* sk[2] = {c.key[hc ^ 1], c.key[hc]};
+    uint32_t* sv[2] = {c.val[hc ^ 1], c.val[hc]};
+    int cur = 0;
+    if (nsub)
+        if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, false, &cur)) return r;
+    // 3. the crossing bits become the leader bits: other members are cleared
     if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
-    if (mc) k_c_marks<<<grid_for(mc), CT, 0, s>>>(c.key[cur], c.val[cur], mc, c.cross, c.multi, c.gref);
-    if (int r = launch_exclusive_scan(s, c.cross, c.pos, c.m + 1, c.scan_tmp, c.scan_words)) return r;
-    k_c_emit<<<grid_for(c.m), CT, 0, s>>>(c.m, c.eu, c.ev, c.w, c.cmap, c.cross, c.multi, c.pos, c.gref, c.key[cur],
-                                          c.val[cur], mc, c.ceu, c.cev, c.cw);
+    if (nsub) k_c_marks<<<grid_for(nsub), CT, 0, s>>>(sk[cur], sv[cur], nsub, c.w, c.cross, c.multi, c.gref);
+    // 4. leaders ranked by words of the bitmask; the leaders write the coarse edges
+    k_c_wcount<<<grid_for((uint64_t)words + 1), CT, 0, s>>>(c.cross, words, c.wlead);
+    if (int r = launch_exclusive_scan(s, c.wlead, c.wpos, words + 1, c.scan_tmp, c.scan_words)) return r;
+    if ((e = cudaMemcpyAsync(c.counts + 2, c.wpos + words, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)))
+        return (int)e;
+    if (mc) {
+        if (vec)
+            k_c_emit<true><<<egrid, CT, 0, s>>>(c.m, c.cpair, c.w, c.cross, c.wpos, c.multi, c.gref, c.ceu, c.cev,
+                                                c.cw);
+        else
+            k_c_emit<false><<<egrid, CT, 0, s>>>(c.m, c.cpair, c.w, c.cross, c.wpos, c.multi, c.gref, c.ceu, c.cev,
+                                                 c.cw);
+    }
     return (int)cudaGetLastError();
 }
 

@@ -285,20 +285,24 @@ struct ContractArgs {
     float* cw;
     uint32_t* flag;           // [n + 1] representative flags
     uint32_t* rank;           // [n + 1] their exclusive prefix (rank[n] = coarse vertices)
-    uint32_t* cross;          // [m + 1] crossing-edge flags, then leader flags
-    uint32_t* cpos;           // [1] crossing edges (counted while keying)
+    uint32_t* cross;          // [m / 32 + 2] bit e: edge e joins two coarse vertices, then: it leads its group
+    uint32_t* counts;         // [4] crossing edges, items in runs of equal hash, coarse edges
+    uint32_t* cpair;          // [2 m] coarse endpoints of every edge, cmap[eu[e]] then cmap[ev[e]]
     unsigned long long* key[2];  // [m] coarse pair of each crossing edge (radix ping-pong)
     uint32_t* val[2];         // [m] its edge index
-    uint32_t* hist;           // [256 * blocks] digit counts of a radix pass
-    uint32_t* hoff;           // [256 * blocks + 1] their exclusive prefix
+    unsigned long long* status;  // [tiles * 256] a radix pass's per-tile digit counts (look-back)
+    uint32_t* digits;         // [8 * 256] digit counts of every pass, [8 * 256] their starts, [8] tile tickets
     uint32_t* multi;          // [m / 32 + 2] bit e: edge e leads a group of several edges
-    uint32_t* pos;            // [m + 1] exclusive prefix of the leader flags (pos[m] = coarse edges)
-    uint32_t* gref;           // [m] a leader's group start in sorted order
+    uint32_t* wlead;          // [m / 32 + 2] leaders per word of cross
+    uint32_t* wpos;           // [m / 32 + 2] their exclusive prefix (wpos[words] = coarse edges)
+    uint32_t* tsum;           // [2 * (m / 4096 + 2)] per-tile counts of run items and their prefix
+    uint32_t* gref;           // [m] float32 bits of the weight of a group led by edge e (groups of several edges)
     uint32_t* scan_tmp;
     size_t scan_words;
-    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n
+    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n, 4: a sort's look-back gave up
 };
-size_t contract_sort_tmp_words(uint32_t m);  // words of hist (and of hoff, plus one)
+size_t contract_status_entries(uint32_t m);  // entries of status
+size_t contract_digit_words();               // words of digits
 // runs every step; mc_host_slot: 2 pinned words (crossing edges and coarse vertices
 // are read back once, to size the sort); returns a cudaError_t value
 int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot);

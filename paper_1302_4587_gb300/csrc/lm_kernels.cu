@@ -1660,50 +1660,89 @@ __global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase,
     }
 }
 
-// ---------------------------------------------------------------- exclusive scan (graph set-up only)
-constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 16, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// ---------------------------------------------------------------- exclusive scan (set-up and contraction)
+// A block scans a tile of 4096 words in two launches (tile sums, then the tiles'
+// prefixes applied), recursing on the tile sums.  Thread t holds four chunks of
+// four consecutive words, chunk c at tile offset 1024 c + 4 t, so every warp
+// load and store moves 512 contiguous bytes; one block scan runs over the four
+// chunk sums of every thread at once.  Unaligned arrays take scalar accesses.
+constexpr int SCAN_THREADS = 256, SCAN_CHUNKS = 4, SCAN_TILE = SCAN_THREADS * 4 * SCAN_CHUNKS;
 
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* tmp, uint32_t& total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t incl = warp_incl_scan(x, lane);
-    if (lane == 31) tmp[warp] = incl;
-    __syncthreads();
-    uint32_t before = 0;
-    total = 0;
-    for (int w = 0; w < SCAN_THREADS / 32; w++) {
-        if (w < warp) before += tmp[w];
-        total += tmp[w];
-    }
-    __syncthreads();
-    return before + incl - x;
+template <bool VEC>
+__device__ __forceinline__ uint4 scan_load4(const uint32_t* in, uint64_t i, uint32_t count) {
+    if (VEC && i + 4 <= count) return *reinterpret_cast<const uint4*>(in + i);
+    uint4 v;
+    v.x = i < count ? in[i] : 0u;
+    v.y = i + 1 < count ? in[i + 1] : 0u;
+    v.z = i + 2 < count ? in[i + 2] : 0u;
+    v.w = i + 3 < count ? in[i + 3] : 0u;
+    return v;
 }
 
+template <bool VEC>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* in, uint32_t count, uint32_t* sums) {
     __shared__ uint32_t tmp[SCAN_THREADS / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    uint4 v[SCAN_CHUNKS];
+#pragma unroll
+    for (int c = 0; c < SCAN_CHUNKS; c++) v[c] = scan_load4<VEC>(in, base + 1024 * c, count);
     uint32_t x = 0;
-    for (int i = 0; i < SCAN_ITEMS; i++)
-        if (base + i < count) x += in[base + i];
-    uint32_t total;
-    block_excl_scan(x, tmp, total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+#pragma unroll
+    for (int c = 0; c < SCAN_CHUNKS; c++) x += v[c].x + v[c].y + v[c].z + v[c].w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    if (lane == 0) tmp[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; w++) t += tmp[w];
+        sums[blockIdx.x] = t;
+    }
 }
 
+template <bool VEC>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* in, uint32_t count,
                                                              const uint32_t* offsets, uint32_t* out) {
-    __shared__ uint32_t tmp[SCAN_THREADS / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS];
-    uint32_t x = 0;
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        v[i] = (base + i < count) ? in[base + i] : 0u;
-        x += v[i];
+    __shared__ uint32_t tmp[SCAN_CHUNKS][SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    uint4 v[SCAN_CHUNKS];
+    uint32_t incl[SCAN_CHUNKS], own[SCAN_CHUNKS];
+#pragma unroll
+    for (int c = 0; c < SCAN_CHUNKS; c++) {
+        v[c] = scan_load4<VEC>(in, base + 1024 * c, count);
+        own[c] = v[c].x + v[c].y + v[c].z + v[c].w;
+        incl[c] = warp_incl_scan(own[c], lane);
+        if (lane == 31) tmp[c][warp] = incl[c];
     }
-    uint32_t total;
-    uint32_t run = block_excl_scan(x, tmp, total) + (offsets ? offsets[blockIdx.x] : 0u);
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        if (base + i < count) out[base + i] = run;
-        run += v[i];
+    __syncthreads();
+    // chunk c starts after every earlier chunk of the tile; within it, after the
+    // earlier warps and lanes
+    uint32_t run = offsets ? offsets[blockIdx.x] : 0u;
+#pragma unroll
+    for (int c = 0; c < SCAN_CHUNKS; c++) {
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; w++) {
+            const uint32_t t = tmp[c][w];
+            before += w < warp ? t : 0u;
+            total += t;
+        }
+        uint4 o;
+        o.x = run + before + incl[c] - own[c];
+        o.y = o.x + v[c].x;
+        o.z = o.y + v[c].y;
+        o.w = o.z + v[c].z;
+        const uint64_t i = base + 1024 * c;
+        if (VEC && i + 4 <= count) {
+            *reinterpret_cast<uint4*>(out + i) = o;
+        } else {
+            if (i < count) out[i] = o.x;
+            if (i + 1 < count) out[i + 1] = o.y;
+            if (i + 2 < count) out[i + 2] = o.z;
+            if (i + 3 < count) out[i + 3] = o.w;
+        }
+        run += total;
     }
 }
 
@@ -1712,7 +1751,7 @@ size_t exclusive_scan_tmp_words(uint32_t count) {
     uint64_t c = count;
     while (c > SCAN_TILE) {
         c = (c + SCAN_TILE - 1) / SCAN_TILE;
-        words += 2 * c + 2;  // block sums and their scan at this level
+        words += 2 * ((c + 3) & ~3ull) + 4;  // block sums and their scan at this level, 16-byte aligned
     }
     return words + 4;
 }
@@ -1721,19 +1760,23 @@ int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint3
                           size_t tmp_words) {
     cudaStream_t s = (cudaStream_t)stream;
     if (count == 0) return 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
     const uint32_t blocks = (count + SCAN_TILE - 1) / SCAN_TILE;
     if (blocks == 1) {
-        k_scan_apply<<<1, SCAN_THREADS, 0, s>>>(in, count, nullptr, out);
+        if (vec) k_scan_apply<true><<<1, SCAN_THREADS, 0, s>>>(in, count, nullptr, out);
+        else k_scan_apply<false><<<1, SCAN_THREADS, 0, s>>>(in, count, nullptr, out);
         return (int)cudaGetLastError();
     }
-    if (tmp_words < (size_t)blocks * 2 + 2) return (int)cudaErrorInvalidValue;
+    const size_t bw = ((size_t)blocks + 3) & ~(size_t)3;
+    if (tmp_words < 2 * bw + 4) return (int)cudaErrorInvalidValue;
     uint32_t* sums = tmp;
-    uint32_t* sums_scan = tmp + blocks;
-    k_scan_reduce<<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums);
-    int e = launch_exclusive_scan(stream, sums, sums_scan, blocks, tmp + 2 * (size_t)blocks,
-                                  tmp_words - 2 * (size_t)blocks);
+    uint32_t* sums_scan = tmp + bw;
+    if (vec) k_scan_reduce<true><<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums);
+    else k_scan_reduce<false><<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums);
+    int e = launch_exclusive_scan(stream, sums, sums_scan, blocks, tmp + 2 * bw, tmp_words - 2 * bw);
     if (e) return e;
-    k_scan_apply<<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums_scan, out);
+    if (vec) k_scan_apply<true><<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums_scan, out);
+    else k_scan_apply<false><<<blocks, SCAN_THREADS, 0, s>>>(in, count, sums_scan, out);
     return (int)cudaGetLastError();
 }
 

@@ -114,6 +114,51 @@ def test_edge_cases(lmc):
     _same(_contract(lmc, 4, eu, ev, w, mate), oracle.contract(4, eu, ev, w, mate))
 
 
+def _contract_offset(L, n, eu, ev, w, mate):
+    # the same arrays one element into a device buffer: 4-byte but not 16-byte aligned
+    torch, lm = L.torch, L.lm
+    def shifted(a, dt):
+        b = np.concatenate([np.zeros(1, a.dtype), a])
+        return _dev(torch, b, dt)[1:]
+    args = [shifted(eu, np.int32), shifted(ev, np.int32), shifted(w, np.float32),
+            _dev(torch, mate.astype(np.uint32), np.int32)]
+    assert args[0].data_ptr() % 16 != 0
+    cmap, cvw, ceu, cev, cw = lm.lm_contract(L.ctx, n, *args)
+    return (to_u32(cmap), to_u32(cvw), to_u32(ceu), to_u32(cev), cw.cpu().numpy())
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 31, 33, 127, 129, 4095, 4097, 3 * 4096 + 7])
+def test_ragged_sizes_and_unaligned_arrays(lmc, m):
+    # edge counts around the 4-edge groups, 32-edge words and 4096-item tiles, with
+    # parallel edges in both orientations, aligned and one element off
+    rng = np.random.default_rng(m)
+    n = max(4, m // 3)
+    eu = rng.integers(0, n, m).astype(np.uint32)
+    ev = ((eu + 1 + rng.integers(0, n - 1, m)) % n).astype(np.uint32)
+    k = m // 4
+    eu[m - k:], ev[m - k:] = ev[:k], eu[:k]
+    w = synth.weights(m, m + 1)
+    mate = oracle.greedy(n, eu, ev, w, 5)
+    want = oracle.contract(n, eu, ev, w, mate)
+    _same(_contract(lmc, n, eu, ev, w, mate), want)
+    _same(_contract_offset(lmc, n, eu, ev, w, mate), want)
+
+
+def test_one_pair_holds_every_edge(lmc):
+    # two matched pairs, 10,000 parallel edges between them: one group, summed in input order
+    m = 10_000
+    rng = np.random.default_rng(9)
+    eu = rng.integers(0, 2, m).astype(np.uint32)
+    ev = (2 + rng.integers(0, 2, m)).astype(np.uint32)
+    sw = rng.random(m) < 0.5
+    eu[sw], ev[sw] = ev[sw], eu[sw]
+    w = (rng.random(m) * 10 ** rng.uniform(-3, 3, m)).astype(np.float32)
+    mate = np.array([1, 0, 3, 2], np.uint32)
+    want = oracle.contract(4, eu, ev, w, mate)
+    assert want[2].shape[0] == 1
+    _same(_contract(lmc, 4, eu, ev, w, mate), want)
+
+
 def test_refusals(lmc):
     lm, torch = lmc.lm, lmc.torch
     eu = _dev(torch, np.array([0, 1], np.uint32), np.int32)
