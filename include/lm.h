@@ -298,8 +298,7 @@ int  lm_match_small_noalloc(uint32_t n, uint32_t m, const uint32_t* eu, const ui
  * Runs on the context's stream and returns when the outputs are complete; the
  * caller owns every array.  Errors: LM_EINVAL (null or host pointer; mate not
  * a matching of the vertex set; an endpoint >= n; m >= 2^31; n = 2^32 - 1),
- * LM_ENOMEM, LM_ETIMEOUT (a bounded wait inside the sort gave up; the outputs
- * are then incomplete, the context stays usable), LM_ECUDA. */
+ * LM_ENOMEM, LM_ECUDA. */
 int  lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const uint32_t* ev, const float* w,
                  const uint32_t* vw, const uint32_t* mate, uint32_t* cmap, uint32_t* cvw, uint32_t* ceu,
                  uint32_t* cev, float* cw, uint32_t* n_out, uint32_t* m_out);

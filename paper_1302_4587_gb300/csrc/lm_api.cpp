@@ -1033,8 +1033,7 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     cv.add(&c.key[1], M);
     cv.add(&c.val[0], M);
     cv.add(&c.val[1], M);
-    cv.add(&c.status, contract_status_entries(m));
-    cv.add(&c.digits, contract_digit_words());
+    cv.add(&c.shist, contract_sort_words(m));
     cv.add(&c.multi, (size_t)m / 32 + 2);
     cv.add(&c.wlead, W);
     cv.add(&c.wpos, W);
@@ -1069,7 +1068,6 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     if (ce != cudaSuccess) return fail(ctx, LM_ECUDA, "contraction: %s", cudaGetErrorString(ce));
     if (hp[0] & 1u) return fail(ctx, LM_EINVAL, "mate is not a matching of the vertex set");
     if (hp[0] & 2u) return fail(ctx, LM_EINVAL, "an edge endpoint is >= n");
-    if (hp[0] & 4u) return fail(ctx, LM_ETIMEOUT, "contraction: a radix pass's look-back wait gave up");
     *n_out = hp[1];
     *m_out = hp[2];
     return LM_OK;

@@ -96,18 +96,15 @@ __device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? 
 // every edge in input order, keyed by a hash of its unordered coarse pair (equal
 // pairs get equal keys); an edge inside a pair (or with an endpoint >= n) gets the
 // key 0xFFFFFFFF, above every pair's, so the sort puts it at the end.  Bit e of
-// cross: edge e joins two coarse vertices (counted in counts[0]).  The keys' four
-// digits are counted into hist[0 .. 1024) for the sort.  A warp takes 64 groups of
-// four edges per step, their loads issued together.
+// cross: edge e joins two coarse vertices (counted in counts[0]); cpair: the
+// coarse endpoints of every edge.  A warp takes 64 groups of four edges per step,
+// their loads issued together.
 template <bool VEC>
 __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev,
                                                uint32_t m, uint32_t n, const uint32_t* __restrict__ cmap,
                                                uint32_t* __restrict__ key, uint32_t* __restrict__ cpair,
                                                uint32_t* __restrict__ cross, uint32_t* __restrict__ counts,
-                                               uint32_t* __restrict__ hist, uint32_t* __restrict__ err) {
-    __shared__ uint32_t h[4][256];
-    for (uint32_t i = threadIdx.x; i < 4 * 256; i += CT) (&h[0][0])[i] = 0;
-    __syncthreads();
+                                               uint32_t* __restrict__ err) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t groups = (uint32_t)(((uint64_t)m + 3) / 4);
     uint32_t mine = 0;
@@ -146,8 +143,6 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
                     k[j] = pair_hash(pair_word(cu[u][j], cv[u][j]));
                     nib |= 1u << j;
                 }
-#pragma unroll
-                for (int d = 0; d < 4; d++) atomicAdd(&h[d][(k[j] >> (8 * d)) & 0xFFu], 1u);
             }
             if (e0 + 4 <= m) {  // key and cpair are 16-byte aligned scratch
                 *reinterpret_cast<uint4*>(key + e0) = make_uint4(k[0], k[1], k[2], k[3]);
@@ -174,11 +169,6 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
     if (lane == 0 && mine) atomicAdd(&counts[0], mine);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < 4 * 256; i += CT) {
-        const uint32_t x = (&h[0][0])[i];
-        if (x) atomicAdd(&hist[i], x);
-    }
 }
 
 // ---- items of the hash-sorted order that sit in runs of equal hashes longer than
@@ -273,115 +263,76 @@ __global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__
 }
 
 // ---- stable LSD radix sort of (key, value) pairs, 8 bits per pass ----------
-// One-sweep form: a first read of the keys counts the digits of every pass at
-// once, which fixes where each digit's items start in every pass's output.  A
-// pass is then one launch.  A block takes the next tile in ticket order (so the
-// tiles before it belong to blocks that are already running), ranks its items
-// stably (warp by warp, 32 items at a time in input order: lanes with the same
-// digit by a match, earlier rounds and warps by shared counters), and learns
-// how many items of each digit the tiles before it hold by looking back over
-// their published counts: a tile publishes its own count at once and the
-// inclusive count as soon as it knows it, and a look-back stops at the first
-// inclusive count.  Each wait reads a bounded number of times; a wait that runs
-// out flags the error, publishes a count so that no later tile waits on it,
-// and the block writes nothing.
-constexpr uint32_t RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32, RS_PASSES = 8;
-constexpr unsigned long long RS_AGG = 1ull << 32, RS_INC = 2ull << 32;
-constexpr uint32_t RS_SPIN = 1u << 20, RS_LB = 8;
-constexpr uint32_t C_ERR_SORT = 4u;
+// A pass is three launches.  The first counts each tile's digits; an exclusive
+// scan over (digit, tile) then gives every tile the output position of its first
+// item of each digit; the third ranks each tile's items stably (warp by warp, 32
+// items at a time in input order: lanes with the same digit from one ballot per
+// digit bit, earlier rounds and warps by shared counters), puts the tile in digit
+// order in shared memory and writes it out.  No block waits on another.
+constexpr uint32_t RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
 
 template <class K>
 struct RsSmem {
     uint32_t wcnt[RS_W][256];  // items of each digit seen so far by each warp, then where the warp's start
-    uint32_t gofs[256];        // output position of the tile's first item of each digit, minus dstart
+    uint32_t gofs[256];        // output position of the tile's first item of each digit, minus its tile start
     uint32_t wsum[RS_W];
-    uint32_t tile, bad;
     K sk[RS_TILE];
     uint32_t sv[RS_TILE];
 };
 
-__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// digit counts of passes 0 .. npass-1 over all items; hist is zero on entry
+// digit counts of every tile, digit-major (hist[d * tiles + t]) for the scan
 template <class K>
-__global__ void __launch_bounds__(RS_T) k_rs_count(const K* __restrict__ key, uint32_t cnt, uint32_t npass,
-                                                   uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[RS_PASSES][256];
-    for (uint32_t i = threadIdx.x; i < RS_PASSES * 256; i += RS_T) (&h[0][0])[i] = 0;
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const K* __restrict__ key, uint32_t cnt, uint32_t shift,
+                                                  uint32_t tiles, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[RS_W][256];
+    for (uint32_t i = threadIdx.x; i < RS_W * 256; i += RS_T) (&h[0][0])[i] = 0;
     __syncthreads();
-    for (uint32_t i = blockIdx.x * RS_T + threadIdx.x; i < cnt; i += gridDim.x * RS_T) {
-        const K k = key[i];
-        for (uint32_t p = 0; p < npass; p++) atomicAdd(&h[p][(uint32_t)(k >> (8 * p)) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < npass * 256; i += RS_T) {
-        const uint32_t x = (&h[0][0])[i];
-        if (x) atomicAdd(&hist[i], x);
-    }
-}
-
-// exclusive prefix of each pass's 256 digit counts (one block per pass)
-__global__ void __launch_bounds__(256) k_rs_starts(const uint32_t* __restrict__ hist, uint32_t* __restrict__ start) {
-    __shared__ uint32_t ws[8];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t v = hist[blockIdx.x * 256 + threadIdx.x];
-    uint32_t x = v;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t base = blockIdx.x * RS_TILE + threadIdx.x;
+    K k[RS_I];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= (uint32_t)o) x += y;
+    for (int j = 0; j < (int)RS_I; j++) {
+        const uint32_t q = base + j * RS_T;
+        k[j] = q < cnt ? key[q] : (K)0;
     }
-    if (lane == 31) ws[warp] = x;
+#pragma unroll
+    for (int j = 0; j < (int)RS_I; j++)
+        if (base + j * RS_T < cnt) atomicAdd(&h[warp][(uint32_t)(k[j] >> shift) & 0xFFu], 1u);
     __syncthreads();
-    uint32_t before = 0;
-    for (uint32_t w = 0; w < warp; w++) before += ws[w];
-    start[blockIdx.x * 256 + threadIdx.x] = before + x - v;
+    uint32_t x = 0;
+#pragma unroll
+    for (int w = 0; w < (int)RS_W; w++) x += h[w][threadIdx.x];
+    hist[threadIdx.x * tiles + blockIdx.x] = x;
 }
 
-// val_in NULL: the values are the items' indices.  A block takes one tile, in
-// ticket order.
+// val_in NULL: the values are the items' indices
 template <class K>
 __global__ void __launch_bounds__(RS_T, sizeof(K) == 4 ? 3 : 2)
-    k_rs_pass(const K* __restrict__ key_in, const uint32_t* __restrict__ val_in, uint32_t cnt, uint32_t shift,
-              const uint32_t* __restrict__ start, unsigned long long* __restrict__ status,
-              uint32_t* __restrict__ ticket, uint32_t* __restrict__ err, K* __restrict__ key_out,
-              uint32_t* __restrict__ val_out) {
+    k_rs_scatter(const K* __restrict__ key_in, const uint32_t* __restrict__ val_in, uint32_t cnt, uint32_t shift,
+                 uint32_t tiles, const uint32_t* __restrict__ offs, K* __restrict__ key_out,
+                 uint32_t* __restrict__ val_out) {
     extern __shared__ __align__(16) unsigned char rs_raw[];
     RsSmem<K>& S = *reinterpret_cast<RsSmem<K>*>(rs_raw);
     auto& wcnt = S.wcnt;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) {
-        S.tile = atomicAdd(ticket, 1u);
-        S.bad = 0;
-    }
+    const uint32_t tile = blockIdx.x, dg = threadIdx.x;  // (one digit per thread below)
+    const uint32_t gstart = offs[dg * tiles + tile];
     for (uint32_t i = threadIdx.x; i < RS_W * 256; i += RS_T) (&wcnt[0][0])[i] = 0;
-    K k[RS_I];
-    uint32_t v[RS_I], r[RS_I];
-    // warp w owns items [w * 32 RS_I, (w + 1) * 32 RS_I) of a tile, 32 per round in order
-    auto load = [&](uint32_t t) {
-        const uint32_t base = t * RS_TILE + warp * 32 * RS_I;
-#pragma unroll
-        for (int j = 0; j < (int)RS_I; j++) {
-            const uint32_t q = base + j * 32 + lane;
-            const bool ok = q < cnt;
-            k[j] = ok ? key_in[q] : (K)0;
-            v[j] = ok ? (val_in ? val_in[q] : q) : 0u;  // no values: each item's own index
-        }
-    };
-    __syncthreads();
-    const uint32_t tile = S.tile;
-    load(tile);
+    // warp w owns items [w * 32 RS_I, (w + 1) * 32 RS_I) of the tile, 32 per round in order
     const uint32_t tile0 = tile * RS_TILE;
     const uint32_t base = tile0 + warp * 32 * RS_I;
     const uint32_t nin = cnt > tile0 ? min(RS_TILE, cnt - tile0) : 0u;
+    K k[RS_I];
+    uint32_t v[RS_I], r[RS_I];
+#pragma unroll
+    for (int j = 0; j < (int)RS_I; j++) {
+        const uint32_t q = base + j * 32 + lane;
+        const bool ok = q < cnt;
+        k[j] = ok ? key_in[q] : (K)0;
+        v[j] = ok ? (val_in ? val_in[q] : q) : 0u;  // no values: each item's own index
+    }
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < (int)RS_I; j++) {
         const bool ok = base + j * 32 + lane < cnt;
@@ -403,33 +354,31 @@ __global__ void __launch_bounds__(RS_T, sizeof(K) == 4 ? 3 : 2)
         __syncwarp();
     }
     __syncthreads();
-    const uint32_t dg = threadIdx.x;  // one digit per thread
-    uint32_t run = 0;
-    for (int w = 0; w < (int)RS_W; w++) run += wcnt[w][dg];
-    unsigned long long* my = status + (size_t)tile * 256 + dg;
-    st_status(my, (tile == 0 ? RS_INC : RS_AGG) | run);
-    // exclusive scan of the 256 digit totals across the tile
-    uint32_t x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) S.wsum[warp] = x;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int w = 0; w < warp; w++) before += S.wsum[w];
-    const uint32_t dst = before + x - run;
     {
+        uint32_t run = 0;
+        for (int w = 0; w < (int)RS_W; w++) run += wcnt[w][dg];
+        // exclusive scan of the 256 digit totals across the tile
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) S.wsum[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; w++) before += S.wsum[w];
+        const uint32_t dst = before + x - run;
         uint32_t acc = dst;
         for (int w = 0; w < (int)RS_W; w++) {
             const uint32_t c = wcnt[w][dg];
             wcnt[w][dg] = acc;
             acc += c;
         }
+        S.gofs[dg] = gstart - dst;
     }
     __syncthreads();
-    // the tile in digit order in shared memory
+    // the tile in digit order in shared memory ...
 #pragma unroll
     for (int j = 0; j < (int)RS_I; j++) {
         if (base + j * 32 + lane >= cnt) continue;
@@ -437,42 +386,9 @@ __global__ void __launch_bounds__(RS_T, sizeof(K) == 4 ? 3 : 2)
         S.sk[p] = k[j];
         S.sv[p] = v[j];
     }
-    // items of this digit in the tiles before this one, read RS_LB tiles per round
-    // trip (a look-back of one tile at a time would make its length the pass's limit)
-    uint32_t excl = 0;
-    bool ok = true, done = false;
-    for (uint32_t t = tile; t > 0 && !done;) {
-        const uint32_t nw = min(t, RS_LB);
-        unsigned long long sv[RS_LB];
-#pragma unroll
-        for (uint32_t i = 0; i < RS_LB; i++)
-            if (i < nw) sv[i] = ld_status(status + (size_t)(t - 1 - i) * 256 + dg);
-#pragma unroll
-        for (uint32_t i = 0; i < RS_LB; i++) {
-            if (i >= nw || done) continue;
-            unsigned long long y = sv[i];
-            uint32_t spin = 0;
-            while ((y >> 32) == 0 && ++spin < RS_SPIN) y = ld_status(status + (size_t)(t - 1 - i) * 256 + dg);
-            if ((y >> 32) == 0) {
-                ok = false;
-                done = true;
-                continue;
-            }
-            excl += (uint32_t)y;
-            if (y & RS_INC) done = true;
-        }
-        t -= nw;
-    }
-    if (tile > 0) st_status(my, RS_INC | (excl + run));
-    if (!ok) {
-        S.bad = 1;
-        atomicOr(err, C_ERR_SORT);
-    }
-    S.gofs[dg] = start[dg] + excl - dst;
     __syncthreads();
-    if (S.bad) return;
-    // written out: consecutive threads take consecutive items, which within a digit
-    // land on consecutive addresses
+    // ... then written out: consecutive threads take consecutive items, which within
+    // a digit land on consecutive addresses
     for (uint32_t p = threadIdx.x; p < nin; p += RS_T) {
         const K kk = S.sk[p];
         const uint32_t o = S.gofs[(uint32_t)(kk >> shift) & 0xFFu] + p;
@@ -585,10 +501,10 @@ uint32_t bits_for(uint32_t x) {  // bits to write 0 .. x
 
 }  // namespace
 
-size_t contract_status_entries(uint32_t m) {
-    return (size_t)(((uint64_t)m + RS_TILE - 1) / RS_TILE) * 256 + 1;
+size_t contract_sort_words(uint32_t m) {
+    const uint64_t tiles = ((uint64_t)m + RS_TILE - 1) / RS_TILE;
+    return (size_t)(2 * (256 * tiles + 4));
 }
-size_t contract_digit_words() { return 2 * RS_PASSES * 256 + RS_PASSES; }
 
 int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot) {
     cudaStream_t s = (cudaStream_t)stream;
@@ -600,38 +516,29 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     if (int r = launch_exclusive_scan(s, c.flag, c.rank, c.n + 1, c.scan_tmp, c.scan_words)) return r;
     k_c_map<<<grid_for(c.n), CT, 0, s>>>(c.mate, c.n, c.rank, c.vw, c.cmap, c.cvw);
     if (c.m == 0) return (int)cudaGetLastError();
-    if ((e = cudaFuncSetAttribute(k_rs_pass<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rs_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(RsSmem<uint32_t>)))) return (int)e;
-    if ((e = cudaFuncSetAttribute(k_rs_pass<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_rs_scatter<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(RsSmem<unsigned long long>)))) return (int)e;
     // stable sort by the low `bits` bits of the keys (8-bit digits), ping-ponging
     // between the two buffers; *cur tells which holds the result
     // (ident: the values are the items' indices, and v0 is not read)
-    // (counted: the digits of the keys are in hist already, and the tickets zero)
     auto radix = [&](auto* k0, auto* k1, uint32_t* v0, uint32_t* v1, uint32_t cnt, uint32_t bits, bool ident,
-                     bool counted, int* cur) -> int {
+                     int* cur) -> int {
         using K = typename std::remove_pointer<decltype(k0)>::type;
         K* kk[2] = {k0, k1};
         uint32_t* vv[2] = {v0, v1};
         *cur = 0;
         if (cnt < 2) return 0;
-        const uint32_t npass = (bits + 7) / 8;
         const uint32_t tiles = (cnt + RS_TILE - 1) / RS_TILE;
-        uint32_t* hist = c.digits;
-        uint32_t* starts = c.digits + RS_PASSES * 256;
-        uint32_t* tickets = c.digits + 2 * RS_PASSES * 256;
-        cudaError_t ce;
-        if (!counted) {
-            if ((ce = cudaMemsetAsync(c.digits, 0, contract_digit_words() * sizeof(uint32_t), s))) return (int)ce;
-            k_rs_count<K><<<grid_for((uint64_t)cnt / 8), RS_T, 0, s>>>(k0, cnt, npass, hist);
-        }
-        k_rs_starts<<<npass, 256, 0, s>>>(hist, starts);
-        for (uint32_t p = 0; p < npass; p++) {
-            if ((ce = cudaMemsetAsync(c.status, 0, (size_t)tiles * 256 * sizeof(unsigned long long), s))) return (int)ce;
+        uint32_t* hist = c.shist;
+        uint32_t* offs = c.shist + ((256 * (size_t)tiles + 4) & ~(size_t)3);
+        for (uint32_t p = 0; p * 8 < bits; p++) {
+            k_rs_hist<K><<<tiles, RS_T, 0, s>>>(kk[*cur], cnt, 8 * p, tiles, hist);
+            if (int r = launch_exclusive_scan(s, hist, offs, 256 * tiles, c.scan_tmp, c.scan_words)) return r;
             const uint32_t* vin = (ident && p == 0) ? nullptr : vv[*cur];
-            k_rs_pass<K><<<tiles, RS_T, sizeof(RsSmem<K>), s>>>(kk[*cur], vin, cnt, 8 * p, starts + 256 * p,
-                                                                c.status, tickets + p, c.err, kk[*cur ^ 1],
-                                                                vv[*cur ^ 1]);
+            k_rs_scatter<K><<<tiles, RS_T, sizeof(RsSmem<K>), s>>>(kk[*cur], vin, cnt, 8 * p, tiles, offs,
+                                                                   kk[*cur ^ 1], vv[*cur ^ 1]);
             *cur ^= 1;
         }
         return (int)cudaGetLastError();
@@ -644,21 +551,18 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     const bool vec = ((reinterpret_cast<uintptr_t>(c.eu) | reinterpret_cast<uintptr_t>(c.ev) |
                        reinterpret_cast<uintptr_t>(c.w)) & 15u) == 0;
     if ((e = cudaMemsetAsync(c.counts, 0, 4 * sizeof(uint32_t), s))) return (int)e;
-    if ((e = cudaMemsetAsync(c.digits, 0, contract_digit_words() * sizeof(uint32_t), s))) return (int)e;
     const uint32_t kgrid = grid_for(((uint64_t)c.m + 7) / 8);
     if (vec)
-        k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.digits,
-                                            c.err);
+        k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.err);
     else
-        k_c_keys<false><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.digits,
-                                             c.err);
+        k_c_keys<false><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.err);
     if ((e = cudaMemcpyAsync(mc_host_slot, c.counts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaMemcpyAsync(mc_host_slot + 1, c.rank + c.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaStreamSynchronize(s))) return (int)e;
     const uint32_t mc = mc_host_slot[0], nc = mc_host_slot[1];
     int hc = 0;
     if (mc > 1)
-        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, true, &hc)) return r;
+        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, &hc)) return r;
     // 2. runs of equal hash longer than one (groups of several edges, and collisions),
     //    taken out in sorted order with their pair as the key, and sorted again by the pair
     uint32_t nsub = 0;
@@ -682,7 +586,7 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     uint32_t* sv[2] = {c.val[hc ^ 1], c.val[hc]};
     int cur = 0;
     if (nsub)
-        if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, false, &cur)) return r;
+        if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, &cur)) return r;
     // 3. the crossing bits become the leader bits: other members are cleared
     if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
     if (nsub) k_c_marks<<<grid_for(nsub), CT, 0, s>>>(sk[cur], sv[cur], nsub, c.w, c.cross, c.multi, c.gref);

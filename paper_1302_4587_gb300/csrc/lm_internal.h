@@ -290,8 +290,7 @@ struct ContractArgs {
     uint32_t* cpair;          // [2 m] coarse endpoints of every edge, cmap[eu[e]] then cmap[ev[e]]
     unsigned long long* key[2];  // [m] coarse pair of each crossing edge (radix ping-pong)
     uint32_t* val[2];         // [m] its edge index
-    unsigned long long* status;  // [tiles * 256] a radix pass's per-tile digit counts (look-back)
-    uint32_t* digits;         // [8 * 256] digit counts of every pass, [8 * 256] their starts, [8] tile tickets
+    uint32_t* shist;          // radix pass: [256 * tiles] per-tile digit counts, then their exclusive prefix
     uint32_t* multi;          // [m / 32 + 2] bit e: edge e leads a group of several edges
     uint32_t* wlead;          // [m / 32 + 2] leaders per word of cross
     uint32_t* wpos;           // [m / 32 + 2] their exclusive prefix (wpos[words] = coarse edges)
@@ -299,10 +298,9 @@ struct ContractArgs {
     uint32_t* gref;           // [m] float32 bits of the weight of a group led by edge e (groups of several edges)
     uint32_t* scan_tmp;
     size_t scan_words;
-    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n, 4: a sort's look-back gave up
+    uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n
 };
-size_t contract_status_entries(uint32_t m);  // entries of status
-size_t contract_digit_words();               // words of digits
+size_t contract_sort_words(uint32_t m);  // words of shist
 // runs every step; mc_host_slot: 2 pinned words (crossing edges and coarse vertices
 // are read back once, to size the sort); returns a cudaError_t value
 int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot);
