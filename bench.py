@@ -686,7 +686,10 @@ def run_contract(args, ws, rank, local):
             "roofline": {"bound": "hbm", "kernel": "lm_contract (all its kernels)", "achieved": ach, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                          "bytes_per_step": algo},
-            "clocks": clk.summary(), "gpu_launches": 50 * args.steps}  # R-MAT 23: 9 kernels, 6 radix passes of 5, 3 scans
+            # R-MAT 23, per call: coarse map 2 + scan 3, keys 1, four hash passes of 5 (counts, scan 3,
+            # scatter), run flags 1 + scan 3 + take 1, six pair passes of 5, marks 1, leader counts 1 +
+            # scan 3, emit 1 (the ncu launch list of this command counts the same 67)
+            "clocks": clk.summary(), "gpu_launches": 67 * args.steps}
 
 
 def run_coarsen(args, ws, rank, local):
