@@ -687,9 +687,9 @@ def run_contract(args, ws, rank, local):
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                          "bytes_per_step": algo},
             # R-MAT 23, per call: coarse map 2 + scan 3, keys 1, four hash passes of 5 (counts, scan 3,
-            # scatter), run flags 1 + scan 3 + take 1, six pair passes of 5, marks 1, leader counts 1 +
-            # scan 3, emit 1 (the ncu launch list of this command counts the same 67)
-            "clocks": clk.summary(), "gpu_launches": 67 * args.steps}
+            # scatter), runs of equal hash 1, leader counts 1 + scan 3, emit 1 (no run here needs the
+            # pair sort; the ncu launch list of this command counts the same 32)
+            "clocks": clk.summary(), "gpu_launches": 32 * args.steps}
 
 
 def run_coarsen(args, ws, rank, local):

@@ -1027,7 +1027,7 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     cv.add(&c.rank, (size_t)n + 1);
     const size_t W = (size_t)m / 32 + 2;
     cv.add(&c.cross, W);
-    cv.add(&c.counts, 4);
+    cv.add(&c.counts, 8);
     cv.add(&c.cpair, 2 * (size_t)m + 8);
     cv.add(&c.key[0], M);
     cv.add(&c.key[1], M);

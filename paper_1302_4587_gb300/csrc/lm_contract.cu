@@ -171,34 +171,162 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
     if (lane == 0 && mine) atomicAdd(&counts[0], mine);
 }
 
-// ---- items of the hash-sorted order that sit in runs of equal hashes longer than
-// one (groups of several edges, and pairs whose hashes collide): a tile of 4096
-// items per block, thread t holding chunks c = 0..3 of four items at tile offset
-// 1024 c + 4 t.  One launch counts them per tile; after a scan of the counts the
-// second takes them out in order, keyed by their pair.
-constexpr uint32_t RN_TILE = 4096;
+// ---- runs of equal hash (two or more items) in the hash-sorted order: groups of
+// several edges, and pairs whose hashes collide.  A run keeps its edges in input
+// order.  One thread walks each run from its first item: with at most GR_PAIRS
+// distinct pairs among at most GR_MAX items (the case on simple graphs, where a
+// group has at most four edges), it finds the groups in registers -- a group's
+// first edge leads it, every later member loses its crossing bit, and a leader of
+// several edges gets its multi bit and the group's weight summed in double in input
+// order -- in two walks, the first deciding and the second writing.  Any other run
+// is flagged in ofl and handled by the general path below: taken out in order with
+// its pair as the key and sorted again by the pair.
+constexpr uint32_t GR_MAX = 64, GR_PAIRS = 4;
 
-// bit j: item i + j is in such a run (items at or past cnt are not)
-__device__ __forceinline__ uint32_t run_bits(const uint32_t* __restrict__ key, uint64_t i, uint32_t cnt) {
-    const uint4 k = load4<true>(key, i, cnt);
-    const uint32_t prev = i > 0 && i - 1 < cnt ? key[i - 1] : ~k.x;
-    const uint32_t next = i + 4 < cnt ? key[i + 4] : ~k.w;
-    uint32_t f = 0;
-    if (i < cnt && (prev == k.x || (i + 1 < cnt && k.y == k.x))) f |= 1u;
-    if (i + 1 < cnt && (k.x == k.y || (i + 2 < cnt && k.z == k.y))) f |= 2u;
-    if (i + 2 < cnt && (k.y == k.z || (i + 3 < cnt && k.w == k.z))) f |= 4u;
-    if (i + 3 < cnt && (k.z == k.w || next == k.w)) f |= 8u;
-    return f;
+__device__ __forceinline__ unsigned long long upair(const uint32_t* __restrict__ cpair, uint32_t e) {
+    const uint2 p = *reinterpret_cast<const uint2*>(cpair + 2 * (size_t)e);
+    return ((unsigned long long)min(p.x, p.y) << 32) | max(p.x, p.y);
 }
 
-__global__ void __launch_bounds__(CT) k_c_runs_count(const uint32_t* __restrict__ key, uint32_t cnt,
+// A block stages its tile of GR_TILE sorted keys (and one key on each side) in
+// shared memory, lists the runs that start in the tile, then its threads walk
+// those runs side by side (a run's items four per round trip).
+constexpr uint32_t GR_TILE = 4096;
+
+__global__ void __launch_bounds__(CT) k_c_groups(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
+                                                 uint32_t cnt, const uint32_t* __restrict__ cpair,
+                                                 const float* __restrict__ w, uint32_t* __restrict__ cross,
+                                                 uint32_t* __restrict__ multi, uint32_t* __restrict__ gsum,
+                                                 uint32_t* __restrict__ ofl, uint32_t* __restrict__ counts) {
+    __shared__ __align__(16) uint32_t sk[GR_TILE + 4];  // sk[q + 1] = key[t0 + q], q in -1 .. GR_TILE
+    __shared__ uint32_t starts[GR_TILE / 2];
+    __shared__ uint32_t nstart;
+    const uint64_t t0 = (uint64_t)blockIdx.x * GR_TILE;
+    // (keys past cnt read as 0; every comparison below checks its index against cnt)
+    for (uint32_t c = threadIdx.x; c < GR_TILE / 4; c += CT) {
+        const uint4 x = load4<true>(key, t0 + 4 * c, cnt);
+        sk[4 * c + 1] = x.x;
+        sk[4 * c + 2] = x.y;
+        sk[4 * c + 3] = x.z;
+        sk[4 * c + 4] = x.w;
+    }
+    if (threadIdx.x == 0) {
+        nstart = 0;
+        sk[0] = t0 > 0 && t0 - 1 < cnt ? key[t0 - 1] : 0u;
+        sk[GR_TILE + 1] = t0 + GR_TILE < cnt ? key[t0 + GR_TILE] : 0u;
+    }
+    __syncthreads();
+    const uint32_t tn = cnt > t0 ? (uint32_t)min((uint64_t)GR_TILE, cnt - t0) : 0u;  // items of the tile
+    for (uint32_t q = threadIdx.x; q < tn; q += CT) {
+        const uint64_t i = t0 + q;
+        if (i + 1 >= cnt) continue;
+        const uint32_t k = sk[q + 1];
+        if ((i == 0 || sk[q] != k) && sk[q + 2] == k) starts[atomicAdd(&nstart, 1u)] = q;
+    }
+    __syncthreads();
+    const uint32_t ns = nstart;
+    for (uint32_t sidx = threadIdx.x; sidx < ns; sidx += CT) {
+        const uint32_t q0 = starts[sidx], i = (uint32_t)t0 + q0;
+        const uint32_t k = sk[q0 + 1];
+        uint32_t len = 2;
+        while (i + len < cnt && (q0 + len < GR_TILE ? sk[q0 + len + 1] : key[i + len]) == k && len <= GR_MAX) len++;
+        unsigned long long gp[GR_PAIRS];
+        uint32_t gl[GR_PAIRS], gn[GR_PAIRS];
+        double gs[GR_PAIRS];
+        uint32_t ng = 0;
+        bool over = len > GR_MAX;
+        for (uint32_t j0 = 0; j0 < len && !over; j0 += 4) {
+            uint32_t e[4];
+            unsigned long long pj[4];
+            float wj[4];
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) e[t] = j0 + t < len ? val[i + j0 + t] : 0u;
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) {
+                pj[t] = j0 + t < len ? upair(cpair, e[t]) : 0ull;
+                wj[t] = j0 + t < len ? w[e[t]] : 0.0f;
+            }
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) {
+                if (j0 + t >= len || over) continue;
+                bool found = false;
+#pragma unroll
+                for (uint32_t g = 0; g < GR_PAIRS; g++)
+                    if (!found && g < ng && gp[g] == pj[t]) {
+                        gs[g] += (double)wj[t];
+                        gn[g]++;
+                        found = true;
+                    }
+                if (!found) {
+                    if (ng == GR_PAIRS) {
+                        over = true;
+                    } else {
+#pragma unroll
+                        for (uint32_t g = 0; g < GR_PAIRS; g++)
+                            if (g == ng) {
+                                gp[g] = pj[t];
+                                gl[g] = e[t];
+                                gn[g] = 1;
+                                gs[g] = (double)wj[t];
+                            }
+                        ng++;
+                    }
+                }
+            }
+        }
+        if (over) {
+            // the whole run goes to the general path
+            uint32_t n = i;
+            while (n < cnt && key[n] == k) {
+                atomicOr(&ofl[n >> 5], 1u << (n & 31));
+                n++;
+            }
+            atomicAdd(&counts[1], n - i);
+            continue;
+        }
+        for (uint32_t j0 = 0; j0 < len; j0 += 4) {
+            uint32_t e[4];
+            unsigned long long pj[4];
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) e[t] = j0 + t < len ? val[i + j0 + t] : 0u;
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) pj[t] = j0 + t < len ? upair(cpair, e[t]) : 0ull;
+#pragma unroll
+            for (uint32_t t = 0; t < 4; t++) {
+                if (j0 + t >= len) continue;
+                bool member = false;
+#pragma unroll
+                for (uint32_t g = 0; g < GR_PAIRS; g++) member |= g < ng && gp[g] == pj[t] && gl[g] != e[t];
+                if (member) atomicAnd(&cross[e[t] >> 5], ~(1u << (e[t] & 31)));
+            }
+        }
+#pragma unroll
+        for (uint32_t g = 0; g < GR_PAIRS; g++)
+            if (g < ng && gn[g] > 1) {
+                atomicOr(&multi[gl[g] >> 5], 1u << (gl[g] & 31));
+                gsum[gl[g]] = __float_as_uint((float)gs[g]);
+            }
+    }
+}
+
+// The general path: the flagged items, a tile of 4096 per block, thread t holding
+// chunks c = 0..3 of four items at tile offset 1024 c + 4 t.  One launch counts
+// them per tile; after a scan of the counts the second takes them out in order.
+constexpr uint32_t RN_TILE = 4096;
+
+// bit j: item i + j is flagged (i a multiple of 4)
+__device__ __forceinline__ uint32_t run_bits(const uint32_t* __restrict__ ofl, uint64_t i, uint32_t cnt) {
+    return i < cnt ? (ofl[i >> 5] >> (i & 31)) & 0xFu : 0u;
+}
+
+__global__ void __launch_bounds__(CT) k_c_runs_count(const uint32_t* __restrict__ ofl, uint32_t cnt,
                                                      uint32_t* __restrict__ tcount) {
     __shared__ uint32_t ws[CT / 32];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * RN_TILE + 4 * threadIdx.x;
     uint32_t x = 0;
 #pragma unroll
-    for (int c = 0; c < 4; c++) x += __popc(run_bits(key, base + 1024 * c, cnt));
+    for (int c = 0; c < 4; c++) x += __popc(run_bits(ofl, base + 1024 * c, cnt));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     if (lane == 0) ws[warp] = x;
@@ -210,11 +338,11 @@ __global__ void __launch_bounds__(CT) k_c_runs_count(const uint32_t* __restrict_
     }
 }
 
-// the run items in sorted order (so a pair's edges keep their input order), with
-// (min, max) of their coarse pair as the key of a second sort; counts[1] = how many.
+// the flagged items in sorted order (so a pair's edges keep their input order), with
+// (min, max) of their coarse pair as the key of a second sort; counts[3] = how many.
 // The tile's run items are listed in shared memory first, so that the gathers of
 // their pairs spread over all threads.
-__global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
+__global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__ ofl, const uint32_t* __restrict__ val,
                                                     uint32_t cnt, const uint32_t* __restrict__ toffs,
                                                     const uint32_t* __restrict__ cpair, uint32_t bits,
                                                     unsigned long long* __restrict__ skey,
@@ -227,7 +355,7 @@ __global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__
     uint32_t f[4], incl[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
-        f[c] = run_bits(key, base + 1024 * c, cnt);
+        f[c] = run_bits(ofl, base + 1024 * c, cnt);
         uint32_t x = __popc(f[c]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -259,7 +387,7 @@ __global__ void __launch_bounds__(CT) k_c_runs_take(const uint32_t* __restrict__
         skey[off + q] = ((unsigned long long)min(x, y) << bits) | max(x, y);  // coarse ids take `bits` bits
         sval[off + q] = e;
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) counts[1] = off + run;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) counts[3] = off + run;
 }
 
 // ---- stable LSD radix sort of (key, value) pairs, 8 bits per pass ----------
@@ -550,7 +678,7 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     const uint32_t egrid = grid_for(((uint64_t)c.m + 3) / 4);
     const bool vec = ((reinterpret_cast<uintptr_t>(c.eu) | reinterpret_cast<uintptr_t>(c.ev) |
                        reinterpret_cast<uintptr_t>(c.w)) & 15u) == 0;
-    if ((e = cudaMemsetAsync(c.counts, 0, 4 * sizeof(uint32_t), s))) return (int)e;
+    if ((e = cudaMemsetAsync(c.counts, 0, 8 * sizeof(uint32_t), s))) return (int)e;
     const uint32_t kgrid = grid_for(((uint64_t)c.m + 7) / 8);
     if (vec)
         k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.err);
@@ -563,33 +691,43 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     int hc = 0;
     if (mc > 1)
         if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, &hc)) return r;
-    // 2. runs of equal hash longer than one (groups of several edges, and collisions),
-    //    taken out in sorted order with their pair as the key, and sorted again by the pair
+    // 2. runs of equal hash (groups of several edges, and collisions): the crossing bits
+    //    become the leader bits, every group member but the first cleared.  Runs with
+    //    few pairs are settled by k_c_groups; the rest are taken out in sorted order
+    //    with their pair as the key, sorted again by the pair and marked.
+    if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
     uint32_t nsub = 0;
     const uint32_t bits = bits_for(nc ? nc - 1 : 0);
+    uint32_t* ofl = c.wlead;  // (free until the leaders are counted)
     if (mc > 1) {
-        const uint32_t tiles = (mc + RN_TILE - 1) / RN_TILE;
-        const uint32_t* hv = c.val[hc];
-        uint32_t* toffs = c.tsum + ((size_t)c.m / RN_TILE + 2);
-        k_c_runs_count<<<tiles, CT, 0, s>>>(hk[hc], mc, c.tsum);
-        if (int r = launch_exclusive_scan(s, c.tsum, toffs, tiles, c.scan_tmp, c.scan_words)) return r;
-        k_c_runs_take<<<tiles, CT, 0, s>>>(hk[hc], hv, mc, toffs, c.cpair, bits, c.key[hc ^ 1],
-                                           c.val[hc ^ 1], c.counts);
+        if ((e = cudaMemsetAsync(ofl, 0, ((size_t)mc / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
+        k_c_groups<<<(mc + GR_TILE - 1) / GR_TILE, CT, 0, s>>>(hk[hc], c.val[hc], mc, c.cpair, c.w, c.cross, c.multi,
+                                                               c.gref, ofl, c.counts);
         if ((e = cudaMemcpyAsync(mc_host_slot + 2, c.counts + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)))
             return (int)e;
         if ((e = cudaStreamSynchronize(s))) return (int)e;
-        nsub = mc_host_slot[2];
+        if (mc_host_slot[2]) {
+            const uint32_t tiles = (mc + RN_TILE - 1) / RN_TILE;
+            uint32_t* toffs = c.tsum + ((size_t)c.m / RN_TILE + 2);
+            k_c_runs_count<<<tiles, CT, 0, s>>>(ofl, mc, c.tsum);
+            if (int r = launch_exclusive_scan(s, c.tsum, toffs, tiles, c.scan_tmp, c.scan_words)) return r;
+            k_c_runs_take<<<tiles, CT, 0, s>>>(ofl, c.val[hc], mc, toffs, c.cpair, bits, c.key[hc ^ 1],
+                                               c.val[hc ^ 1], c.counts);
+            if ((e = cudaMemcpyAsync(mc_host_slot + 2, c.counts + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)))
+                return (int)e;
+            if ((e = cudaStreamSynchronize(s))) return (int)e;
+            nsub = mc_host_slot[2];
+        }
     }
     // the subset's two buffers: the ones the hash sort did not end in, and, once the
     // subset is taken out, the ones it did
     unsigned long long* sk[2] = {c.key[hc ^ 1], c.key[hc]};
     uint32_t* sv[2] = {c.val[hc ^ 1], c.val[hc]};
     int cur = 0;
-    if (nsub)
+    if (nsub) {
         if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, &cur)) return r;
-    // 3. the crossing bits become the leader bits: other members are cleared
-    if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
-    if (nsub) k_c_marks<<<grid_for(nsub), CT, 0, s>>>(sk[cur], sv[cur], nsub, c.w, c.cross, c.multi, c.gref);
+        k_c_marks<<<grid_for(nsub), CT, 0, s>>>(sk[cur], sv[cur], nsub, c.w, c.cross, c.multi, c.gref);
+    }
     // 4. leaders ranked by words of the bitmask; the leaders write the coarse edges
     k_c_wcount<<<grid_for((uint64_t)words + 1), CT, 0, s>>>(c.cross, words, c.wlead);
     if (int r = launch_exclusive_scan(s, c.wlead, c.wpos, words + 1, c.scan_tmp, c.scan_words)) return r;

@@ -286,13 +286,15 @@ struct ContractArgs {
     uint32_t* flag;           // [n + 1] representative flags
     uint32_t* rank;           // [n + 1] their exclusive prefix (rank[n] = coarse vertices)
     uint32_t* cross;          // [m / 32 + 2] bit e: edge e joins two coarse vertices, then: it leads its group
-    uint32_t* counts;         // [4] crossing edges, items in runs of equal hash, coarse edges
+    uint32_t* counts;         // [8] crossing edges, items of runs left to the pair sort, coarse edges,
+                              // items taken out for it
     uint32_t* cpair;          // [2 m] coarse endpoints of every edge, cmap[eu[e]] then cmap[ev[e]]
     unsigned long long* key[2];  // [m] coarse pair of each crossing edge (radix ping-pong)
     uint32_t* val[2];         // [m] its edge index
     uint32_t* shist;          // radix pass: [256 * tiles] per-tile digit counts, then their exclusive prefix
     uint32_t* multi;          // [m / 32 + 2] bit e: edge e leads a group of several edges
-    uint32_t* wlead;          // [m / 32 + 2] leaders per word of cross
+    uint32_t* wlead;          // [m / 32 + 2] flags of the sorted items left to the pair sort, then
+                              // leaders per word of cross
     uint32_t* wpos;           // [m / 32 + 2] their exclusive prefix (wpos[words] = coarse edges)
     uint32_t* tsum;           // [2 * (m / 4096 + 2)] per-tile counts of run items and their prefix
     uint32_t* gref;           // [m] float32 bits of the weight of a group led by edge e (groups of several edges)

@@ -159,6 +159,35 @@ def test_one_pair_holds_every_edge(lmc):
     _same(_contract(lmc, 4, eu, ev, w, mate), want)
 
 
+def test_groups_around_the_register_walk_limit(lmc):
+    # groups of 63, 64, 65 and 66 parallel edges (both orientations, interleaved with
+    # other edges): runs of up to 64 equal hashes are settled in registers, longer ones
+    # by the pair sort; both must match the oracle
+    rng = np.random.default_rng(11)
+    n = 2000
+    g = synth.er(n, 6000, seed=12)
+    eu, ev = [g.eu], [g.ev]
+    for j, mult in enumerate((63, 64, 65, 66)):
+        a, b = 4 * j, 4 * j + 2          # vertices 4j..4j+3: pairs (4j, 4j+1) and (4j+2, 4j+3) once matched
+        x = np.full(mult, a, np.uint32)
+        y = np.full(mult, b, np.uint32)
+        flip = rng.random(mult) < 0.5
+        x[flip], y[flip] = b, a
+        eu.append(x)
+        ev.append(y)
+    eu, ev = np.concatenate(eu), np.concatenate(ev)
+    perm = rng.permutation(eu.shape[0])
+    eu, ev = eu[perm].astype(np.uint32), ev[perm].astype(np.uint32)
+    keep = eu != ev
+    eu, ev = eu[keep], ev[keep]
+    w = synth.weights(eu.shape[0], 13)
+    mate = oracle.greedy(n, eu, ev, w, 3)
+    _same(_contract(lmc, n, eu, ev, w, mate), oracle.contract(n, eu, ev, w, mate))
+    # the same edges with every vertex in a pair (4j with 4j+1, 4j+2 with 4j+3)
+    mate2 = np.arange(n, dtype=np.uint32) ^ 1
+    _same(_contract(lmc, n, eu, ev, w, mate2), oracle.contract(n, eu, ev, w, mate2))
+
+
 def test_refusals(lmc):
     lm, torch = lmc.lm, lmc.torch
     eu = _dev(torch, np.array([0, 1], np.uint32), np.int32)
