@@ -97,19 +97,24 @@ __device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? 
 // pairs get equal keys); an edge inside a pair (or with an endpoint >= n) gets the
 // key 0xFFFFFFFF, above every pair's, so the sort puts it at the end.  Bit e of
 // cross: edge e joins two coarse vertices (counted in counts[0]); cpair: the
-// coarse endpoints of every edge.  A warp takes 64 groups of four edges per step,
-// their loads issued together.
+// coarse endpoints of every edge; hist: each tile's counts of the keys' low byte,
+// the sort's first digit.  A warp takes 64 groups of four edges per step, their
+// loads issued together.
 template <bool VEC>
 __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, const uint32_t* __restrict__ ev,
                                                uint32_t m, uint32_t n, const uint32_t* __restrict__ cmap,
                                                uint32_t* __restrict__ key, uint32_t* __restrict__ cpair,
                                                uint32_t* __restrict__ cross, uint32_t* __restrict__ counts,
-                                               uint32_t* __restrict__ err) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t groups = (uint32_t)(((uint64_t)m + 3) / 4);
+                                               uint32_t* __restrict__ hist, uint32_t* __restrict__ err) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t mine = 0;
-    // g0: the warp's first group (a multiple of 64, so of 8)
-    for (uint64_t g0 = 2ull * (blockIdx.x * CT + threadIdx.x - lane); g0 < groups; g0 += 2ull * gridDim.x * CT) {
+    // a block takes the 4096 edges of one tile of the sort that follows (1024 groups
+    // of four); g0: the warp's first group of a step (a multiple of 64, so of 8)
+    for (uint32_t it = 0; it < 2; it++) {
+        const uint64_t g0 = (uint64_t)blockIdx.x * 1024 + warp * 128 + it * 64;
         uint4 a[2], b[2];
 #pragma unroll
         for (int u = 0; u < 2; u++) {
@@ -143,6 +148,7 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
                     k[j] = pair_hash(pair_word(cu[u][j], cv[u][j]));
                     nib |= 1u << j;
                 }
+                atomicAdd(&h[k[j] & 0xFFu], 1u);  // the sort's first digit
             }
             if (e0 + 4 <= m) {  // key and cpair are 16-byte aligned scratch
                 *reinterpret_cast<uint4*>(key + e0) = make_uint4(k[0], k[1], k[2], k[3]);
@@ -169,6 +175,8 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
     if (lane == 0 && mine) atomicAdd(&counts[0], mine);
+    __syncthreads();
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];  // digit-major, as the sort's counts
 }
 
 // ---- runs of equal hash (two or more items) in the hash-sorted order: groups of
@@ -651,8 +659,9 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     // stable sort by the low `bits` bits of the keys (8-bit digits), ping-ponging
     // between the two buffers; *cur tells which holds the result
     // (ident: the values are the items' indices, and v0 is not read)
+    // (counted0: the first pass's per-tile digit counts are in place already)
     auto radix = [&](auto* k0, auto* k1, uint32_t* v0, uint32_t* v1, uint32_t cnt, uint32_t bits, bool ident,
-                     int* cur) -> int {
+                     bool counted0, int* cur) -> int {
         using K = typename std::remove_pointer<decltype(k0)>::type;
         K* kk[2] = {k0, k1};
         uint32_t* vv[2] = {v0, v1};
@@ -662,7 +671,7 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
         uint32_t* hist = c.shist;
         uint32_t* offs = c.shist + ((256 * (size_t)tiles + 4) & ~(size_t)3);
         for (uint32_t p = 0; p * 8 < bits; p++) {
-            k_rs_hist<K><<<tiles, RS_T, 0, s>>>(kk[*cur], cnt, 8 * p, tiles, hist);
+            if (!(counted0 && p == 0)) k_rs_hist<K><<<tiles, RS_T, 0, s>>>(kk[*cur], cnt, 8 * p, tiles, hist);
             if (int r = launch_exclusive_scan(s, hist, offs, 256 * tiles, c.scan_tmp, c.scan_words)) return r;
             const uint32_t* vin = (ident && p == 0) ? nullptr : vv[*cur];
             k_rs_scatter<K><<<tiles, RS_T, sizeof(RsSmem<K>), s>>>(kk[*cur], vin, cnt, 8 * p, tiles, offs,
@@ -679,18 +688,21 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     const bool vec = ((reinterpret_cast<uintptr_t>(c.eu) | reinterpret_cast<uintptr_t>(c.ev) |
                        reinterpret_cast<uintptr_t>(c.w)) & 15u) == 0;
     if ((e = cudaMemsetAsync(c.counts, 0, 8 * sizeof(uint32_t), s))) return (int)e;
-    const uint32_t kgrid = grid_for(((uint64_t)c.m + 7) / 8);
+    static_assert(RS_TILE == 4096 && CT == 256, "k_c_keys takes one tile of the sort per block");
+    const uint32_t kgrid = (uint32_t)(((uint64_t)c.m + RS_TILE - 1) / RS_TILE);  // the sort's tiles
     if (vec)
-        k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.err);
+        k_c_keys<true><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.shist,
+                                            c.err);
     else
-        k_c_keys<false><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.err);
+        k_c_keys<false><<<kgrid, CT, 0, s>>>(c.eu, c.ev, c.m, c.n, c.cmap, hk[0], c.cpair, c.cross, c.counts, c.shist,
+                                             c.err);
     if ((e = cudaMemcpyAsync(mc_host_slot, c.counts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaMemcpyAsync(mc_host_slot + 1, c.rank + c.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaStreamSynchronize(s))) return (int)e;
     const uint32_t mc = mc_host_slot[0], nc = mc_host_slot[1];
     int hc = 0;
     if (mc > 1)
-        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, &hc)) return r;
+        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, true, &hc)) return r;
     // 2. runs of equal hash (groups of several edges, and collisions): the crossing bits
     //    become the leader bits, every group member but the first cleared.  Runs with
     //    few pairs are settled by k_c_groups; the rest are taken out in sorted order
@@ -725,7 +737,7 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     uint32_t* sv[2] = {c.val[hc ^ 1], c.val[hc]};
     int cur = 0;
     if (nsub) {
-        if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, &cur)) return r;
+        if (int r = radix(sk[0], sk[1], sv[0], sv[1], nsub, 2 * bits, false, false, &cur)) return r;
         k_c_marks<<<grid_for(nsub), CT, 0, s>>>(sk[cur], sv[cur], nsub, c.w, c.cross, c.multi, c.gref);
     }
     // 4. leaders ranked by words of the bitmask; the leaders write the coarse edges
