@@ -1465,13 +1465,13 @@ __global__ void k_ec_check(const EdgeArgs* __restrict__ pa, cudaGraphConditional
 __device__ __forceinline__ uint32_t warp_add(uint32_t* ctr, uint32_t key, bool active, uint32_t lane) {
     const uint32_t act = __ballot_sync(FULL, active);
     const uint32_t peers = __match_any_sync(FULL, key) & act;
+    // every lane reads its group leader's slot through one full-warp shuffle (a shuffle
+    // under each group's own mask inside a branch would run once per group)
+    const uint32_t leader = active ? __ffs(peers) - 1 : lane;
     uint32_t base = 0;
-    if (active) {
-        const uint32_t leader = __ffs(peers) - 1;
-        if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader) + __popc(peers & ((1u << lane) - 1u));
-    }
-    return base;
+    if (active && lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    return active ? base + __popc(peers & ((1u << lane) - 1u)) : 0u;
 }
 
 __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n, uint32_t m,
