@@ -831,10 +831,10 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     const uint32_t* d_ev = ev;
     const float* d_w = w;
     const size_t nn = (size_t)n + 1;
-    const size_t scan_words = exclusive_scan_tmp_words(n + 1);
+    const size_t scan_words = std::max(exclusive_scan_tmp_words(n + 1), exclusive_scan_tmp_words(build_fill_scan_count(n, m)));
     Carver tc;
     uint32_t *t_eu = nullptr, *t_ev = nullptr, *deg = nullptr, *cursor = nullptr;
-    uint32_t *flags = nullptr, *rowidx = nullptr, *scan_tmp = nullptr, *err = nullptr;
+    uint32_t *flags = nullptr, *rowidx = nullptr, *scan_tmp = nullptr, *err = nullptr, *fill_tmp = nullptr;
     float* t_w = nullptr;
     if (mem == LM_HOST && m > 0) {
         tc.add(&t_eu, m);
@@ -847,6 +847,7 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     tc.add(&rowidx, nn);
     tc.add(&scan_tmp, scan_words);
     tc.add(&err, 4);
+    if (m > 0) tc.add(&fill_tmp, build_fill_tmp_words(n, m));
     void* tmp = nullptr;
     cudaError_t ce = fault_alloc(ctx) ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&tmp, tc.total, ctx->pool, s);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph staging");
@@ -923,7 +924,8 @@ int lm_graph_create(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, con
     LM_CK(ctx, launch_exclusive_scan(s, deg, g->off, n + 1, scan_tmp, scan_words));
     if (m > 0) {
         LM_CK(ctx, cudaMemcpyAsync(cursor, g->off, nn * 4, cudaMemcpyDeviceToDevice, s));
-        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, m, cursor, g->nbr, g->pk, g->edges, g->eword, err));
+        LM_CK(ctx, launch_build_fill(s, d_eu, d_ev, d_w, n, m, cursor, g->nbr, g->pk, g->edges, g->eword, fill_tmp,
+                                     scan_tmp, scan_words, err));
         LM_CK(ctx, cudaMemcpyAsync(&hp[2], err, 4, cudaMemcpyDeviceToHost, s));
     }
     LM_CK(ctx, launch_build_rows(s, deg, rowidx, g->off, n, g->nrows, g->nent, g->vid, g->rdeg, g->roff));

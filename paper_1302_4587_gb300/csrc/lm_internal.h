@@ -319,9 +319,13 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
 int launch_exclusive_scan(void* stream, const uint32_t* in, uint32_t* out, uint32_t count, uint32_t* tmp,
                           size_t tmp_words);
 size_t exclusive_scan_tmp_words(uint32_t count);
-int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword,
-                      uint32_t* err);  // err |= 2 when a fill slot falls outside 2m
+// fill: tmp = build_fill_tmp_words(n, m) words of 16-byte aligned scratch; scan_tmp sized for
+// exclusive scans of build_fill_scan_count(n, m) words
+size_t build_fill_tmp_words(uint32_t n, uint32_t m);
+uint32_t build_fill_scan_count(uint32_t n, uint32_t m);
+int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n, uint32_t m,
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword, uint32_t* tmp,
+                      uint32_t* scan_tmp, size_t scan_words, uint32_t* err);  // err |= 2 when a fill slot falls outside 2m
 int launch_build_rows(void* stream, const uint32_t* deg, const uint32_t* rowidx_excl, const uint32_t* off,
                       uint32_t n, uint32_t nrows, uint32_t nent, uint32_t* vid0, uint32_t* rdeg0, uint32_t* roff);
 int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uint32_t nent, uint32_t* tmap,

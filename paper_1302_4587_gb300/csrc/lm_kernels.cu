@@ -1495,12 +1495,45 @@ __global__ void k_build_degrees(const uint32_t* eu, const uint32_t* ev, const fl
         warp_add(&deg[ok ? v : 0], v, ok, lane);
     }
 }
-__global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                             uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword,
-                             uint32_t* err) {
-    const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
-    const uint32_t mr = (m + 31) & ~31u;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < mr; e += stride) {
+// The fill writes every edge's two adjacency entries.  Entries of the first end
+// follow the input's order (inputs listed by source vertex write them in runs);
+// the second end's would land at random rows, each a partial sector anywhere in
+// the arrays.  So they go through 256 buckets of vertex ranges first:
+// k_build_vhist counts each tile of BF_TILE edges per bucket, a scan places every
+// (bucket, tile) run, k_build_fill_u writes the first ends and appends each
+// second-end record (row, neighbour, entry word) to its run, and k_build_fill_v
+// walks the records in bucket order, so that the rows it writes at any time lie in
+// a window of the arrays that L2 holds.
+constexpr uint32_t BF_TILE = 4096, BF_T = 256, BF_NB = 256;
+
+__global__ void __launch_bounds__(BF_T) k_build_vhist(const uint32_t* ev, uint32_t m, uint32_t shift, uint32_t tiles,
+                                                      uint32_t* hist) {
+    __shared__ uint32_t h[BF_NB];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * BF_TILE;
+#pragma unroll 4
+    for (uint32_t j = 0; j < BF_TILE / BF_T; j++) {
+        const uint64_t e = t0 + j * BF_T + threadIdx.x;
+        if (e < m) atomicAdd(&h[(ev[e] >> shift) & (BF_NB - 1)], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];  // bucket-major, for the scan
+}
+
+__global__ void __launch_bounds__(BF_T) k_build_fill_u(const uint32_t* eu, const uint32_t* ev, const float* w,
+                                                       uint32_t m, uint32_t shift, uint32_t tiles,
+                                                       const uint32_t* offs, uint32_t* cursor, uint32_t* nbr,
+                                                       uint64_t* pk, uint64_t* edges, uint32_t* eword, uint4* vrec,
+                                                       uint32_t* err) {
+    __shared__ uint32_t gs[BF_NB], cnt[BF_NB];
+    gs[threadIdx.x] = offs[threadIdx.x * tiles + blockIdx.x];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t t0 = (uint64_t)blockIdx.x * BF_TILE;
+    for (uint32_t j = 0; j < BF_TILE / BF_T; j++) {  // whole warps iterate together
+        const uint64_t e = t0 + j * BF_T + threadIdx.x;
         const bool ok = e < m;
         uint32_t u = 0, v = 0;
         uint64_t word = 0;
@@ -1508,21 +1541,44 @@ __global__ void k_build_fill(const uint32_t* eu, const uint32_t* ev, const float
             u = eu[e];
             v = ev[e];
             const uint32_t ow = ord_of_bits(__float_as_uint(w[e]));
-            word = ((uint64_t)ow << 32) | e;
+            word = ((uint64_t)ow << 32) | (uint32_t)e;
             edges[e] = (uint64_t)u | ((uint64_t)v << 32);
             eword[e] = ow;
         }
         const uint32_t pu = warp_add(&cursor[u], u, ok, lane);
-        const uint32_t pv = warp_add(&cursor[v], v, ok, lane);
-        // the cursors start at the row offsets and the degrees were counted from the
-        // same edges, so every slot is below 2m; a stale cursor is reported, not written
-        if (ok && (pu >= 2 * m || pv >= 2 * m)) {
-            atomicOr(err, 2u);
-        } else if (ok) {
-            nbr[pu] = v;
-            pk[pu] = word;
-            nbr[pv] = u;
-            pk[pv] = word;
+        if (ok) {
+            // the cursors start at the row offsets and the degrees were counted from the
+            // same edges, so every slot is below 2m; a stale cursor is reported, not written
+            if (pu >= 2 * m) {
+                atomicOr(err, 2u);
+            } else {
+                nbr[pu] = v;
+                pk[pu] = word;
+            }
+            const uint32_t b = (v >> shift) & (BF_NB - 1);
+            const uint32_t q = gs[b] + atomicAdd(&cnt[b], 1u);
+            if (q < m) vrec[q] = make_uint4(v, u, (uint32_t)word, (uint32_t)(word >> 32));
+            else atomicOr(err, 2u);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BF_T) k_build_fill_v(const uint4* vrec, uint32_t m, uint32_t* cursor, uint32_t* nbr,
+                                                       uint64_t* pk, uint32_t* err) {
+    const uint32_t stride = gridDim.x * blockDim.x, lane = threadIdx.x & 31;
+    const uint32_t mr = (m + 31) & ~31u;  // whole warps iterate together
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < mr; i += stride) {
+        const bool ok = i < m;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (ok) r = vrec[i];
+        const uint32_t pv = warp_add(&cursor[r.x], r.x, ok, lane);
+        if (ok) {
+            if (pv >= 2 * m) {
+                atomicOr(err, 2u);
+            } else {
+                nbr[pv] = r.y;
+                pk[pv] = ((uint64_t)r.w << 32) | r.z;
+            }
         }
     }
 }
@@ -1886,11 +1942,31 @@ int launch_build_degrees(void* stream, const uint32_t* eu, const uint32_t* ev, c
     k_build_degrees<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, n, m, deg, err);
     return (int)cudaGetLastError();
 }
-int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t m,
-                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword,
-                      uint32_t* err) {
-    k_build_fill<<<grid_for(m, 256), 256, 0, (cudaStream_t)stream>>>(eu, ev, w, m, cursor, nbr, pk, edges,
-                                                                     eword, err);
+size_t build_fill_tmp_words(uint32_t n, uint32_t m) {
+    (void)n;
+    const uint64_t tiles = ((uint64_t)m + BF_TILE - 1) / BF_TILE;
+    return (size_t)4 * m + 2 * (BF_NB * tiles + 4) + 8;  // the records (16 B each), counts, their prefix
+}
+uint32_t build_fill_scan_count(uint32_t n, uint32_t m) {
+    (void)n;
+    return (uint32_t)(BF_NB * (((uint64_t)m + BF_TILE - 1) / BF_TILE));
+}
+int launch_build_fill(void* stream, const uint32_t* eu, const uint32_t* ev, const float* w, uint32_t n, uint32_t m,
+                      uint32_t* cursor, uint32_t* nbr, uint64_t* pk, uint64_t* edges, uint32_t* eword, uint32_t* tmp,
+                      uint32_t* scan_tmp, size_t scan_words, uint32_t* err) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0) return 0;
+    if (!tmp) return (int)cudaErrorInvalidValue;
+    uint32_t shift = 0;  // bucket = v >> shift, below 256
+    while (((uint64_t)(n - 1) >> shift) > BF_NB - 1) shift++;
+    const uint32_t tiles = (uint32_t)(((uint64_t)m + BF_TILE - 1) / BF_TILE);
+    uint4* vrec = reinterpret_cast<uint4*>(tmp);           // 16-byte aligned (the caller's carve)
+    uint32_t* hist = tmp + 4 * (size_t)m;
+    uint32_t* offs = hist + ((BF_NB * (size_t)tiles + 4) & ~(size_t)3);
+    k_build_vhist<<<tiles, BF_T, 0, s>>>(ev, m, shift, tiles, hist);
+    if (int r = launch_exclusive_scan(stream, hist, offs, BF_NB * tiles, scan_tmp, scan_words)) return r;
+    k_build_fill_u<<<tiles, BF_T, 0, s>>>(eu, ev, w, m, shift, tiles, offs, cursor, nbr, pk, edges, eword, vrec, err);
+    k_build_fill_v<<<grid_for(m, 256), BF_T, 0, s>>>(vrec, m, cursor, nbr, pk, err);
     return (int)cudaGetLastError();
 }
 int launch_nonzero_flags(void* stream, const uint32_t* deg, uint32_t n, uint32_t* flags) {
