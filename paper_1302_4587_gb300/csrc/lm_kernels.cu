@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(ST, LM_SWEEP_MINB) k_sweep(const SweepArgs* __
 #define LM_R0C 256
 #endif
 #ifndef LM_R0MINB
-#define LM_R0MINB 4   // CTAs per SM (56 registers a thread, about 45 KB of shared memory a CTA)
+#define LM_R0MINB 5   // CTAs per SM (40 registers a thread, 32 bytes spilled; about 45 KB of shared memory a CTA)
 #endif
 constexpr int R0S = LM_R0S;                         // pipeline stages
 constexpr int R0C = LM_R0C;                         // consumer threads
