@@ -9,14 +9,19 @@
 // is their sum (accumulated in double in input order, rounded once to float32).
 //
 // Device steps (all of them here): representatives and their prefix ranks;
-// the coarse map and vertex weights; every edge, in input order, gets its
-// unordered coarse pair as a key (edges inside a pair a key above all pairs,
-// so that they end up last); a stable LSD radix sort
-// (8-bit digits over the key's significant bits) groups equal pairs with their
-// edges still in input order; each group's first edge is its leader and the
-// group's weight sum is taken over its edges in order; leader flags over the
-// edges (the crossing flags with every non-leader cleared) and their prefix
-// ranks give each coarse edge its place; the leaders write the coarse edges.
+// the coarse map and vertex weights; every edge, in input order, gets a 32-bit
+// hash of its unordered coarse pair as a key (edges inside a pair the key
+// 0xFFFFFFFF, which no pair's hash takes, so that they end up last), and its
+// coarse endpoints are stored; a stable LSD radix sort by the hash (four 8-bit
+// passes) brings each pair's edges together, still in input order.  An edge
+// alone with its hash is alone in its group and leads it.  Each run of equal
+// hash (a group of several edges, or pairs whose hashes collide) is walked in
+// order: its groups' first edges lead, every later member loses its crossing
+// bit, and a leader of several edges records the group's weight summed over
+// its edges in order.  Runs too long or too mixed for that walk are taken out
+// and sorted again by the pair itself.  Prefix counts of the remaining bits
+// (the leaders) give each coarse edge its place, and the leaders write the
+// coarse edges.
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
