@@ -680,7 +680,7 @@ int match_batch(lm_ctx* ctx, Engine& e, const lm_graph* const* gs, uint32_t coun
     rc = run_job(ctx, e, job, prof);
     if (rc) return rc;
     prof.begin(LM_K_OTHER);
-    LM_CK(ctx, launch_to_local_batch(s, w.mate, w.gvbase, count, w.gdst, w.gmatched, (uint32_t)nv));
+    LM_CK(ctx, launch_to_local_batch(s, w.mate, w.gvbase, w.gid, count, w.gdst, w.gmatched, (uint32_t)nv));
     prof.end();
     bool any_host = false;
     for (uint32_t i = 0; i < count; i++) any_host |= host_dst[i] != 0;

@@ -342,7 +342,7 @@ int launch_req_setup(void* stream, const uint32_t* off, uint32_t n, uint32_t vba
 int launch_to_local(void* stream, const uint32_t* mate_global, uint32_t vbase, uint32_t n, uint32_t* out,
                     unsigned long long* matched2);
 // union results -> per-graph local ids into dst[g] (device pointers; NULL = skip); matched2[g] += matched vertices
-int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32_t* gvbase, uint32_t ngraphs,
-                          uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert);
+int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32_t* gvbase, const uint32_t* gid,
+                          uint32_t ngraphs, uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert);
 
 }  // namespace lm

@@ -1623,49 +1623,18 @@ __global__ void k_build_tiledesc(const uint32_t* roff, const uint32_t* tmap, uin
     }
 }
 
-__device__ __forceinline__ uint32_t graph_of(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v) {
-    uint32_t lo = 0, hi = ngraphs - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (gvbase[mid] <= v) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// graph of vertex v for a warp walking consecutive vertices: lane 0 searches
-// for the warp's first vertex, every lane walks forward from there (a warp
-// spans few graphs), falling back to a search after 32 steps (runs of empty graphs)
-__device__ __forceinline__ uint32_t graph_of_warp(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v,
-                                                  uint32_t v0, int lane) {
-    // v0: used from lane 0, the warp's lowest vertex
-    uint32_t g = 0;
-    if (lane == 0) g = graph_of(gvbase, ngraphs, v0);
-    g = __shfl_sync(FULL, g, 0);
-    for (int steps = 0; g + 1 < ngraphs && gvbase[g + 1] <= v; steps++) {
-        if (steps == 32) return graph_of(gvbase, ngraphs, v);
-        g++;
-    }
-    return g;
-}
-
+// one block per graph: its vertices' row starts, graph id and length
 __global__ void k_union_setup(const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
-                              uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    const uint32_t nr = (nvert + 31) & ~31u;  // whole warps iterate together
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += stride) {
-        const uint32_t vv = min(v, nvert - 1);
-        const uint32_t g = graph_of_warp(gvbase, ngraphs, vv, vv, lane);  // lane 0's vertex starts the warp
-        if (v >= nvert) continue;
-        const uint32_t i = v - gvbase[g];
-        const uint32_t* off = offs[g];
-        const uint32_t o0 = off[i], o1 = off[i + 1];
-        start[v] = ebase[g] + o0;
+                              uint32_t* start, uint32_t* gid, uint32_t* len0) {
+    const uint32_t g = blockIdx.x, vb = gvbase[g], ng = gvbase[g + 1] - vb, eb = ebase[g];
+    const uint32_t* off = offs[g];
+    for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) {
+        const uint32_t o0 = off[i], o1 = off[i + 1], v = vb + i;
+        start[v] = eb + o0;
         gid[v] = g;
         len0[v] = o1 - o0;
     }
 }
-
 // serving: vertices [vbase, vbase + n) of one request get their row starts and slot
 __global__ void k_req_setup(const uint32_t* off, uint32_t n, uint32_t vbase, uint32_t ebase, uint32_t slot,
                             uint32_t* start, uint32_t* gid) {
@@ -1692,17 +1661,16 @@ __global__ void k_to_local(const uint32_t* mate_g, uint32_t vbase, uint32_t n, u
     }
 }
 
-__global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase, uint32_t ngraphs,
+__global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase, const uint32_t* gid,
                                  uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    const uint32_t nr = (nvert + 31) & ~31u;
+    const uint32_t nr = (nvert + 31) & ~31u;  // whole warps iterate together
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += stride) {
-        const uint32_t vv = min(v, nvert - 1);
-        const uint32_t g = graph_of_warp(gvbase, ngraphs, vv, vv, lane);  // lane 0's vertex starts the warp
         const bool live = v < nvert;
-        uint32_t x = NIL;
+        uint32_t x = NIL, g = NIL;
         if (live) {
+            g = gid[v];
             const uint32_t vb = gvbase[g];
             x = mate_u[v];
             uint32_t* d = dst[g];
@@ -1715,7 +1683,6 @@ __global__ void k_to_local_batch(const uint32_t* mate_u, const uint32_t* gvbase,
             atomicAdd(&matched2[g], (unsigned long long)__popc(peers));
     }
 }
-
 // ---------------------------------------------------------------- exclusive scan (set-up and contraction)
 // A block scans a tile of 4096 words in two launches (tile sums, then the tiles'
 // prefixes applied), recursing on the tile sums.  Thread t holds four chunks of
@@ -1990,8 +1957,7 @@ int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uin
 int launch_union_setup(void* stream, const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
                        uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
     if (nvert == 0 || ngraphs == 0) return 0;
-    k_union_setup<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(gvbase, ebase, offs, ngraphs, nvert, start,
-                                                                          gid, len0);
+    k_union_setup<<<ngraphs, 256, 0, (cudaStream_t)stream>>>(gvbase, ebase, offs, start, gid, len0);
     return (int)cudaGetLastError();
 }
 int launch_req_setup(void* stream, const uint32_t* off, uint32_t n, uint32_t vbase, uint32_t ebase, uint32_t slot,
@@ -2006,11 +1972,11 @@ int launch_to_local(void* stream, const uint32_t* mate_global, uint32_t vbase, u
     k_to_local<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(mate_global, vbase, n, out, matched2);
     return (int)cudaGetLastError();
 }
-int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32_t* gvbase, uint32_t ngraphs,
-                          uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert) {
+int launch_to_local_batch(void* stream, const uint32_t* mate_union, const uint32_t* gvbase, const uint32_t* gid,
+                          uint32_t ngraphs, uint32_t* const* dst, unsigned long long* matched2, uint32_t nvert) {
     if (nvert == 0 || ngraphs == 0) return 0;
-    k_to_local_batch<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(mate_union, gvbase, ngraphs, dst,
-                                                                             matched2, nvert);
+    k_to_local_batch<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(mate_union, gvbase, gid, dst, matched2,
+                                                                             nvert);
     return (int)cudaGetLastError();
 }
 
