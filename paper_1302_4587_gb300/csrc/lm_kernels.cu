@@ -1623,14 +1623,45 @@ __global__ void k_build_tiledesc(const uint32_t* roff, const uint32_t* tmap, uin
     }
 }
 
-// one block per graph: its vertices' row starts, graph id and length
+
+__device__ __forceinline__ uint32_t graph_of(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v) {
+    uint32_t lo = 0, hi = ngraphs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (gvbase[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// graph of vertex v for a warp walking consecutive vertices: lane 0 searches
+// for the warp's first vertex, every lane walks forward from there (a warp
+// spans few graphs), falling back to a search after 32 steps (runs of empty graphs)
+__device__ __forceinline__ uint32_t graph_of_warp(const uint32_t* gvbase, uint32_t ngraphs, uint32_t v,
+                                                  uint32_t v0, int lane) {
+    // v0: used from lane 0, the warp's lowest vertex
+    uint32_t g = 0;
+    if (lane == 0) g = graph_of(gvbase, ngraphs, v0);
+    g = __shfl_sync(FULL, g, 0);
+    for (int steps = 0; g + 1 < ngraphs && gvbase[g + 1] <= v; steps++) {
+        if (steps == 32) return graph_of(gvbase, ngraphs, v);
+        g++;
+    }
+    return g;
+}
+
 __global__ void k_union_setup(const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
-                              uint32_t* start, uint32_t* gid, uint32_t* len0) {
-    const uint32_t g = blockIdx.x, vb = gvbase[g], ng = gvbase[g + 1] - vb, eb = ebase[g];
-    const uint32_t* off = offs[g];
-    for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) {
-        const uint32_t o0 = off[i], o1 = off[i + 1], v = vb + i;
-        start[v] = eb + o0;
+                              uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nr = (nvert + 31) & ~31u;  // whole warps iterate together
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += stride) {
+        const uint32_t vv = min(v, nvert - 1);
+        const uint32_t g = graph_of_warp(gvbase, ngraphs, vv, vv, lane);  // lane 0's vertex starts the warp
+        if (v >= nvert) continue;
+        const uint32_t i = v - gvbase[g];
+        const uint32_t* off = offs[g];
+        const uint32_t o0 = off[i], o1 = off[i + 1];
+        start[v] = ebase[g] + o0;
         gid[v] = g;
         len0[v] = o1 - o0;
     }
@@ -1957,7 +1988,8 @@ int launch_build_tilemap(void* stream, const uint32_t* roff, uint32_t nrows, uin
 int launch_union_setup(void* stream, const uint32_t* gvbase, const uint32_t* ebase, const uint32_t* const* offs,
                        uint32_t ngraphs, uint32_t nvert, uint32_t* start, uint32_t* gid, uint32_t* len0) {
     if (nvert == 0 || ngraphs == 0) return 0;
-    k_union_setup<<<ngraphs, 256, 0, (cudaStream_t)stream>>>(gvbase, ebase, offs, start, gid, len0);
+    k_union_setup<<<grid_for(nvert, 256), 256, 0, (cudaStream_t)stream>>>(gvbase, ebase, offs, ngraphs, nvert, start,
+                                                                          gid, len0);
     return (int)cudaGetLastError();
 }
 int launch_req_setup(void* stream, const uint32_t* off, uint32_t n, uint32_t vbase, uint32_t ebase, uint32_t slot,
