@@ -191,9 +191,11 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
 // group has at most four edges), it finds the groups in registers -- a group's
 // first edge leads it, every later member loses its crossing bit, and a leader of
 // several edges gets its multi bit and the group's weight summed in double in input
-// order -- in two walks, the first deciding and the second writing.  Any other run
-// is flagged in ofl and handled by the general path below: taken out in order with
-// its pair as the key and sorted again by the pair.
+// order -- in one walk (a member's bit is cleared as soon as it is seen to follow
+// its group's leader; multi bits and sums are written once the run is known to
+// fit).  Any other run is flagged in ofl and handled by the general path below:
+// taken out in order with its pair as the key and sorted again by the pair (which
+// clears the same bits again).
 constexpr uint32_t GR_MAX = 64, GR_PAIRS = 4;
 
 __device__ __forceinline__ unsigned long long upair(const uint32_t* __restrict__ cpair, uint32_t e) {
@@ -270,6 +272,9 @@ __global__ void __launch_bounds__(CT) k_c_groups(const uint32_t* __restrict__ ke
                         gn[g]++;
                         found = true;
                     }
+                // a later member of a group: not a leader, whatever the rest of the run
+                // holds (a run left to the general path has the same bits cleared there)
+                if (found) atomicAnd(&cross[e[t] >> 5], ~(1u << (e[t] & 31)));
                 if (!found) {
                     if (ng == GR_PAIRS) {
                         over = true;
@@ -296,22 +301,6 @@ __global__ void __launch_bounds__(CT) k_c_groups(const uint32_t* __restrict__ ke
             }
             atomicAdd(&counts[1], n - i);
             continue;
-        }
-        for (uint32_t j0 = 0; j0 < len; j0 += 4) {
-            uint32_t e[4];
-            unsigned long long pj[4];
-#pragma unroll
-            for (uint32_t t = 0; t < 4; t++) e[t] = j0 + t < len ? val[i + j0 + t] : 0u;
-#pragma unroll
-            for (uint32_t t = 0; t < 4; t++) pj[t] = j0 + t < len ? upair(cpair, e[t]) : 0ull;
-#pragma unroll
-            for (uint32_t t = 0; t < 4; t++) {
-                if (j0 + t >= len) continue;
-                bool member = false;
-#pragma unroll
-                for (uint32_t g = 0; g < GR_PAIRS; g++) member |= g < ng && gp[g] == pj[t] && gl[g] != e[t];
-                if (member) atomicAnd(&cross[e[t] >> 5], ~(1u << (e[t] & 31)));
-            }
         }
 #pragma unroll
         for (uint32_t g = 0; g < GR_PAIRS; g++)
