@@ -688,10 +688,10 @@ def run_contract(args, ws, rank, local):
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                          "bytes_per_step": algo},
             # R-MAT 23, per call: coarse map 2 + scan 3, keys (with the first pass's digit counts) 1,
-            # four hash passes of 5 (counts but in the first, scan 3, scatter), runs of equal hash 1,
-            # leader counts 1 + scan 3, emit 1 (no run here needs the pair sort; the ncu launch list
-            # of this command counts the same 31)
-            "clocks": clk.summary(), "gpu_launches": 31 * args.steps}
+            # two hash passes (16 bits for about 1900 edges a bucket) of 4 and 5 (counts but in the
+            # first, scan 3, scatter), buckets 1, leader counts 1 + scan 3, emit 1 (no run here needs
+            # the pair sort)
+            "clocks": clk.summary(), "gpu_launches": 21 * args.steps}
 
 
 def run_coarsen(args, ws, rank, local):

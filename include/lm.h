@@ -201,8 +201,8 @@ int  lm_set_limits(lm_ctx* ctx, uint32_t max_rounds, uint32_t time_limit_ms);
  *                       lm_create fails as out of memory (calls return LM_ENOMEM)
  *   LM_FAULT=alloc:N    only the next N of them fail. */
 
-/* Launch parameters of a context's matching path (the paper has no
- * counterpart; they only affect speed, never the result):
+/* Launch parameters of a context's matching and contraction paths (the paper
+ * has no counterpart; they only affect speed, never the result):
  *   rmax               rows with at most this many live entries are swept in
  *                      batches, one batch to a warp; longer rows are split into
  *                      chunks (1 .. 2^20)
@@ -212,15 +212,20 @@ int  lm_set_limits(lm_ctx* ctx, uint32_t max_rounds, uint32_t time_limit_ms);
  *                      entries); a power of two, 2^6 .. 2^20, or 0 = 32 rows only
  *   sweep_ctas_per_sm  CTAs per SM of the sweep kernel (0 = as many as fit, at most 16)
  *   vertex_ctas_per_sm CTAs per SM of the vertex pass (0 = 4, at most 4)
+ *   contract_bits      lm_contract: the low bits of each edge's pair hash that its
+ *                      sort orders by (8, 16, 24 or 32), the buckets of equal low bits
+ *                      then searched for repeated hashes in shared memory; 0 = by
+ *                      size (as few bytes as leave about 2048 edges to a bucket)
  *   ms                 lm_autotune only: median time of one call with these parameters
- * Defaults: rmax 1024, chunk 1024, sweep 0, vertex 4, batch 512.  The serving thread takes
- * the context's parameters when it starts (first lm_submit). */
+ * Defaults: rmax 1024, chunk 1024, sweep 0, vertex 4, batch 512, contract_bits 0.
+ * The serving thread takes the context's parameters when it starts (first lm_submit). */
 typedef struct lm_tuning {
     uint32_t rmax;
     uint32_t chunk;
     uint32_t sweep_ctas_per_sm;
     uint32_t vertex_ctas_per_sm;
     uint32_t batch;
+    uint32_t contract_bits;
     double   ms;
 } lm_tuning;
 

@@ -55,11 +55,13 @@ class LmStats(ctypes.Structure):
 
 class LmTuning(ctypes.Structure):
     _fields_ = [("rmax", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("sweep_ctas_per_sm", ctypes.c_uint32),
-                ("vertex_ctas_per_sm", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("ms", ctypes.c_double)]
+                ("vertex_ctas_per_sm", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("contract_bits", ctypes.c_uint32),
+                ("ms", ctypes.c_double)]
 
     def to_dict(self) -> dict:
         return {"rmax": int(self.rmax), "chunk": int(self.chunk), "sweep_ctas_per_sm": int(self.sweep_ctas_per_sm),
-                "vertex_ctas_per_sm": int(self.vertex_ctas_per_sm), "batch": int(self.batch), "ms": float(self.ms)}
+                "vertex_ctas_per_sm": int(self.vertex_ctas_per_sm), "batch": int(self.batch),
+                "contract_bits": int(self.contract_bits), "ms": float(self.ms)}
 
 
 class LmError(RuntimeError):
@@ -392,8 +394,8 @@ def lm_get_tuning(ctx) -> dict:
 
 
 def lm_set_tuning(ctx, rmax: int, chunk: int, sweep_ctas_per_sm: int = 0, vertex_ctas_per_sm: int = 4,
-                  batch: int = 512) -> None:
-    t = LmTuning(rmax, chunk, sweep_ctas_per_sm, vertex_ctas_per_sm, batch, 0.0)
+                  batch: int = 512, contract_bits: int = 0) -> None:
+    t = LmTuning(rmax, chunk, sweep_ctas_per_sm, vertex_ctas_per_sm, batch, contract_bits, 0.0)
     _check(load().lm_set_tuning(ctx, ctypes.byref(t)), ctx)
 
 

@@ -1019,6 +1019,7 @@ int lm_contract(lm_ctx* ctx, uint32_t n, uint32_t m, const uint32_t* eu, const u
     c.ceu = ceu;
     c.cev = cev;
     c.cw = cw;
+    c.sort_bits = e.cfg.contract_bits;
     if (m >= (1u << 31)) return fail(ctx, LM_EINVAL, "too many edges");
     if (n == 0xFFFFFFFFu) return fail(ctx, LM_EINVAL, "n must be below 2^32 - 1");
     const uint32_t scan_count = (n > m ? n : m) + 1;
@@ -1136,6 +1137,7 @@ bool cfg_from(const lm_tuning* t, LaunchCfg* c) {
     if (t->chunk < 256 || t->chunk > (1u << 20) || (t->chunk & (t->chunk - 1))) return false;
     if (t->sweep_ctas_per_sm > 16 || t->vertex_ctas_per_sm > 4) return false;
     if (t->batch && (t->batch < 64 || t->batch > (1u << 20) || (t->batch & (t->batch - 1)))) return false;
+    if (t->contract_bits % 8 || t->contract_bits > 32) return false;
     c->batch_shift = 32;
     if (t->batch)
         for (c->batch_shift = 0; (1u << c->batch_shift) < t->batch;) c->batch_shift++;
@@ -1144,6 +1146,7 @@ bool cfg_from(const lm_tuning* t, LaunchCfg* c) {
     while ((1u << c->chunk_shift) < t->chunk) c->chunk_shift++;
     c->sweep_ctas_per_sm = t->sweep_ctas_per_sm;
     c->vertex_ctas_per_sm = t->vertex_ctas_per_sm;
+    c->contract_bits = t->contract_bits;
     return true;
 }
 void tuning_of(const LaunchCfg& c, lm_tuning* t) {
@@ -1152,6 +1155,7 @@ void tuning_of(const LaunchCfg& c, lm_tuning* t) {
     t->sweep_ctas_per_sm = c.sweep_ctas_per_sm;
     t->vertex_ctas_per_sm = c.vertex_ctas_per_sm;
     t->batch = c.batch_shift >= 32 ? 0u : 1u << c.batch_shift;
+    t->contract_bits = c.contract_bits;
     t->ms = 0.0;
 }
 }  // namespace
@@ -1194,7 +1198,7 @@ int lm_autotune(lm_ctx* ctx, const lm_graph* const* g, uint32_t count, const uin
     top.ms = -1.0;
     for (const auto& sz : sizes) {
         for (uint32_t sw : sweeps) {
-            lm_tuning t = {sz[0], sz[1], sw, keep.vertex_ctas_per_sm, sz[2], 0.0};
+            lm_tuning t = {sz[0], sz[1], sw, keep.vertex_ctas_per_sm, sz[2], keep.contract_bits, 0.0};
             int rc = lm_set_tuning(ctx, &t);
             if (rc) return rc;
             std::vector<double> ms;

@@ -11,17 +11,19 @@
 // Device steps (all of them here): representatives and their prefix ranks;
 // the coarse map and vertex weights; every edge, in input order, gets a 32-bit
 // hash of its unordered coarse pair as a key (edges inside a pair the key
-// 0xFFFFFFFF, which no pair's hash takes, so that they end up last), and its
-// coarse endpoints are stored; a stable LSD radix sort by the hash (four 8-bit
-// passes) brings each pair's edges together, still in input order.  An edge
-// alone with its hash is alone in its group and leads it.  Each run of equal
-// hash (a group of several edges, or pairs whose hashes collide) is walked in
-// order: its groups' first edges lead, every later member loses its crossing
-// bit, and a leader of several edges records the group's weight summed over
-// its edges in order.  Runs too long or too mixed for that walk are taken out
-// and sorted again by the pair itself.  Prefix counts of the remaining bits
-// (the leaders) give each coarse edge its place, and the leaders write the
-// coarse edges.
+// 0xFFFFFFFF; no pair's hash ends in the byte 0xFF, so that they end up last),
+// and its coarse endpoints are stored.  A stable LSD radix sort by the low B
+// bits of the hash (8-bit passes, as few as leave about 2048 edges to a
+// bucket of equal low bits) brings each pair's edges into one bucket, still in
+// input order.  Inside each bucket a shared-memory hash table finds the items
+// whose full hash repeats; each such run (a group of several edges, or pairs
+// whose hashes collide) is put in input order and walked: its groups' first
+// edges lead, every later member loses its crossing bit, and a leader of
+// several edges records the group's weight summed over its edges in order.
+// An edge alone with its hash is alone in its group and leads it.  Buckets,
+// runs too long or too mixed for that walk are taken out and sorted again by
+// the pair itself.  Prefix counts of the remaining bits (the leaders) give
+// each coarse edge its place, and the leaders write the coarse edges.
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -71,8 +73,9 @@ __global__ void k_c_map(const uint32_t* __restrict__ mate, uint32_t n, const uin
 __device__ __forceinline__ unsigned long long pair_word(uint32_t c, uint32_t d) {
     return ((unsigned long long)min(c, d) << 32) | max(c, d);
 }
-// 32-bit hash of a pair word (a 64-bit finaliser's upper half); 0xFFFFFFFF is left for
-// the edges inside a pair
+// 32-bit hash of a pair word (a 64-bit finaliser's upper half) whose low byte is never
+// 0xFF: sorted by any number of low bytes, the pairs come before the edges inside a
+// pair (key 0xFFFFFFFF)
 __device__ __forceinline__ uint32_t pair_hash(unsigned long long x) {
     x ^= x >> 33;
     x *= 0xFF51AFD7ED558CCDull;
@@ -80,7 +83,7 @@ __device__ __forceinline__ uint32_t pair_hash(unsigned long long x) {
     x *= 0xC4CEB9FE1A85EC53ull;
     x ^= x >> 33;
     const uint32_t h = (uint32_t)(x >> 32);
-    return h == 0xFFFFFFFFu ? 0xFFFFFFFEu : h;
+    return (h & 0xFFu) == 0xFFu ? h ^ 1u : h;
 }
 
 // Edge kernels take four consecutive edges per thread (vector loads when the
@@ -184,130 +187,313 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
     hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];  // digit-major, as the sort's counts
 }
 
-// ---- runs of equal hash (two or more items) in the hash-sorted order: groups of
-// several edges, and pairs whose hashes collide.  A run keeps its edges in input
-// order.  One thread walks each run from its first item: with at most GR_PAIRS
-// distinct pairs among at most GR_MAX items (the case on simple graphs, where a
-// group has at most four edges), it finds the groups in registers -- a group's
-// first edge leads it, every later member loses its crossing bit, and a leader of
-// several edges gets its multi bit and the group's weight summed in double in input
-// order -- in one walk (a member's bit is cleared as soon as it is seen to follow
-// its group's leader; multi bits and sums are written once the run is known to
-// fit).  Any other run is flagged in ofl and handled by the general path below:
-// taken out in order with its pair as the key and sorted again by the pair (which
-// clears the same bits again).
+// ---- buckets of the partial hash sort --------------------------------------
+// The sort orders the items by the low B bits of their keys only, so a bucket
+// (the items sharing those bits) holds every edge of each of its pairs, in input
+// order.  A block takes the buckets that start in its chunk of BK_C sorted items.
+// It reads a window of BK_W keys from the chunk's first bucket on into registers,
+// enters the keys of its buckets in a shared-memory hash table with a count per
+// key, and lists the items whose key repeats grouped by key.  Each such run (a
+// group of several edges, or pairs whose hashes collide) is put back in input
+// order and walked by one thread: with at most GR_PAIRS distinct pairs among at
+// most GR_MAX items (the case on simple graphs, where a group has at most four
+// edges) it finds the groups in registers -- a group's first edge leads it, every
+// later member loses its crossing bit as soon as it is seen, and a leader of
+// several edges gets its multi bit and the group's weight summed in double in
+// input order once the run is known to fit.  A bucket that runs past the window
+// is done in a second window that starts at it.  A bucket longer than a window,
+// and any run that does not fit the walk, is flagged in ofl for the general path
+// below: taken out in order with its pair as the key and sorted again by the pair
+// (which clears the same bits again).
 constexpr uint32_t GR_MAX = 64, GR_PAIRS = 4;
+constexpr uint32_t BK_T = 256, BK_J = 24, BK_W = BK_T * BK_J, BK_C = 4096, BK_TS = 8192, BK_TS_BITS = 13;
+constexpr uint32_t BK_AVG = 2048;  // the sort takes as few bytes as leave at most this many items to a bucket
+constexpr uint32_t BK_EMPTY = 0xFFFFFFFFu;
+static_assert(BK_TS == 1u << BK_TS_BITS && BK_TS / 32 == BK_T && BK_W < BK_TS && BK_W < 65536 && BK_C < BK_W,
+              "table of at most 3/4 load, 16-bit counts and window indices, a chunk shorter than a window");
+
+struct BkSmem {
+    uint32_t tab[BK_TS];        // keys of the table (BK_EMPTY: free), linear probing
+    uint32_t cnt[BK_TS / 2];    // a 16-bit field per slot: its items, then where its run goes in dl
+    uint32_t dupb[BK_TS / 32];  // slots whose key repeats
+    uint32_t dl[BK_W];          // items of runs, slot << 16 | window index, grouped by slot
+    uint32_t wsum[BK_T / 32];
+    uint32_t first, lastp1, end, ndup;
+};
+
+__device__ __forceinline__ uint32_t bk_slot(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - BK_TS_BITS); }
 
 __device__ __forceinline__ unsigned long long upair(const uint32_t* __restrict__ cpair, uint32_t e) {
     const uint2 p = *reinterpret_cast<const uint2*>(cpair + 2 * (size_t)e);
     return ((unsigned long long)min(p.x, p.y) << 32) | max(p.x, p.y);
 }
 
-// A block stages its tile of GR_TILE sorted keys (and one key on each side) in
-// shared memory, lists the runs that start in the tile, then its threads walk
-// those runs side by side (a run's items four per round trip).
-constexpr uint32_t GR_TILE = 4096;
-
-__global__ void __launch_bounds__(CT) k_c_groups(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val,
-                                                 uint32_t cnt, const uint32_t* __restrict__ cpair,
-                                                 const float* __restrict__ w, uint32_t* __restrict__ cross,
-                                                 uint32_t* __restrict__ multi, uint32_t* __restrict__ gsum,
-                                                 uint32_t* __restrict__ ofl, uint32_t* __restrict__ counts) {
-    __shared__ __align__(16) uint32_t sk[GR_TILE + 4];  // sk[q + 1] = key[t0 + q], q in -1 .. GR_TILE
-    __shared__ uint32_t starts[GR_TILE / 2];
-    __shared__ uint32_t nstart;
-    const uint64_t t0 = (uint64_t)blockIdx.x * GR_TILE;
-    // (keys past cnt read as 0; every comparison below checks its index against cnt)
-    for (uint32_t c = threadIdx.x; c < GR_TILE / 4; c += CT) {
-        const uint4 x = load4<true>(key, t0 + 4 * c, cnt);
-        sk[4 * c + 1] = x.x;
-        sk[4 * c + 2] = x.y;
-        sk[4 * c + 3] = x.z;
-        sk[4 * c + 4] = x.w;
-    }
-    if (threadIdx.x == 0) {
-        nstart = 0;
-        sk[0] = t0 > 0 && t0 - 1 < cnt ? key[t0 - 1] : 0u;
-        sk[GR_TILE + 1] = t0 + GR_TILE < cnt ? key[t0 + GR_TILE] : 0u;
-    }
-    __syncthreads();
-    const uint32_t tn = cnt > t0 ? (uint32_t)min((uint64_t)GR_TILE, cnt - t0) : 0u;  // items of the tile
-    for (uint32_t q = threadIdx.x; q < tn; q += CT) {
-        const uint64_t i = t0 + q;
-        if (i + 1 >= cnt) continue;
-        const uint32_t k = sk[q + 1];
-        if ((i == 0 || sk[q] != k) && sk[q + 2] == k) starts[atomicAdd(&nstart, 1u)] = q;
-    }
-    __syncthreads();
-    const uint32_t ns = nstart;
-    for (uint32_t sidx = threadIdx.x; sidx < ns; sidx += CT) {
-        const uint32_t q0 = starts[sidx], i = (uint32_t)t0 + q0;
-        const uint32_t k = sk[q0 + 1];
-        uint32_t len = 2;
-        while (i + len < cnt && (q0 + len < GR_TILE ? sk[q0 + len + 1] : key[i + len]) == k && len <= GR_MAX) len++;
-        unsigned long long gp[GR_PAIRS];
-        uint32_t gl[GR_PAIRS], gn[GR_PAIRS];
-        double gs[GR_PAIRS];
-        uint32_t ng = 0;
-        bool over = len > GR_MAX;
-        for (uint32_t j0 = 0; j0 < len && !over; j0 += 4) {
-            uint32_t e[4];
-            unsigned long long pj[4];
-            float wj[4];
+// One run of dl[i .. i + len) (window indices in input order), items at sorted
+// positions ws + index: settled here, or flagged for the general path.
+__device__ void bk_walk(const BkSmem& S, uint32_t i, uint32_t len, uint32_t ws, const uint32_t* __restrict__ val,
+                        const uint32_t* __restrict__ cpair, const float* __restrict__ w, uint32_t* __restrict__ cross,
+                        uint32_t* __restrict__ multi, uint32_t* __restrict__ gsum, uint32_t* __restrict__ ofl,
+                        uint32_t* __restrict__ counts) {
+    unsigned long long gp[GR_PAIRS];
+    uint32_t gl[GR_PAIRS], gn[GR_PAIRS];
+    double gs[GR_PAIRS];
+    uint32_t ng = 0;
+    bool over = len > GR_MAX;
+    for (uint32_t j0 = 0; j0 < len && !over; j0 += 4) {
+        uint32_t e[4];
+        unsigned long long pj[4];
+        float wj[4];
 #pragma unroll
-            for (uint32_t t = 0; t < 4; t++) e[t] = j0 + t < len ? val[i + j0 + t] : 0u;
+        for (uint32_t t = 0; t < 4; t++) e[t] = j0 + t < len ? val[ws + (S.dl[i + j0 + t] & 0xFFFFu)] : 0u;
 #pragma unroll
-            for (uint32_t t = 0; t < 4; t++) {
-                pj[t] = j0 + t < len ? upair(cpair, e[t]) : 0ull;
-                wj[t] = j0 + t < len ? w[e[t]] : 0.0f;
-            }
+        for (uint32_t t = 0; t < 4; t++) {
+            pj[t] = j0 + t < len ? upair(cpair, e[t]) : 0ull;
+            wj[t] = j0 + t < len ? w[e[t]] : 0.0f;
+        }
 #pragma unroll
-            for (uint32_t t = 0; t < 4; t++) {
-                if (j0 + t >= len || over) continue;
-                bool found = false;
+        for (uint32_t t = 0; t < 4; t++) {
+            if (j0 + t >= len || over) continue;
+            bool found = false;
 #pragma unroll
-                for (uint32_t g = 0; g < GR_PAIRS; g++)
-                    if (!found && g < ng && gp[g] == pj[t]) {
-                        gs[g] += (double)wj[t];
-                        gn[g]++;
-                        found = true;
-                    }
-                // a later member of a group: not a leader, whatever the rest of the run
-                // holds (a run left to the general path has the same bits cleared there)
-                if (found) atomicAnd(&cross[e[t] >> 5], ~(1u << (e[t] & 31)));
-                if (!found) {
-                    if (ng == GR_PAIRS) {
-                        over = true;
-                    } else {
+            for (uint32_t g = 0; g < GR_PAIRS; g++)
+                if (!found && g < ng && gp[g] == pj[t]) {
+                    gs[g] += (double)wj[t];
+                    gn[g]++;
+                    found = true;
+                }
+            // a later member of a group: not a leader, whatever the rest of the run
+            // holds (a run left to the general path has the same bits cleared there)
+            if (found) atomicAnd(&cross[e[t] >> 5], ~(1u << (e[t] & 31)));
+            if (!found) {
+                if (ng == GR_PAIRS) {
+                    over = true;
+                } else {
 #pragma unroll
-                        for (uint32_t g = 0; g < GR_PAIRS; g++)
-                            if (g == ng) {
-                                gp[g] = pj[t];
-                                gl[g] = e[t];
-                                gn[g] = 1;
-                                gs[g] = (double)wj[t];
-                            }
-                        ng++;
-                    }
+                    for (uint32_t g = 0; g < GR_PAIRS; g++)
+                        if (g == ng) {
+                            gp[g] = pj[t];
+                            gl[g] = e[t];
+                            gn[g] = 1;
+                            gs[g] = (double)wj[t];
+                        }
+                    ng++;
                 }
             }
         }
-        if (over) {
-            // the whole run goes to the general path
-            uint32_t n = i;
-            while (n < cnt && key[n] == k) {
-                atomicOr(&ofl[n >> 5], 1u << (n & 31));
-                n++;
-            }
-            atomicAdd(&counts[1], n - i);
-            continue;
+    }
+    if (over) {
+        for (uint32_t a = 0; a < len; a++) {
+            const uint32_t p = ws + (S.dl[i + a] & 0xFFFFu);
+            atomicOr(&ofl[p >> 5], 1u << (p & 31));
         }
+        atomicAdd(&counts[1], len);
+        return;
+    }
 #pragma unroll
-        for (uint32_t g = 0; g < GR_PAIRS; g++)
-            if (g < ng && gn[g] > 1) {
-                atomicOr(&multi[gl[g] >> 5], 1u << (gl[g] & 31));
-                gsum[gl[g]] = __float_as_uint((float)gs[g]);
+    for (uint32_t g = 0; g < GR_PAIRS; g++)
+        if (g < ng && gn[g] > 1) {
+            atomicOr(&multi[gl[g] >> 5], 1u << (gl[g] & 31));
+            gsum[gl[g]] = __float_as_uint((float)gs[g]);
+        }
+}
+
+// key: the sorted keys of the cnt crossing items (sorted by the bits in mask);
+// val: their edge indices
+__global__ void __launch_bounds__(BK_T, 3)
+    k_c_buckets(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt, uint32_t mask,
+                const uint32_t* __restrict__ cpair, const float* __restrict__ w, uint32_t* __restrict__ cross,
+                uint32_t* __restrict__ multi, uint32_t* __restrict__ gsum, uint32_t* __restrict__ ofl,
+                uint32_t* __restrict__ counts) {
+    extern __shared__ __align__(16) unsigned char bk_raw[];
+    BkSmem& S = *reinterpret_cast<BkSmem*>(bk_raw);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // (cnt < 2^31: every index below fits in 32 bits)
+    const uint32_t c0 = blockIdx.x * BK_C;
+    const uint32_t cend = min(cnt, c0 + BK_C);  // this block's buckets start in [c0, cend)
+    uint32_t ws = c0;                           // the window: sorted items ws .. ws + BK_W - 1
+    for (;;) {
+        // item q of the window (thread q % BK_T, slot q / BK_T) ...
+        uint32_t k[BK_J];
+#pragma unroll
+        for (int j = 0; j < (int)BK_J; j++) {
+            const uint32_t p = ws + j * BK_T + tid;
+            k[j] = p < cnt ? key[p] : BK_EMPTY;
+        }
+        for (uint32_t i = tid; i < BK_TS / 4; i += BK_T)
+            reinterpret_cast<uint4*>(S.tab)[i] = make_uint4(BK_EMPTY, BK_EMPTY, BK_EMPTY, BK_EMPTY);
+        for (uint32_t i = tid; i < BK_TS / 8; i += BK_T) reinterpret_cast<uint4*>(S.cnt)[i] = make_uint4(0, 0, 0, 0);
+        if (tid == 0) {
+            S.first = ~0u;
+            S.lastp1 = 0;
+            S.end = ~0u;
+        }
+        // ... starts a bucket when its key's low bits differ from the previous item's:
+        // the first and last bucket starts in the chunk, and the first one after it
+        // (each warp's last lane hands its keys to the next warp's first lane through
+        // dl, which is free until the runs are listed)
+        const uint32_t chunk_q = cend > ws ? cend - ws : 0u;
+        if (lane == 31)
+#pragma unroll
+            for (int j = 0; j < (int)BK_J; j++) S.dl[j * (BK_T / 32) + warp] = k[j];
+        if (tid == 0) S.dl[BK_J * (BK_T / 32)] = ws > 0 ? key[ws - 1] : 0u;
+        __syncthreads();
+        uint32_t f = ~0u, l = 0, e = ~0u;
+#pragma unroll
+        for (int j = 0; j < (int)BK_J; j++) {
+            const uint32_t q = j * BK_T + tid;
+            const uint32_t p = ws + q;
+            uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, k[j], 1);
+            if (lane == 0) prev = S.dl[warp > 0 ? j * (BK_T / 32) + warp - 1 : j > 0 ? j * (BK_T / 32) - 1 : BK_J * (BK_T / 32)];
+            if (p < cnt && (p == 0 || ((k[j] ^ prev) & mask) != 0)) {
+                if (q < chunk_q) {
+                    f = min(f, q);
+                    l = max(l, q + 1);
+                } else {
+                    e = min(e, q);
+                }
             }
+        }
+        f = __reduce_min_sync(0xFFFFFFFFu, f);
+        l = __reduce_max_sync(0xFFFFFFFFu, l);
+        e = __reduce_min_sync(0xFFFFFFFFu, e);
+        if (lane == 0) {
+            if (f != ~0u) atomicMin(&S.first, f);
+            if (l) atomicMax(&S.lastp1, l);
+            if (e != ~0u) atomicMin(&S.end, e);
+        }
+        __syncthreads();
+        const uint32_t s = S.first, last = S.lastp1 - 1u;
+        uint32_t end = S.end;
+        if (ws + BK_W >= cnt) end = min(end, cnt - ws);
+        if (s == ~0u) return;  // no bucket starts in this block's chunk
+        // the buckets done in this window: [lo, hi)
+        uint32_t lo = s, hi = s;
+        bool again = false;
+        if (end != ~0u) {
+            hi = end;
+        } else if (last > s) {
+            hi = last;  // the last one runs past the window: a window of its own
+            again = true;
+        } else if (s > 0) {
+            again = true;  // the only one runs past the window: a window of its own
+        } else {
+            // a bucket longer than a window: all of it to the general path
+            const uint32_t bv = key[ws] & mask;
+            uint32_t mine = 0;
+            for (uint32_t p = ws + tid;; p += BK_T) {
+                const bool in = p < cnt && (key[p] & mask) == bv;
+                if (!__syncthreads_or(in)) break;
+                if (in) {
+                    atomicOr(&ofl[p >> 5], 1u << (p & 31));
+                    mine++;
+                }
+            }
+            mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+            if (lane == 0 && mine) atomicAdd(&counts[1], mine);
+            return;
+        }
+        // every item of [lo, hi) into the table; its slot kept in 16 bits of sp
+        uint32_t sp[BK_J / 2];
+#pragma unroll
+        for (int j = 0; j < (int)BK_J; j++) {
+            const uint32_t q = j * BK_T + tid;
+            uint32_t sl = 0;
+            if (q >= lo && q < hi) {
+                sl = bk_slot(k[j]);
+                // (at most BK_W < BK_TS keys: a free slot or the key is always found)
+                for (uint32_t probe = 0; probe < BK_TS; probe++) {
+                    const uint32_t old = atomicCAS(&S.tab[sl], BK_EMPTY, k[j]);
+                    if (old == BK_EMPTY || old == k[j]) break;
+                    sl = (sl + 1) & (BK_TS - 1);
+                }
+                atomicAdd(&S.cnt[sl >> 1], 1u << (16 * (sl & 1)));
+            }
+            if (j & 1) sp[j >> 1] |= sl << 16;
+            else sp[j >> 1] = sl;
+        }
+        __syncthreads();
+        // slots of two or more items, and where each one's run starts in dl (thread t:
+        // slots 32 t .. 32 t + 31)
+        {
+            uint4* cq = reinterpret_cast<uint4*>(S.cnt) + 4 * tid;
+            uint32_t tot = 0, bits = 0;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const uint4 x = cq[v];
+                const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int h = 0; h < 8; h++) {
+                    const uint32_t c = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+                    if (c >= 2) {
+                        tot += c;
+                        bits |= 1u << (8 * v + h);
+                    }
+                }
+            }
+            uint32_t x = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane == 31) S.wsum[warp] = x;
+            __syncthreads();
+            uint32_t run = x - tot;
+            for (uint32_t v = 0; v < warp; v++) run += S.wsum[v];
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                if (!((bits >> (8 * v)) & 0xFFu)) continue;
+                const uint4 x4 = cq[v];
+                uint32_t wv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                for (int h = 0; h < 8; h++) {
+                    if (!((bits >> (8 * v + h)) & 1u)) continue;
+                    const uint32_t sh = 16 * (h & 1);
+                    const uint32_t c = (wv[h >> 1] >> sh) & 0xFFFFu;
+                    wv[h >> 1] = (wv[h >> 1] & ~(0xFFFFu << sh)) | (run << sh);
+                    run += c;
+                }
+                cq[v] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            S.dupb[tid] = bits;
+            if (tid == BK_T - 1) S.ndup = run;
+        }
+        __syncthreads();
+        // the items of repeated keys into dl, grouped by slot
+#pragma unroll
+        for (int j = 0; j < (int)BK_J; j++) {
+            const uint32_t q = j * BK_T + tid;
+            if (q >= lo && q < hi) {
+                const uint32_t sl = (sp[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                if ((S.dupb[sl >> 5] >> (sl & 31)) & 1u) {
+                    const uint32_t sh = 16 * (sl & 1);
+                    const uint32_t pos = (atomicAdd(&S.cnt[sl >> 1], 1u << sh) >> sh) & 0xFFFFu;
+                    S.dl[pos] = (sl << 16) | q;
+                }
+            }
+        }
+        __syncthreads();
+        // each run by the thread that holds its first entry: back in input order
+        // (insertion sort on the window index; its entries share their slot bits, which
+        // is all that other threads read of them), then walked
+        const uint32_t nd = S.ndup;
+        for (uint32_t i = tid; i < nd; i += BK_T) {
+            const uint32_t sl = S.dl[i] >> 16;
+            if (i > 0 && (S.dl[i - 1] >> 16) == sl) continue;
+            uint32_t len = 1;
+            while (i + len < nd && (S.dl[i + len] >> 16) == sl) len++;
+            if (len <= GR_MAX)
+                for (uint32_t a = 1; a < len; a++) {
+                    const uint32_t y = S.dl[i + a];
+                    uint32_t b = a;
+                    for (; b > 0 && S.dl[i + b - 1] > y; b--) S.dl[i + b] = S.dl[i + b - 1];
+                    S.dl[i + b] = y;
+                }
+            bk_walk(S, i, len, ws, val, cpair, w, cross, multi, gsum, ofl, counts);
+        }
+        if (!again) return;
+        __syncthreads();  // (dl and the table are free again)
+        ws += hi > s ? hi : s;
     }
 }
 
@@ -694,12 +880,18 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     if ((e = cudaMemcpyAsync(mc_host_slot + 1, c.rank + c.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s))) return (int)e;
     if ((e = cudaStreamSynchronize(s))) return (int)e;
     const uint32_t mc = mc_host_slot[0], nc = mc_host_slot[1];
+    // the sort's bits: as few bytes as leave at most BK_AVG crossing edges to a bucket
+    uint32_t sbits = c.sort_bits;
+    if (!sbits)
+        for (sbits = 8; sbits < 32 && (uint64_t)mc > ((uint64_t)BK_AVG << sbits); sbits += 8) {
+        }
+    const uint32_t mask = sbits >= 32 ? ~0u : (1u << sbits) - 1u;
     int hc = 0;
     if (mc > 1)
-        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, 32, true, true, &hc)) return r;
+        if (int r = radix(hk[0], hk[1], c.val[0], c.val[1], c.m, sbits, true, true, &hc)) return r;
     // 2. runs of equal hash (groups of several edges, and collisions): the crossing bits
     //    become the leader bits, every group member but the first cleared.  Runs with
-    //    few pairs are settled by k_c_groups; the rest are taken out in sorted order
+    //    few pairs are settled by k_c_buckets; the rest are taken out in sorted order
     //    with their pair as the key, sorted again by the pair and marked.
     if ((e = cudaMemsetAsync(c.multi, 0, ((size_t)c.m / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
     uint32_t nsub = 0;
@@ -707,8 +899,13 @@ int launch_contract(void* stream, const ContractArgs& c, uint32_t* mc_host_slot)
     uint32_t* ofl = c.wlead;  // (free until the leaders are counted)
     if (mc > 1) {
         if ((e = cudaMemsetAsync(ofl, 0, ((size_t)mc / 32 + 2) * sizeof(uint32_t), s))) return (int)e;
-        k_c_groups<<<(mc + GR_TILE - 1) / GR_TILE, CT, 0, s>>>(hk[hc], c.val[hc], mc, c.cpair, c.w, c.cross, c.multi,
-                                                               c.gref, ofl, c.counts);
+        if ((e = cudaFuncSetAttribute(k_c_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BkSmem))))
+            return (int)e;
+        if ((e = cudaFuncSetAttribute(k_c_buckets, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared)))
+            return (int)e;
+        k_c_buckets<<<(mc + BK_C - 1) / BK_C, BK_T, sizeof(BkSmem), s>>>(hk[hc], c.val[hc], mc, mask, c.cpair, c.w,
+                                                                       c.cross, c.multi, c.gref, ofl, c.counts);
         if ((e = cudaMemcpyAsync(mc_host_slot + 2, c.counts + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)))
             return (int)e;
         if ((e = cudaStreamSynchronize(s))) return (int)e;

@@ -131,6 +131,7 @@ struct LaunchCfg {
     uint32_t vertex_ctas_per_sm = 4;
     uint32_t batch_shift = LM_BATCH_SHIFT;  // 32: batches of 32 rows only
     bool renew = false;  // sweeps renew the order every round (LM_F_RENEW)
+    uint32_t contract_bits = 0;  // bits of the contraction's hash sort (0: by size); no match graph uses it
     LaunchCfg() {
         while ((1u << chunk_shift) < CHUNK) chunk_shift++;
     }
@@ -301,6 +302,7 @@ struct ContractArgs {
     uint32_t* scan_tmp;
     size_t scan_words;
     uint32_t* err;            // bit 1: mate is not a matching, 2: endpoint >= n
+    uint32_t sort_bits;       // low bits of the hash the sort orders by (8, 16, 24, 32; 0: by size)
 };
 size_t contract_sort_words(uint32_t m);  // words of shist
 // runs every step; mc_host_slot: 2 pinned words (crossing edges and coarse vertices

@@ -214,3 +214,47 @@ def test_rmat21_full_parity(lmc):
     finally:
         lmc.lm.lm_graph_destroy(h)
     _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate))
+
+
+def _tuned_bits(L, bits):
+    keep = L.lm.lm_get_tuning(L.ctx)
+    L.lm.lm_set_tuning(L.ctx, keep["rmax"], keep["chunk"], keep["sweep_ctas_per_sm"], keep["vertex_ctas_per_sm"],
+                       keep["batch"], contract_bits=bits)
+    assert L.lm.lm_get_tuning(L.ctx)["contract_bits"] == bits
+    return keep
+
+
+@pytest.mark.parametrize("bits", [8, 16, 24, 32])
+def test_every_sort_width(lmc, bits):
+    # the hash sorted by its low 8, 16, 24 or 32 bits: buckets of thousands of edges
+    # (at 8 bits on a million edges, most of them running past a block's chunk) down to
+    # runs of one hash; the same contraction every time
+    keep = _tuned_bits(lmc, bits)
+    try:
+        g = synth.rmat(scale=16, edge_factor=16, seed=3)
+        mate, _ = lmc.match(g, 19)
+        _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate))
+        h = synth.rmat(scale=12, edge_factor=64, a=0.7, b=0.1, c=0.1, seed=4)  # hub pairs with many parallel edges
+        mate = oracle.greedy(h.n, h.eu, h.ev, h.w, 5)
+        _same(_contract(lmc, h.n, h.eu, h.ev, h.w, mate), oracle.contract(h.n, h.eu, h.ev, h.w, mate))
+        # two levels, the second on a multigraph of summed weights
+        cm, cvw, ceu, cev, cw = oracle.contract(h.n, h.eu, h.ev, h.w, mate)
+        n2 = int(cvw.shape[0])
+        mate2 = oracle.greedy(n2, ceu, cev, cw, 6)
+        _same(_contract(lmc, n2, ceu, cev, cw, mate2, cvw), oracle.contract(n2, ceu, cev, cw, mate2, cvw))
+    finally:
+        lmc.lm.lm_set_tuning(lmc.ctx, keep["rmax"], keep["chunk"], keep["sweep_ctas_per_sm"],
+                             keep["vertex_ctas_per_sm"], keep["batch"], contract_bits=keep["contract_bits"])
+
+
+def test_buckets_longer_than_a_window(lmc):
+    # 8 sort bits on 2M crossing edges leave about 8000 edges to every bucket, more than
+    # a block's window: every bucket goes to the pair sort
+    keep = _tuned_bits(lmc, 8)
+    try:
+        g = synth.rmat(scale=17, edge_factor=16, seed=7)
+        mate = oracle.greedy(g.n, g.eu, g.ev, g.w, 2)
+        _same(_contract(lmc, g.n, g.eu, g.ev, g.w, mate), oracle.contract(g.n, g.eu, g.ev, g.w, mate))
+    finally:
+        lmc.lm.lm_set_tuning(lmc.ctx, keep["rmax"], keep["chunk"], keep["sweep_ctas_per_sm"],
+                             keep["vertex_ctas_per_sm"], keep["batch"], contract_bits=keep["contract_bits"])

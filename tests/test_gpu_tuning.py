@@ -78,7 +78,8 @@ def test_out_of_range_settings_are_rejected():
     try:
         for bad in [(0, 4096, 0, 4), (64, 1000, 0, 4), (64, 128, 0, 4), (64, 1 << 21, 0, 4),
                     (64, 4096, 17, 4), (64, 4096, 0, 5), ((1 << 20) + 1, 4096, 0, 4),
-                    (64, 4096, 0, 4, 32), (64, 4096, 0, 4, 1000), (64, 4096, 0, 4, 1 << 21)]:
+                    (64, 4096, 0, 4, 32), (64, 4096, 0, 4, 1000), (64, 4096, 0, 4, 1 << 21),
+                    (64, 4096, 0, 4, 512, 4), (64, 4096, 0, 4, 512, 40)]:
             with pytest.raises(lm.LmError) as ei:
                 lm.lm_set_tuning(L.ctx, *bad)
             assert ei.value.code == lm.LM_EINVAL
