@@ -206,17 +206,20 @@ __global__ void __launch_bounds__(CT) k_c_keys(const uint32_t* __restrict__ eu, 
 // below: taken out in order with its pair as the key and sorted again by the pair
 // (which clears the same bits again).
 constexpr uint32_t GR_MAX = 64, GR_PAIRS = 4;
-constexpr uint32_t BK_T = 256, BK_J = 24, BK_W = BK_T * BK_J, BK_C = 4096, BK_TS = 8192, BK_TS_BITS = 13;
+constexpr uint32_t BK_T = 512, BK_J = 12, BK_W = BK_T * BK_J, BK_C = 4096, BK_TS = 8192, BK_TS_BITS = 13;
 constexpr uint32_t BK_AVG = 2048;  // the sort takes as few bytes as leave at most this many items to a bucket
 constexpr uint32_t BK_EMPTY = 0xFFFFFFFFu;
-static_assert(BK_TS == 1u << BK_TS_BITS && BK_TS / 32 == BK_T && BK_W < BK_TS && BK_W < 65536 && BK_C < BK_W,
+static_assert(BK_TS == 1u << BK_TS_BITS && BK_TS / 16 == BK_T && BK_W < BK_TS && BK_W < 65536 && BK_C < BK_W,
               "table of at most 3/4 load, 16-bit counts and window indices, a chunk shorter than a window");
 
 struct BkSmem {
-    uint32_t tab[BK_TS];        // keys of the table (BK_EMPTY: free), linear probing
+    union {
+        uint32_t tab[BK_TS];    // keys of the table (BK_EMPTY: free), linear probing; then
+        uint32_t dl[BK_W];      // items of runs, slot << 16 | window index, grouped by slot
+    };
     uint32_t cnt[BK_TS / 2];    // a 16-bit field per slot: its items, then where its run goes in dl
     uint32_t dupb[BK_TS / 32];  // slots whose key repeats
-    uint32_t dl[BK_W];          // items of runs, slot << 16 | window index, grouped by slot
+    uint32_t hand[BK_J * (BK_T / 32) + 1];  // each warp's last keys, and the key before the window
     uint32_t wsum[BK_T / 32];
     uint32_t first, lastp1, end, ndup;
 };
@@ -299,7 +302,7 @@ __device__ void bk_walk(const BkSmem& S, uint32_t i, uint32_t len, uint32_t ws, 
 
 // key: the sorted keys of the cnt crossing items (sorted by the bits in mask);
 // val: their edge indices
-__global__ void __launch_bounds__(BK_T, 3)
+__global__ void __launch_bounds__(BK_T, 2)
     k_c_buckets(const uint32_t* __restrict__ key, const uint32_t* __restrict__ val, uint32_t cnt, uint32_t mask,
                 const uint32_t* __restrict__ cpair, const float* __restrict__ w, uint32_t* __restrict__ cross,
                 uint32_t* __restrict__ multi, uint32_t* __restrict__ gsum, uint32_t* __restrict__ ofl,
@@ -329,13 +332,12 @@ __global__ void __launch_bounds__(BK_T, 3)
         }
         // ... starts a bucket when its key's low bits differ from the previous item's:
         // the first and last bucket starts in the chunk, and the first one after it
-        // (each warp's last lane hands its keys to the next warp's first lane through
-        // dl, which is free until the runs are listed)
+        // (each warp's last lane hands its keys to the next warp's first lane)
         const uint32_t chunk_q = cend > ws ? cend - ws : 0u;
         if (lane == 31)
 #pragma unroll
-            for (int j = 0; j < (int)BK_J; j++) S.dl[j * (BK_T / 32) + warp] = k[j];
-        if (tid == 0) S.dl[BK_J * (BK_T / 32)] = ws > 0 ? key[ws - 1] : 0u;
+            for (int j = 0; j < (int)BK_J; j++) S.hand[j * (BK_T / 32) + warp] = k[j];
+        if (tid == 0) S.hand[BK_J * (BK_T / 32)] = ws > 0 ? key[ws - 1] : 0u;
         __syncthreads();
         uint32_t f = ~0u, l = 0, e = ~0u;
 #pragma unroll
@@ -343,7 +345,8 @@ __global__ void __launch_bounds__(BK_T, 3)
             const uint32_t q = j * BK_T + tid;
             const uint32_t p = ws + q;
             uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, k[j], 1);
-            if (lane == 0) prev = S.dl[warp > 0 ? j * (BK_T / 32) + warp - 1 : j > 0 ? j * (BK_T / 32) - 1 : BK_J * (BK_T / 32)];
+            if (lane == 0)
+                prev = S.hand[warp > 0 ? j * (BK_T / 32) + warp - 1 : j > 0 ? j * (BK_T / 32) - 1 : BK_J * (BK_T / 32)];
             if (p < cnt && (p == 0 || ((k[j] ^ prev) & mask) != 0)) {
                 if (q < chunk_q) {
                     f = min(f, q);
@@ -413,12 +416,12 @@ __global__ void __launch_bounds__(BK_T, 3)
         }
         __syncthreads();
         // slots of two or more items, and where each one's run starts in dl (thread t:
-        // slots 32 t .. 32 t + 31)
+        // slots 16 t .. 16 t + 15, cnt words 8 t .. 8 t + 7)
         {
-            uint4* cq = reinterpret_cast<uint4*>(S.cnt) + 4 * tid;
+            uint4* cq = reinterpret_cast<uint4*>(S.cnt) + 2 * tid;
             uint32_t tot = 0, bits = 0;
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < 2; v++) {
                 const uint4 x = cq[v];
                 const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(BK_T, 3)
             uint32_t run = x - tot;
             for (uint32_t v = 0; v < warp; v++) run += S.wsum[v];
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < 2; v++) {
                 if (!((bits >> (8 * v)) & 0xFFu)) continue;
                 const uint4 x4 = cq[v];
                 uint32_t wv[4] = {x4.x, x4.y, x4.z, x4.w};
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(BK_T, 3)
                 }
                 cq[v] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             }
-            S.dupb[tid] = bits;
+            reinterpret_cast<uint16_t*>(S.dupb)[tid] = (uint16_t)bits;  // bit 16 t + h: slot 16 t + h
             if (tid == BK_T - 1) S.ndup = run;
         }
         __syncthreads();
