@@ -32,6 +32,38 @@ def test_library_loads_and_exports_every_declared_symbol():
     assert {s for s in exported if s.startswith("lm_")} == set(declared)
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    # every struct the binding passes through the C ABI has the header's field names,
+    # order, offsets and sizes, as a C compiler lays them out from include/lm.h
+    import paper_1302_4587_gb300 as lm
+    structs = {"lm_config": lm.binding.LmConfig, "lm_stats": lm.binding.LmStats, "lm_tuning": lm.binding.LmTuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname}*)0)->{fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    run = subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+    out = dict(l.split(" ", 1) for l in run.stdout.splitlines())  # name -> "size" or "offset size"
+    for cname, py in structs.items():
+        assert int(out[cname].split()[-1]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            off, size = (int(x) for x in out[f"{cname}.{fname}"].split())
+            field = getattr(py, fname)
+            assert (field.offset, field.size) == (off, size), (cname, fname)
+    # and the header declares no field the binding lacks
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lm.h")).read(), flags=re.S)
+    for cname, py in structs.items():
+        body = re.search(r"typedef struct\s*\w*\s*\{([^}]*)\}\s*" + cname + ";", hdr).group(1)
+        names = re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
+        assert names == [f for f, _ in py._fields_], cname
+
+
 def test_strerror_without_gpu():
     import paper_1302_4587_gb300 as lm
     assert lm.lm_strerror(lm.LM_OK) == "ok"
